@@ -1,0 +1,324 @@
+"""FP64 CPU oracle for HENN (arXiv 2505.17368) -- TEST INFRASTRUCTURE ONLY.
+
+The oracle is the slow, literal statement of what the GPU path computes
+(henn_oracle.c).  Only the test-suite, __graft_entry__.smoke() and the
+CPU-baseline leg of bench.py may import it; the product package never does.
+This module compiles the C source with gcc and wraps it with ctypes/numpy.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "henn_oracle.c")
+_HDR = os.path.join(_HERE, "henn_oracle.h")
+_OUT = os.path.join(_HERE, "_build", "libhenn_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+L2, ANGULAR = 0, 1
+GRAPH_NSW, GRAPH_KNN = 0, 1
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (plain C11, FP64, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_OUT), exist_ok=True)
+    fresh = os.path.exists(_OUT) and os.path.getmtime(_OUT) >= max(
+        os.path.getmtime(_SRC), os.path.getmtime(_HDR)
+    )
+    if force or not fresh:
+        tmp = _OUT + f".{os.getpid()}.tmp"
+        subprocess.check_call(
+            ["gcc", "-O2", "-std=c11", "-ffp-contract=off", "-fno-fast-math", "-fopenmp", "-fPIC", "-shared",
+             _SRC, "-o", tmp, "-lm"]
+        )
+        os.replace(tmp, _OUT)
+    return _OUT
+
+
+def _p(a, t):
+    return a.ctypes.data_as(C.POINTER(t))
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            _lib = C.CDLL(build())
+            L = _lib
+            L.ho_mix64.restype = C.c_uint64
+            L.ho_mix64.argtypes = [C.c_uint64]
+            L.ho_derive.restype = C.c_uint64
+            L.ho_derive.argtypes = [C.c_uint64, C.c_uint64]
+            L.ho_bounded.restype = C.c_uint64
+            L.ho_bounded.argtypes = [C.c_uint64, C.c_uint64]
+            L.ho_order_rank.restype = C.c_int64
+            L.ho_order_rank.argtypes = [C.c_uint64, C.c_int32, C.c_int64, C.c_int64]
+            L.ho_ring_window.restype = C.c_int64
+            L.ho_ring_window.argtypes = [C.c_double, C.c_int32, C.c_int64, C.c_int32]
+            L.ho_dist.restype = C.c_double
+            L.ho_dist.argtypes = [C.POINTER(C.c_float), C.POINTER(C.c_float), C.c_int32, C.c_int32]
+            L.ho_sample_positions.restype = C.c_int64
+            L.ho_sample_positions.argtypes = [C.c_uint64, C.c_int32, C.c_int32, C.c_int64, C.c_int64,
+                                              C.POINTER(C.c_int64)]
+            L.ho_verify.restype = C.c_int32
+            L.ho_verify.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.POINTER(C.c_int64),
+                                    C.c_int64, C.POINTER(C.c_int64), C.c_int64, C.c_uint64, C.c_int32,
+                                    C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_uint8)]
+            L.ho_build_layers.restype = C.c_int32
+            L.ho_build_layers.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_int32, C.c_int32,
+                                          C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32,
+                                          C.c_uint64, C.c_int32, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int32)]
+            L.ho_forward_lists.restype = None
+            L.ho_forward_lists.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32,
+                                           C.POINTER(C.c_int64), C.c_int64, C.c_uint64, C.c_int32,
+                                           C.c_int32, C.c_int32, C.POINTER(C.c_int32),
+                                           C.POINTER(C.c_double)]
+            L.ho_forward_row.restype = None
+            L.ho_forward_row.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32,
+                                         C.POINTER(C.c_int64), C.c_int64, C.c_uint64, C.c_int32,
+                                         C.c_int32, C.c_int32, C.c_int64, C.POINTER(C.c_int32),
+                                         C.POINTER(C.c_double)]
+            L.ho_edge_rule.restype = None
+            L.ho_edge_rule.argtypes = [C.POINTER(C.c_int32), C.POINTER(C.c_double), C.c_int64,
+                                       C.c_int32, C.c_int32, C.c_int32, C.POINTER(C.c_int32)]
+            L.ho_search.restype = None
+            L.ho_search.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_int32, C.c_int32, C.c_int32,
+                                    C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_float), C.c_int64,
+                                    C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32, C.c_uint64,
+                                    C.POINTER(C.c_uint64), C.POINTER(C.c_int64),
+                                    C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int64)]
+            L.ho_greedy_layer.restype = C.c_int64
+            L.ho_greedy_layer.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32,
+                                          C.POINTER(C.c_int64), C.POINTER(C.c_int32), C.c_int32,
+                                          C.POINTER(C.c_float), C.c_int64, C.POINTER(C.c_int64),
+                                          C.POINTER(C.c_int64)]
+            L.ho_bruteforce.restype = None
+            L.ho_bruteforce.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_int32, C.c_int32,
+                                        C.POINTER(C.c_float), C.c_int64, C.c_int32,
+                                        C.POINTER(C.c_int64), C.POINTER(C.c_double)]
+            L.ho_bf16_bits.restype = C.c_uint16
+            L.ho_bf16_bits.argtypes = [C.c_float]
+            L.ho_e4m3_bits.restype = C.c_uint8
+            L.ho_e4m3_bits.argtypes = [C.c_float]
+            L.ho_e4m3_value.restype = C.c_double
+            L.ho_e4m3_value.argtypes = [C.c_uint8]
+        return _lib
+
+
+def _f32(X):
+    return np.ascontiguousarray(X, dtype=np.float32)
+
+
+# ----------------------------------------------------------------- RNG
+
+def mix64(z: int) -> int:
+    return lib().ho_mix64(z & 0xFFFFFFFFFFFFFFFF)
+
+
+def derive(h: int, w: int) -> int:
+    return lib().ho_derive(h & 0xFFFFFFFFFFFFFFFF, w & 0xFFFFFFFFFFFFFFFF)
+
+
+def bounded(u: int, s: int) -> int:
+    return lib().ho_bounded(u & 0xFFFFFFFFFFFFFFFF, s)
+
+
+def order_ranks(seed: int, layer: int, s: int) -> np.ndarray:
+    f = lib().ho_order_rank
+    return np.array([f(seed, layer, s, x) for x in range(s)], dtype=np.int64)
+
+
+def ring_window(c0: float, d: int, s: int, m: int) -> int:
+    return lib().ho_ring_window(c0, d, s, m)
+
+
+def dist(a, b, metric=L2) -> float:
+    a, b = _f32(a), _f32(b)
+    return lib().ho_dist(_p(a, C.c_float), _p(b, C.c_float), a.shape[-1], metric)
+
+
+# ------------------------------------------------------------ layers
+
+def sample_positions(seed: int, layer: int, attempt: int, s: int, t: int) -> np.ndarray:
+    out = np.empty(max(t, 1), dtype=np.int64)
+    cnt = lib().ho_sample_positions(seed, layer, attempt, s, t, _p(out, C.c_int64))
+    return out[:cnt].copy()
+
+
+def verify(X, prev, net_pos, seed, layer, attempt, r, w, metric=L2, exhaustive=False):
+    X = _f32(X)
+    prev = np.ascontiguousarray(prev, dtype=np.int64)
+    net_pos = np.ascontiguousarray(net_pos, dtype=np.int64)
+    ring_ok = np.zeros(max(r, 1), dtype=np.uint8)
+    ok = lib().ho_verify(_p(X, C.c_float), X.shape[1], metric, _p(prev, C.c_int64), len(prev),
+                         _p(net_pos, C.c_int64), len(net_pos), seed, layer, attempt, r, w,
+                         int(exhaustive), _p(ring_ok, C.c_uint8))
+    return bool(ok), ring_ok[:r].astype(bool)
+
+
+def build_layers(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, metric=L2,
+                 exhaustive=False):
+    """Layer membership (Alg. 1 + Alg. 2).  Returns dict or raises RuntimeError."""
+    X = _f32(X)
+    n, d = X.shape
+    sizes = np.zeros(64, dtype=np.int64)
+    ids = np.zeros(max(n, 1), dtype=np.int64)
+    down = np.zeros(max(n, 1), dtype=np.int64)
+    attempts = np.zeros(64, dtype=np.int32)
+    L = lib().ho_build_layers(_p(X, C.c_float), n, d, metric, m, max_layers, c0, r, max_attempts,
+                              seed, int(exhaustive), _p(sizes, C.c_int64), _p(ids, C.c_int64),
+                              _p(down, C.c_int64), _p(attempts, C.c_int32))
+    if L < 0:
+        raise RuntimeError("no epsilon-net found within max_attempts")
+    layer_ids, layer_down = [np.arange(n, dtype=np.int64)], [None]
+    off = 0
+    for i in range(1, L + 1):
+        s = int(sizes[i])
+        layer_ids.append(ids[off:off + s].copy())
+        layer_down.append(down[off:off + s].copy())
+        off += s
+    return dict(L=L, sizes=sizes[:L + 1].copy(), ids=layer_ids, down=layer_down,
+                attempts=attempts[:L + 1].copy())
+
+
+def forward_lists(X, ids, seed, layer, M=16, graph=GRAPH_NSW, metric=L2):
+    X = _f32(X)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    s = len(ids)
+    fwd = np.empty((max(s, 1), M), dtype=np.int32)
+    fwd_d = np.empty((max(s, 1), M), dtype=np.float64)
+    lib().ho_forward_lists(_p(X, C.c_float), X.shape[1], metric, _p(ids, C.c_int64), s, seed, layer,
+                           M, graph, _p(fwd, C.c_int32), _p(fwd_d, C.c_double))
+    return fwd[:s], fwd_d[:s]
+
+
+def forward_row(X, ids, seed, layer, p, M=16, graph=GRAPH_NSW, metric=L2):
+    X = _f32(X)
+    ids = np.ascontiguousarray(ids, dtype=np.int64)
+    fwd = np.empty(M, dtype=np.int32)
+    fwd_d = np.empty(M, dtype=np.float64)
+    lib().ho_forward_row(_p(X, C.c_float), X.shape[1], metric, _p(ids, C.c_int64), len(ids), seed, layer, M,
+                         graph, int(p), _p(fwd, C.c_int32), _p(fwd_d, C.c_double))
+    return fwd, fwd_d
+
+
+def edge_rule(fwd, fwd_d, Mmax=32, graph=GRAPH_NSW):
+    fwd = np.ascontiguousarray(fwd, dtype=np.int32)
+    fwd_d = np.ascontiguousarray(fwd_d, dtype=np.float64)
+    s, M = fwd.shape
+    adj = np.empty((max(s, 1), Mmax), dtype=np.int32)
+    lib().ho_edge_rule(_p(fwd, C.c_int32), _p(fwd_d, C.c_double), s, M, Mmax, graph,
+                       _p(adj, C.c_int32))
+    return adj[:s]
+
+
+def build_index(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, M=16, Mmax=32,
+                graph=GRAPH_NSW, metric=L2, exhaustive=False):
+    """Full HENN (Alg. 1): layers, per-layer forward lists and adjacency."""
+    idx = build_layers(X, m, max_layers, c0, r, max_attempts, seed, metric, exhaustive)
+    idx["fwd"], idx["fwd_d"], idx["adj"] = [], [], []
+    for i, ids in enumerate(idx["ids"]):
+        f, fd = forward_lists(X, ids, seed, i, M, graph, metric)
+        idx["fwd"].append(f)
+        idx["fwd_d"].append(fd)
+        idx["adj"].append(edge_rule(f, fd, Mmax, graph))
+    idx.update(M=M, Mmax=Mmax, seed=seed, metric=metric, graph=graph)
+    return idx
+
+
+def search(idx, X, Q, k=10, ef=64, keys=None, out_stride=None, seed=None, ef_upper=1):
+    """Alg. 4 descent + layer-0 beam.  Returns (ids int64, dists f64, stats)."""
+    X, Q = _f32(X), _f32(Q)
+    n, d = X.shape
+    nq = Q.shape[0]
+    kq = np.broadcast_to(np.asarray(k, dtype=np.int32), (nq,)).copy()
+    efq = np.broadcast_to(np.asarray(ef, dtype=np.int32), (nq,)).copy()
+    stride = int(out_stride or max(int(kq.max()) if nq else 1, 1))
+    L = idx["L"]
+    sizes = np.ascontiguousarray(idx["sizes"], dtype=np.int64)
+    ids = np.ascontiguousarray(np.concatenate([np.zeros(0, np.int64)] + list(idx["ids"][1:])), dtype=np.int64)
+    down = np.ascontiguousarray(np.concatenate([np.zeros(0, np.int64)] + list(idx["down"][1:])), dtype=np.int64)
+    Mmax = idx["Mmax"]
+    adj = np.ascontiguousarray(np.concatenate([a.reshape(-1) for a in idx["adj"]]), dtype=np.int32)
+    if ids.size == 0:
+        ids = np.zeros(1, np.int64)
+        down = np.zeros(1, np.int64)
+    keys_a = None if keys is None else np.ascontiguousarray(keys, dtype=np.uint64)
+    out_ids = np.empty((max(nq, 1), stride), dtype=np.int64)
+    out_d = np.empty((max(nq, 1), stride), dtype=np.float64)
+    stats = np.zeros((max(nq, 1), 4), dtype=np.int64)
+    lib().ho_search(_p(X, C.c_float), n, d, idx["metric"], L + 1, _p(sizes, C.c_int64),
+                    _p(ids, C.c_int64), _p(down, C.c_int64), _p(adj, C.c_int32), Mmax,
+                    _p(Q, C.c_float), nq, _p(kq, C.c_int32), _p(efq, C.c_int32), int(ef_upper),
+                    idx["seed"] if seed is None else seed,
+                    None if keys_a is None else _p(keys_a, C.c_uint64),
+                    _p(out_ids, C.c_int64), _p(out_d, C.c_double), stride, _p(stats, C.c_int64))
+    return out_ids[:nq], out_d[:nq], stats[:nq]
+
+
+def greedy_layer(X, ids, adj, q, start, metric=L2):
+    X, q = _f32(X), _f32(q)
+    ids_a = None if ids is None else np.ascontiguousarray(ids, dtype=np.int64)
+    adj = np.ascontiguousarray(adj, dtype=np.int32)
+    hops = C.c_int64(0)
+    evals = C.c_int64(0)
+    r = lib().ho_greedy_layer(_p(X, C.c_float), X.shape[1], metric,
+                              None if ids_a is None else _p(ids_a, C.c_int64), _p(adj, C.c_int32),
+                              adj.shape[1], _p(q, C.c_float), start, C.byref(hops), C.byref(evals))
+    return int(r), hops.value, evals.value
+
+
+def bruteforce(X, Q, k, metric=L2):
+    X, Q = _f32(X), _f32(Q)
+    nq = Q.shape[0]
+    ids = np.empty((max(nq, 1), k), dtype=np.int64)
+    dd = np.empty((max(nq, 1), k), dtype=np.float64)
+    lib().ho_bruteforce(_p(X, C.c_float), X.shape[0], X.shape[1], metric, _p(Q, C.c_float), nq, k,
+                        _p(ids, C.c_int64), _p(dd, C.c_double))
+    return ids[:nq], dd[:nq]
+
+
+def bf16_bits(x: np.ndarray) -> np.ndarray:
+    f = lib().ho_bf16_bits
+    x = np.asarray(x, dtype=np.float32).reshape(-1)
+    return np.array([f(float(v)) for v in x], dtype=np.uint16)
+
+
+def e4m3_bits(x: np.ndarray) -> np.ndarray:
+    f = lib().ho_e4m3_bits
+    x = np.asarray(x, dtype=np.float32).reshape(-1)
+    return np.array([f(v) for v in x.tolist()], dtype=np.uint8)
+
+
+def e4m3_value(code: int) -> float:
+    return lib().ho_e4m3_value(code)
+
+
+def recall_at_k(found_ids, gt_ids, gt_d, found_d=None, k=None):
+    """Recall@k (Sec. 2): |A_q ∩ O_q| / k per query.  A returned id also
+    counts when its FP64 distance equals the k-th ground-truth distance
+    (ties at the boundary)."""
+    found_ids = np.asarray(found_ids)
+    gt_ids = np.asarray(gt_ids)
+    k = k or gt_ids.shape[1]
+    out = np.empty(found_ids.shape[0])
+    for q in range(found_ids.shape[0]):
+        gt = set(gt_ids[q, :k].tolist())
+        hits = 0
+        for j in range(k):
+            v = found_ids[q, j]
+            if v in gt:
+                hits += 1
+            elif found_d is not None and v >= 0 and found_d[q, j] == gt_d[q, k - 1]:
+                hits += 1
+        out[q] = hits / k
+    return out
