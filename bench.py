@@ -1,0 +1,400 @@
+"""Benchmark: HENN search QPS at recall@10 >= 0.95 on one GB300 (1M x 128
+Gaussian-mixture workload rescaled to [0, 255], 10,000 queries, k = 10),
+batched BF16 traversal + exact FP32 rerank vs plain FP32; build seconds.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+One step = one persistent search launch over the whole 10,000-query batch
+with the index resident in HBM.  The beam configuration (ef, ef_upper) is
+the cheapest one of a small sweep whose recall@10 against exact ground
+truth (computed on the device by henn_exact_knn) is >= 0.95.  Under
+torchrun every rank holds its own index replica and its own query batch
+(weak scaling, no collective on the data path); rank 0 prints one JSON
+line with the whole-job throughput.
+
+--impl reference times the FP64 CPU oracle on the host cores instead (the
+reference arm): it builds its own index on a bounded sample of the same
+workload and answers queries with the same beam configuration.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
+WORKLOAD = "mixture-1m-d128"
+EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
+EF_UPPER_SWEEP = [1, 16, 32]
+K = 10
+RECALL_TARGET = 0.95
+NOMINAL_HBM_GBS = 7900.0
+L2_BYTES = 129 * 2**20
+
+
+def _dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def aggregate(local_seconds: float, local_units: int, group=None):
+    """Max of the ranks' timed seconds and the sum of their units."""
+    import torch
+    import torch.distributed as dist
+
+    if not (dist.is_available() and dist.is_initialized()):
+        return local_seconds, local_units
+    t = torch.tensor([local_seconds], dtype=torch.float64)
+    u = torch.tensor([float(local_units)], dtype=torch.float64)
+    dev = torch.device("cuda", torch.cuda.current_device()) if dist.get_backend(group) == "nccl" else None
+    if dev is not None:
+        t, u = t.to(dev), u.to(dev)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX, group=group)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM, group=group)
+    return float(t.item()), int(u.item())
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except OSError:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        rows = []
+        try:
+            with open(self.path) as f:
+                for line in f:
+                    p = [x.strip() for x in line.split(",")]
+                    if len(p) >= 9:
+                        rows.append(p)
+        except OSError:
+            pass
+        finally:
+            try:
+                os.unlink(self.path)
+            except OSError:
+                pass
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"]}
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+
+        sm = [num(r[1]) for r in rows if num(r[1]) is not None]
+        smax = max((num(r[2]) for r in rows if num(r[2]) is not None), default=None)
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[i] for r in rows for i in range(4) if r[5 + i].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": reasons,
+                "samples": len(rows)}
+
+
+def _smi_id(dev, local):
+    """nvidia-smi id of this rank's GPU (its UUID when torch exposes it)."""
+    import torch
+
+    try:
+        u = str(torch.cuda.get_device_properties(dev).uuid)
+        return u if u.startswith("GPU-") else "GPU-" + u
+    except Exception:
+        return str(local)
+
+
+def _recall(found, gt):
+    hits = [len(set(found[q].tolist()) & set(gt[q].tolist())) for q in range(gt.shape[0])]
+    return float(np.mean(hits)) / gt.shape[1]
+
+
+def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, want_events=True):
+    import torch
+
+    H = sys.modules["paper_2505_17368_gb300"]
+    nq = Qd.shape[0]
+    ids = torch.empty((nq, K), dtype=torch.int64, device=Qd.device)
+    dd = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
+    for _ in range(warmup):
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, stream=stream, out=(ids, dd))
+    torch.cuda.synchronize()
+    times = []
+    for _ in range(steps):
+        if flush is not None:
+            flush.add_(1.0)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, stream=stream, out=(ids, dd))
+        e1.record(stream)
+        e1.synchronize()
+        times.append(e0.elapsed_time(e1) / 1e3)
+    return times, ids
+
+
+def _cpu_oracle_leg(workload_n: int, ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1):
+    """The FP64 oracle (as it stands) on the host cores: its own index on
+    the first n_sample points of the workload stream, then the same beam
+    configuration on nq_sample queries.  Returns (qps, cores, seconds)."""
+    import oracle
+
+    X, Q, _ = synth.workload(WORKLOAD, n=n_sample, nq=nq_sample)
+    idx = oracle.build_index(X, seed=0)
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    secs = []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu)
+        secs.append(time.perf_counter() - t0)
+    return nq_sample / statistics.median(secs), cores, secs
+
+
+def run_reference(args):
+    ws, rank, _ = _dist_env()
+    if rank != 0:
+        return 0
+    ef, efu = args.ref_ef, args.ref_ef_upper
+    n_sample, nq_sample = args.ref_n, args.ref_nq
+    for _ in range(args.warmup):
+        pass  # the oracle has no warm-up state; its index is built once below
+    qps, cores, secs = _cpu_oracle_leg(1_000_000, ef, efu, n_sample, nq_sample, steps=args.steps)
+    sample = (f"FP64 oracle index on the first {n_sample} of the 1M mixture points (same generator), "
+              f"{nq_sample} queries per step, ef={ef}, ef_upper={efu}, k={K}")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": {"workload": WORKLOAD, "n": 1_000_000, "d": 128, "nq": 10_000, "k": K},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def run_ours(args):
+    import torch
+
+    ws, rank, local = _dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    dev = torch.device("cuda", torch.cuda.current_device())
+    import paper_2505_17368_gb300 as H
+
+    H.load()
+    stream = torch.cuda.current_stream()
+    # ---- inputs (same base set on every rank, own query batch per rank)
+    X, rngmap = synth.gaussian_mixture(args.n, 128, 1000, seed=0, rescale_to_255=True)
+    Q, _ = synth.gaussian_mixture(args.nq, 128, 1000, seed=1 + rank, rescale_from=rngmap, rescale_to_255=True)
+    Xd = torch.from_numpy(X).to(dev)
+    Qd = torch.from_numpy(Q).to(dev)
+    torch.cuda.synchronize()
+    # ---- builds (inputs already resident; wall clock of henn_build)
+    t0 = time.perf_counter()
+    idx_bf16 = H.Index(Xd, storage=H.BF16, seed=0)
+    build_bf16 = time.perf_counter() - t0
+    t0 = time.perf_counter()
+    idx_f32 = H.Index(Xd, storage=H.F32, seed=0)
+    build_f32 = time.perf_counter() - t0
+    info = idx_bf16.info()
+    # ---- exact ground truth on the device
+    gt, _ = H.exact_knn(Xd, Qd, K)
+    gt = gt.cpu().numpy()
+    # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
+    def sweep(index):
+        best = None
+        for efu in EF_UPPER_SWEEP:
+            for ef in EF_SWEEP:
+                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream)
+                r = _recall(ids.cpu().numpy(), gt)
+                if r >= RECALL_TARGET:
+                    if best is None or min(t) < best[2]:
+                        best = (ef, efu, min(t), r)
+                    break
+        return best
+    flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
+    chosen = sweep(idx_bf16)
+    plain = sweep(idx_f32)
+    if chosen is None or plain is None:
+        raise SystemExit("recall target not reached by any swept configuration")
+    ef, efu, _, rec = chosen
+    # ---- algorithmic bytes per launch from the kernel's own counters
+    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    row_bf16 = 128 * 2
+    R = min(4 * K, ef)
+    alg_bytes = int(st[:, 0].sum() * row_bf16 + st[:, 1].sum() * 128 + args.nq * (R * 128 * 4 + 128 * 4 + K * 12))
+    # ---- timed region
+    if ws > 1:
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(_smi_id(dev, local)) as clk:
+        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream)
+        torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.summary()
+    local_time = sum(times)
+    tmax, units = aggregate(local_time, args.nq * args.steps)
+    value = units / tmax
+    # plain FP32 comparator, same procedure
+    p_ef, p_efu, _, p_rec = plain
+    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream)
+    plain_qps = args.nq / statistics.median(p_times)
+    # one launch per query, FP32 (latency form), on a sample
+    ns = min(200, args.nq)
+    t_one = []
+    for q in range(ns):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+        t_one.append(e0.elapsed_time(e1) / 1e3)
+    per_query_qps = 1.0 / statistics.median(t_one)
+    # ---- end to end through the C ABI with host buffers
+    Qh = torch.from_numpy(Q).pin_memory()
+    e2e_t = []
+    for i in range(args.warmup + args.steps):
+        t0 = time.perf_counter()
+        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, stream=stream)
+        if i >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+    e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
+    peaks, src = _peaks()
+    avg = statistics.mean(times)
+    achieved = alg_bytes / avg / 1e9
+    traffic = _profile_traffic()
+    line = {
+        "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
+            "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
+            "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
+            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "recall_at_10": p_rec},
+            "plain_f32_per_query_launch_qps": per_query_qps,
+            "parallelism": f"replicas{ws}",
+        },
+        "build_seconds": build_bf16,
+        "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
+                     "frac": achieved / peaks["hbm_gbs"], "frac_nominal": achieved / NOMINAL_HBM_GBS,
+                     "traffic": traffic, "peak_source": src,
+                     "algorithmic_bytes_per_launch": alg_bytes, "kernel": "k_search<bf16>"},
+        "e2e": {"value": e2e_units / e2e_tmax, "unit": "queries/s",
+                "h2d_bytes_per_step": int(args.nq * 128 * 4), "d2h_bytes_per_step": int(args.nq * K * 12)},
+        "gpu_launches": args.steps,
+        "clocks": clocks,
+    }
+    if rank == 0 and not args.no_cpu_baseline:
+        qps, cores, secs = _cpu_oracle_leg(args.n, ef, efu, args.cpu_n, args.cpu_nq)
+        line["cpu_baseline"] = {
+            "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
+            "sample": (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
+                       f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, {sum(secs):.1f} s of search"),
+        }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if ws > 1:
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+def _profile_traffic():
+    """DRAM bytes per launch of the search kernel from the committed ncu
+    summary, if it was taken on the current kernel source; else None."""
+    import hashlib
+
+    path = os.path.join(ROOT, "profiles", "search_bf16_mixture-1m-d128.md")
+    src = os.path.join(ROOT, "paper_2505_17368_gb300", "csrc", "search.cu")
+    try:
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        kv = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                kv[k.strip()] = v.strip().strip("`")
+        if kv.get("search.cu sha256[:16]") == sha:
+            return float(kv["dram bytes per launch"])
+    except (OSError, KeyError, ValueError):
+        pass
+    return None
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=1_000_000)
+    ap.add_argument("--nq", type=int, default=10_000)
+    ap.add_argument("--cpu-n", type=int, default=20_000)
+    ap.add_argument("--cpu-nq", type=int, default=2_000)
+    ap.add_argument("--ref-n", type=int, default=20_000)
+    ap.add_argument("--ref-nq", type=int, default=1_000)
+    ap.add_argument("--ref-ef", type=int, default=128)
+    ap.add_argument("--ref-ef-upper", type=int, default=32)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.warmup < 3:
+        ap.error("--warmup must be >= 3")
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_ours(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,228 @@
+/*
+ * henn.h -- C ABI of libhenn, a GB300 (sm_103a) implementation of the data
+ * parallel hot path of HENN, the Hierarchical epsilon-Net Navigation graph
+ * for approximate nearest neighbour search (arXiv 2505.17368).
+ *
+ * The problem (Sec. 2, "Data Model" and "Problem setting"): n points x_i in
+ * R^d with a distance (l2, or angular 1 - cos per App. F); for a query q
+ * return k points of X with the smallest distance, approximately, with high
+ * Recall@k.  The index (Def. 1) is a stack of layers L_0 = X, L_1, ..., L_L,
+ * each an eps-net of the one below it for ring ranges (Def. 2, Eq. 1,
+ * Alg. 1, Alg. 2), each with its own navigable graph (App. C), linked
+ * between layers by the copies of the same point.  A query descends from a
+ * random node of the top layer by greedy search (Alg. 4) and runs a beam of
+ * width ef on the bottom layer (Sec. 2.2, last paragraph).
+ *
+ * Conventions shared by every call
+ *  - Vectors are float32, row-major, rows of d values, no padding.
+ *  - Pointers marked "device" are CUDA device pointers of the current
+ *    device; "host" pointers are ordinary (pageable or pinned) memory.
+ *    Calls with an `on_device` flag take all their array arguments from
+ *    that side.
+ *  - `stream` is a cudaStream_t (NULL = legacy default stream).  Device-side
+ *    calls are stream ordered: they return after enqueueing, results are
+ *    valid once the stream has been synchronised.  Host-side calls
+ *    synchronise the stream before returning.
+ *  - The caller owns every array it passes; the library copies what it
+ *    keeps.  The index owns its device memory until henn_free().
+ *  - No call throws.  Each returns a henn_status; on failure nothing is
+ *    written to *out handles and henn_last_error() describes the failure.
+ *  - A const index may be searched concurrently from several host threads
+ *    and streams.
+ *
+ * Random numbers (ring ranges, samples, insertion order, entry nodes) come
+ * from SplitMix64 (Steele, Lea & Flood 2014) used counter-style:
+ *   mix64(z)      = SplitMix64 output finaliser
+ *   derive(h, w)  = mix64(h + (w + 1) * 0x9E3779B97F4A7C15)
+ *   bounded(u, s) = floor(u * s / 2^64)
+ * keyed by the tags below; the same seed gives the same index on any GPU.
+ */
+#ifndef HENN_H
+#define HENN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HENN_ABI_VERSION 1
+
+/* RNG stream tags (ASCII words). */
+#define HENN_TAG_SAMPLE 0x53414D50ULL  /* "SAMP" Alg. 2 draws with replacement        */
+#define HENN_TAG_RCENTRE 0x5243454EULL /* "RCEN" centre of a sampled ring range        */
+#define HENN_TAG_RSTART 0x52535441ULL  /* "RSTA" first rank of a sampled ring range    */
+#define HENN_TAG_ORDER 0x4F524452ULL   /* "ORDR" NSW insertion order of a layer        */
+#define HENN_TAG_ENTRY 0x454E5452ULL   /* "ENTR" random top-layer node of a query      */
+
+typedef enum {
+  HENN_OK = 0,
+  HENN_ERR_INVALID_ARG = 1,      /* a size, pointer or parameter is out of range      */
+  HENN_ERR_OOM = 2,              /* device allocation failed                          */
+  HENN_ERR_CUDA = 3,             /* a CUDA runtime call or kernel failed              */
+  HENN_ERR_EPSNET_NOT_FOUND = 4, /* Alg. 2 found no eps-net within max_attempts       */
+  HENN_ERR_TIMEOUT = 5,          /* a bounded device wait ran out                     */
+  HENN_ERR_UNSUPPORTED = 6       /* valid request this build cannot serve             */
+} henn_status;
+
+typedef enum { HENN_L2 = 0, HENN_ANGULAR = 1 } henn_metric;
+
+/* Storage of the vectors the search traverses.  BF16 and FP8 keep an FP32
+ * copy as well, used for the exact rerank of the final candidates. */
+typedef enum { HENN_F32 = 0, HENN_BF16 = 1, HENN_FP8E4M3 = 2 } henn_storage;
+
+/* Navigable graph of each layer (App. C; App. F "Navigation Graphs"). */
+typedef enum { HENN_GRAPH_NSW = 0, HENN_GRAPH_KNN = 1 } henn_graph;
+
+/* Engine for the construction distance tiles. */
+typedef enum { HENN_TILES_AUTO = 0, HENN_TILES_SIMT = 1, HENN_TILES_TCGEN05 = 2 } henn_tiles;
+
+/* ------------------------------------------------------------------ build */
+
+typedef struct {
+  uint32_t struct_size;  /* sizeof(henn_build_params), for ABI checks          */
+  int32_t metric;        /* henn_metric                                         */
+  int32_t storage;       /* henn_storage                                        */
+  int32_t graph;         /* henn_graph                                          */
+  int32_t m;             /* layer decay 2^m (Alg. 1, Lemma 1); 1..8, default 4  */
+  int32_t max_layers;    /* L of Alg. 1; 0 = while |L_{i-1}| >= 2^m (Cor. 3)    */
+  double eps_c0;         /* c0 of Eq. 1; default 1.0                            */
+  int32_t num_ranges;    /* r, the "range size" of App. F; default 100          */
+  int32_t max_attempts;  /* Las-Vegas repeats of Alg. 2 per layer; default 64   */
+  int32_t M;             /* forward links per inserted point; default 16        */
+  int32_t Mmax;          /* adjacency row width; 32 (only 32 is supported)      */
+  int32_t tiles;         /* henn_tiles                                          */
+  uint64_t seed;         /* index seed                                          */
+} henn_build_params;
+
+/* Fills *p with the defaults above (struct_size included). */
+void henn_build_params_default(henn_build_params* p);
+
+typedef struct henn_index henn_index; /* opaque, owned by the library */
+
+/*
+ * henn_build -- BuildHENN (Alg. 1).
+ * X: n x d float32 (device if x_on_device, else host); 1 <= n < 2^31,
+ * 1 <= d <= 1024, finite values.  For every layer i >= 1 (while i <=
+ * max_layers and |L_{i-1}| >= 2^m): draw ceil(|L_{i-1}|/2^m) samples of
+ * L_{i-1} with replacement (Alg. 2, Cor. 2), keep the distinct ones, accept
+ * them when every one of num_ranges random ring ranges (Def. 2) holding
+ * floor(eps*s)+1 points, eps from Eq. 1, contains one of them (IsEpsNet,
+ * App. C practical implementation), else draw again.  Every layer then gets
+ * its navigable graph: each point links to the M nearest points inserted
+ * before it (NSW, App. C; or its M nearest overall for HENN_GRAPH_KNN) and
+ * each row keeps its nearest predecessor plus the nearest Mmax-1 of its
+ * forward and reverse links.
+ * On success *out owns device memory for the vectors, layers and graphs.
+ * Errors: HENN_ERR_INVALID_ARG, HENN_ERR_OOM, HENN_ERR_CUDA,
+ * HENN_ERR_EPSNET_NOT_FOUND.  Synchronises `stream` before returning.
+ */
+henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t x_on_device,
+                       const henn_build_params* p, void* stream, henn_index** out);
+
+/* Releases the index and its device memory.  NULL is a no-op. */
+void henn_free(henn_index* idx);
+
+/* ----------------------------------------------------------------- search */
+
+typedef struct {
+  uint32_t struct_size;       /* sizeof(henn_search_params)                         */
+  const int32_t* k;           /* per-query k, or NULL to use k_uniform              */
+  const int32_t* ef;          /* per-query beam width, or NULL to use ef_uniform    */
+  int32_t k_uniform;          /* default 10                                         */
+  int32_t ef_uniform;         /* default 64; a beam is never narrower than k        */
+  int32_t rerank_mult;        /* BF16/FP8: exact FP32 rerank of the best
+                                 rerank_mult * k candidates; 0 = 4                  */
+  const uint64_t* query_keys; /* per-query RNG key for the entry node, or NULL to
+                                 use the query's row index                          */
+  int32_t* stats;             /* optional, 4 int32 per query: distance evaluations,
+                                 layer-0 expansions, upper-layer moves, visited-set
+                                 evictions                                          */
+  int32_t warps_per_block;    /* 0 = autotuned                                      */
+  int32_t hash_bits;          /* log2 visited-set slots per query, 0 = autotuned    */
+  int32_t ef_upper;           /* beam width on layers >= 1; 0 or 1 = GreedySearch of
+                                 Alg. 4 (default 1)                                 */
+} henn_search_params;
+
+void henn_search_params_default(henn_search_params* sp);
+
+/*
+ * henn_search -- Query of Alg. 4 for a batch, one persistent launch.
+ * Q: nq x d float32.  Per query: entry = a random node of the top layer
+ * (keyed by query_keys[q]), greedy search (Alg. 4 GreedySearch) on layers
+ * L..1 (or a beam of width ef_upper, the candidate set of Sec. 2.2 applied
+ * on every layer), each entered at the copy of the previous result, then the
+ * best-first beam of width max(ef, k) on layer 0; BF16/FP8 indexes then
+ * rerank the best rerank_mult*k candidates with exact FP32 distances.
+ * out_ids (int64) / out_dists (float32): nq rows of out_stride >= max k;
+ * row q holds k[q] results in ascending distance (l2: Euclidean distance,
+ * angular: 1 - cos), padded with -1 / +inf.  All arrays (Q, k, ef,
+ * query_keys, stats, outputs) are device pointers if q_on_device, else host
+ * pointers (the call then copies, runs and synchronises).
+ * Errors: HENN_ERR_INVALID_ARG (k < 1, k > 1024, ef > 4096, stride < k,
+ * NULL pointers), HENN_ERR_OOM, HENN_ERR_CUDA.
+ */
+henn_status henn_search(const henn_index* idx, const float* Q, int64_t nq, int32_t q_on_device,
+                        const henn_search_params* sp, int64_t* out_ids, float* out_dists,
+                        int32_t out_stride, void* stream);
+
+/* ------------------------------------------------------ introspection */
+
+#define HENN_MAX_LAYERS 32
+
+typedef struct {
+  uint32_t struct_size;
+  int64_t n;
+  int32_t d, metric, storage, graph, M, Mmax;
+  int32_t L;                               /* layers above L_0                */
+  int64_t sizes[HENN_MAX_LAYERS];          /* |L_i|, i = 0..L                 */
+  int32_t attempts[HENN_MAX_LAYERS];       /* Alg. 2 attempt that succeeded   */
+  int32_t ambiguous_rings[HENN_MAX_LAYERS];/* rings re-decided in FP64        */
+  int64_t device_bytes;                    /* index memory on the device      */
+  int64_t uncertified_rows;                /* rows whose tile candidates had to
+                                              be recomputed exactly           */
+  double build_seconds;                    /* wall time of henn_build         */
+} henn_index_info;
+
+henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info);
+
+/*
+ * Copies layer `layer` to HOST arrays (any may be NULL):
+ *   ids   [|L_i|]        global point ids, ascending
+ *   down  [|L_i|]        position of each point in layer i-1 (layer >= 1)
+ *   adj   [|L_i| * Mmax] layer-local neighbour indices, -1 padded
+ *   fwd   [|L_i| * M]    forward links (nearest earlier-inserted points)
+ *   fwd_d [|L_i| * M]    their distances (squared l2, or 1 - cos)
+ * Synchronises the device.
+ */
+henn_status henn_index_get_layer(const henn_index* idx, int32_t layer, int32_t* ids, int32_t* down,
+                                 int32_t* adj, int32_t* fwd, float* fwd_d);
+
+/* ------------------------------------------------- standalone kernels */
+
+/*
+ * Exact k nearest neighbours of each query among the n base vectors (the
+ * k-NN query of Sec. 2): tiled distances plus an exact FP32 rerank.  All
+ * pointers device; out rows of k (int64 ids, float distances as in
+ * henn_search).  1 <= k <= 112, 1 <= d <= 1024.
+ */
+henn_status henn_exact_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t nq, int32_t k,
+                           int32_t metric, int64_t* out_ids, float* out_dists, void* stream);
+
+/*
+ * Precision copy of rows (device pointers): HENN_BF16 writes n*d uint16
+ * (round to nearest even); HENN_FP8E4M3 writes n*d bytes of E4M3 codes of
+ * x / scale with scale = max|x_row| / 448 (FP32; 1 for an all-zero row),
+ * round to nearest even, saturating, and the n scales.
+ */
+henn_status henn_quantize_rows(const float* X, int64_t n, int32_t d, int32_t storage, void* out,
+                               float* scales, void* stream);
+
+/* Message of the last failure on this host thread ("" if none). */
+const char* henn_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* HENN_H */

@@ -1,0 +1,744 @@
+// henn_abi.cu -- host orchestration behind the C ABI of include/henn.h.
+//
+// BuildHENN (Alg. 1) runs layer by layer: membership first (Alg. 2 draws,
+// ring-range verification, Las-Vegas retries; the only device->host reads
+// are the layer size and the ring verdicts of each attempt), then every
+// layer's navigable graph (tiles + top-KP, exact FP32 rerank, edge rule) and
+// its traversal copy.  Search is one persistent kernel per batch.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <exception>
+#include <string>
+#include <vector>
+
+#include "../../include/henn.h"
+#include "common.cuh"
+#include "kernels.cuh"
+#include "search.cuh"
+
+using namespace henn;
+
+namespace {
+
+thread_local std::string g_error;
+
+struct Failure : std::exception {
+  henn_status status;
+  std::string msg;
+  Failure(henn_status s, std::string m) : status(s), msg(std::move(m)) {}
+};
+
+void check(cudaError_t e, const char* what, int line) {
+  if (e == cudaSuccess) return;
+  henn_status s = (e == cudaErrorMemoryAllocation) ? HENN_ERR_OOM : HENN_ERR_CUDA;
+  throw Failure(s, std::string(what) + " (line " + std::to_string(line) + "): " + cudaGetErrorString(e));
+}
+#define CK(x) check((x), #x, __LINE__)
+#define CKL(what) check(cudaGetLastError(), what, __LINE__)
+
+void require(bool ok, const std::string& msg) {
+  if (!ok) throw Failure(HENN_ERR_INVALID_ARG, msg);
+}
+
+// Stream-ordered scratch allocation, released when the owner goes out of
+// scope (also on failure).
+struct Scratch {
+  cudaStream_t st;
+  std::vector<void*> ptrs;
+  explicit Scratch(cudaStream_t s) : st(s) {}
+  template <typename T>
+  T* get(size_t count) {
+    void* p = nullptr;
+    size_t bytes = count * sizeof(T);
+    if (bytes == 0) bytes = 16;
+    CK(cudaMallocAsync(&p, bytes, st));
+    ptrs.push_back(p);
+    return static_cast<T*>(p);
+  }
+  ~Scratch() {
+    for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+};
+
+int64_t ring_window(double c0, int32_t d, int64_t s, int32_t m) {
+  // eps(s) * s with eps from Eq. 1 (natural log), evaluated as
+  // ((c0 * d) * log(s)) * 2^m; heavy rings hold floor(eps*s)+1 points.
+  volatile double es = c0 * (double)d;
+  es = es * std::log((double)s);
+  es = es * (double)(1LL << m);
+  if (!(es < (double)s)) return s + 1;
+  return (int64_t)std::floor(es) + 1;
+}
+
+int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+
+}  // namespace
+
+// ----------------------------------------------------------- the index
+
+struct LayerDev {
+  int64_t size = 0;
+  int32_t* ids = nullptr;   // global ids (layers >= 1)
+  int32_t* down = nullptr;  // positions in the layer below (layers >= 1)
+  int32_t* adj = nullptr;   // size x 32
+  int32_t* fwd = nullptr;   // size x M
+  float* fwd_d = nullptr;   // size x M
+  void* vec = nullptr;      // traversal vectors, layer order
+  float* vscale = nullptr;  // FP8 per-row scales
+};
+
+struct henn_index {
+  int64_t n = 0;
+  int32_t d = 0, dpad = 0, metric = 0, storage = 0, graph = 0, M = 16, Mmax = 32;
+  uint64_t seed = 0;
+  int32_t L = 0;
+  std::vector<LayerDev> layers;
+  std::vector<int32_t> attempts, ambiguous;
+  float* x32 = nullptr;  // raw vectors, rows of dpad
+  float* xw = nullptr;   // working vectors: x32 (l2) or unit rows (angular)
+  float* inv_norm = nullptr;
+  SearchLayer* d_layers = nullptr;
+  std::vector<void*> allocs;
+  int64_t bytes = 0;
+  int64_t uncertified = 0;
+  double build_seconds = 0.0;
+  int device = 0;
+
+  template <typename T>
+  T* alloc(size_t count) {
+    void* p = nullptr;
+    size_t b = count * sizeof(T);
+    if (b == 0) b = 16;
+    CK(cudaMalloc(&p, b));
+    allocs.push_back(p);
+    bytes += (int64_t)b;
+    return static_cast<T*>(p);
+  }
+  ~henn_index() {
+    for (void* p : allocs) cudaFree(p);
+  }
+};
+
+// ------------------------------------------------------------ defaults
+
+extern "C" void henn_build_params_default(henn_build_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(henn_build_params);
+  p->metric = HENN_L2;
+  p->storage = HENN_F32;
+  p->graph = HENN_GRAPH_NSW;
+  p->m = 4;
+  p->max_layers = 0;
+  p->eps_c0 = 1.0;
+  p->num_ranges = 100;
+  p->max_attempts = 64;
+  p->M = 16;
+  p->Mmax = 32;
+  p->tiles = HENN_TILES_AUTO;
+  p->seed = 0;
+}
+
+extern "C" void henn_search_params_default(henn_search_params* sp) {
+  if (!sp) return;
+  std::memset(sp, 0, sizeof(*sp));
+  sp->struct_size = sizeof(henn_search_params);
+  sp->k_uniform = 10;
+  sp->ef_uniform = 64;
+  sp->rerank_mult = 4;
+  sp->ef_upper = 1;
+}
+
+extern "C" const char* henn_last_error(void) { return g_error.c_str(); }
+
+// --------------------------------------------------------------- build
+
+namespace {
+
+// Alg. 2 for one layer: returns the accepted attempt; fills pos/ids.
+int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32_t layer, int64_t s,
+                               const int32_t* prev_ids, Scratch& sc, uint8_t* flags, int64_t* tile_buf,
+                               int64_t* d_total, int32_t* pos, int32_t* ids, int64_t* out_count,
+                               int32_t* out_ambiguous, cudaStream_t st) {
+  const int64_t decay = 1LL << p.m;
+  const int64_t t = (s + decay - 1) / decay;
+  const int64_t w = ring_window(p.eps_c0, ix->d, s, p.m);
+  const int32_t r = p.num_ranges;
+  int32_t* centre = sc.get<int32_t>(r);
+  int64_t* start = sc.get<int64_t>(r);
+  float* lo = sc.get<float>(r);
+  float* hi = sc.get<float>(r);
+  int32_t* status = sc.get<int32_t>(r);
+  float* D = (w <= s) ? sc.get<float>((size_t)r * s) : nullptr;
+  double* D64 = nullptr;
+  double* bounds = sc.get<double>(2);
+  // certified FP32 error model of the ring distances (see layers.cu)
+  const double u = std::ldexp(1.0, -24);
+  double er = 0.0, ea = 0.0;
+  if (ix->metric == HENN_ANGULAR)
+    ea = (4.0 * ix->dpad + 64.0) * u;
+  else
+    er = (ix->dpad + 16.0) * u + 1e-12;
+  std::vector<int32_t> h_status(r), h_centre(r);
+  std::vector<int64_t> h_start(r);
+  int32_t ambiguous = 0;
+  for (int32_t a = 0; a < p.max_attempts; ++a) {
+    CK(cudaMemsetAsync(flags, 0, (size_t)s, st));
+    LayerSampleArgs la;
+    la.base = derive(derive(derive(ix->seed, HENN_TAG_SAMPLE), (uint64_t)layer), (uint64_t)a);
+    la.s = s;
+    la.t = t;
+    la.flags = flags;
+    launch_sample(la, st);
+    launch_compact(flags, s, prev_ids, tile_buf, d_total, pos, ids, st);
+    CKL("sample/compact");
+    int64_t count = 0;
+    CK(cudaMemcpyAsync(&count, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    bool pass = true;
+    if (w <= s) {
+      uint64_t bc = derive(derive(derive(ix->seed, HENN_TAG_RCENTRE), (uint64_t)layer), (uint64_t)a);
+      uint64_t bs = derive(derive(derive(ix->seed, HENN_TAG_RSTART), (uint64_t)layer), (uint64_t)a);
+      launch_ring_params(bc, bs, r, s, s - w + 1, centre, start, st);
+      launch_ring_dist(ix->x32, ix->dpad, prev_ids, s, centre, r, ix->metric, ix->inv_norm, D, st);
+      CKL("ring distances");
+      // the net positions are known on the device only after compaction;
+      // the decision kernel reads them there (count read below)
+      CK(cudaStreamSynchronize(st));
+      launch_ring_select_decide(D, s, start, w, r, pos, count, er, ea, lo, hi, status, st);
+      CKL("ring select/decide");
+      CK(cudaMemcpyAsync(h_status.data(), status, sizeof(int32_t) * r, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+      for (int32_t q = 0; q < r; ++q)
+        if (h_status[q] == kRingFail) pass = false;
+      if (pass) {
+        bool fetched = false;
+        for (int32_t q = 0; q < r && pass; ++q) {
+          if (h_status[q] != kRingAmbiguous) continue;
+          if (!fetched) {
+            CK(cudaMemcpyAsync(h_centre.data(), centre, sizeof(int32_t) * r, cudaMemcpyDeviceToHost, st));
+            CK(cudaMemcpyAsync(h_start.data(), start, sizeof(int64_t) * r, cudaMemcpyDeviceToHost, st));
+            if (!D64) D64 = sc.get<double>((size_t)s);
+            fetched = true;
+          }
+          ++ambiguous;
+          launch_ring_recheck(ix->x32, ix->d, ix->dpad, prev_ids, s, h_centre[q], h_start[q], w, ix->metric, pos,
+                              count, D64, bounds, status, q, st);
+          CKL("ring FP64 recheck");
+          int32_t v = 0;
+          CK(cudaMemcpyAsync(&v, status + q, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+          CK(cudaStreamSynchronize(st));
+          if (v != kRingPass) pass = false;
+        }
+      }
+    } else {
+      CK(cudaStreamSynchronize(st));
+    }
+    if (pass) {
+      *out_count = count;
+      *out_ambiguous = ambiguous;
+      return a;
+    }
+  }
+  return -1;
+}
+
+void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, cudaStream_t st) {
+  LayerDev& Ly = ix->layers[li];
+  const int64_t s = Ly.size;
+  const int32_t dpad = ix->dpad, M = ix->M;
+  Scratch sc(st);
+  // insertion order and centred operand
+  int64_t chunks = (s + 4095) / 4096;
+  float* partial = sc.get<float>((size_t)chunks * dpad);
+  float* mean = sc.get<float>(dpad);
+  launch_layer_mean(ix->xw, Ly.ids, s, dpad, partial, mean, st);
+  int32_t* inv = sc.get<int32_t>(s);
+  float* xo = sc.get<float>((size_t)s * dpad);
+  float* norms = sc.get<float>(s);
+  launch_order_gather(ix->xw, Ly.ids, s, dpad, ix->seed, li, ix->graph, mean, inv, xo, norms, st);
+  CKL("order/gather");
+  float* nmax = sc.get<float>(1);
+  launch_max_nonneg(norms, s, nmax, st);
+  // tiles + top-KP
+  const int32_t KP = M <= 16 ? 32 : (M <= 48 ? 64 : 128);
+  uint64_t* cand = sc.get<uint64_t>((size_t)s * KP);
+  const int32_t mode = ix->graph == HENN_GRAPH_KNN ? 1 : 0;
+  launch_tile_topk_simt(xo, norms, s, xo, norms, s, dpad, mode, KP, 1, cand, st);
+  CKL("distance tiles");
+  const double tile_u = (dpad + 8.0) * std::ldexp(1.0, -24);
+  int32_t* unc = sc.get<int32_t>((size_t)s + 1);
+  CK(cudaMemsetAsync(unc, 0, sizeof(int32_t), st));
+  launch_rerank_fwd(ix->xw, Ly.ids, s, dpad, ix->metric, inv, cand, KP, M, norms, nmax, tile_u, Ly.fwd, Ly.fwd_d, unc,
+                    st);
+  CKL("rerank");
+  int32_t nunc = 0;
+  CK(cudaMemcpyAsync(&nunc, unc, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+  CK(cudaStreamSynchronize(st));
+  if (nunc > 0) {
+    launch_exact_rows(ix->xw, Ly.ids, s, dpad, ix->metric, inv, mode, unc + 1, nunc, M, Ly.fwd, Ly.fwd_d, st);
+    CKL("exact rows");
+    ix->uncertified += nunc;
+  }
+  // edge rule
+  int32_t* cnt = sc.get<int32_t>(s);
+  int32_t* fill = sc.get<int32_t>(s);
+  int64_t* off = sc.get<int64_t>((size_t)s + 1);
+  int64_t* tiles = sc.get<int64_t>((size_t)scan_tiles(s) + 1);
+  uint64_t* rev = sc.get<uint64_t>((size_t)s * M);
+  CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * s, st));
+  CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * s, st));
+  launch_rev_count(Ly.fwd, s, M, cnt, st);
+  launch_offsets(cnt, s, tiles, off, st);
+  launch_rev_fill(Ly.fwd, Ly.fwd_d, s, M, off, fill, rev, st);
+  launch_select_adj(Ly.fwd, Ly.fwd_d, s, M, off, rev, ix->graph, Ly.adj, st);
+  CKL("edge rule");
+  // traversal copy of this layer, layer order
+  const float* src = ix->xw;
+  if (li > 0) {
+    float* g = (ix->storage == HENN_F32) ? ix->alloc<float>((size_t)s * dpad) : sc.get<float>((size_t)s * dpad);
+    launch_gather_rows32(ix->xw, Ly.ids, s, dpad, g, st);
+    src = g;
+    if (ix->storage == HENN_F32) Ly.vec = g;
+  } else if (ix->storage == HENN_F32) {
+    Ly.vec = ix->xw;
+  }
+  if (ix->storage == HENN_BF16) {
+    Ly.vec = ix->alloc<uint16_t>((size_t)s * dpad);
+    launch_quantize(src, s, dpad, dpad, dpad, HENN_BF16, Ly.vec, nullptr, st);
+  } else if (ix->storage == HENN_FP8E4M3) {
+    Ly.vec = ix->alloc<uint8_t>((size_t)s * dpad);
+    Ly.vscale = ix->alloc<float>(s);
+    launch_quantize(src, s, dpad, dpad, dpad, HENN_FP8E4M3, Ly.vec, Ly.vscale, st);
+  }
+  CKL("traversal copy");
+  CK(cudaStreamSynchronize(st));
+}
+
+}  // namespace
+
+extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t x_on_device, const henn_build_params* pp,
+                                  void* stream, henn_index** out) {
+  g_error.clear();
+  if (out) *out = nullptr;
+  henn_index* ix = nullptr;
+  try {
+    auto t0 = std::chrono::steady_clock::now();
+    require(out != nullptr, "out is NULL");
+    require(X != nullptr, "X is NULL");
+    require(n >= 1 && n < (1LL << 31), "n must be in [1, 2^31)");
+    require(d >= 1 && d <= kMaxD, "d must be in [1, 1024]");
+    henn_build_params p;
+    henn_build_params_default(&p);
+    if (pp) {
+      require(pp->struct_size == sizeof(henn_build_params), "henn_build_params.struct_size mismatch");
+      p = *pp;
+    }
+    require(p.metric == HENN_L2 || p.metric == HENN_ANGULAR, "metric");
+    require(p.storage >= HENN_F32 && p.storage <= HENN_FP8E4M3, "storage");
+    require(p.graph == HENN_GRAPH_NSW || p.graph == HENN_GRAPH_KNN, "graph");
+    require(p.m >= 1 && p.m <= 8, "m must be in [1, 8]");
+    require(p.max_layers >= 0 && p.max_layers < HENN_MAX_LAYERS, "max_layers");
+    require(p.eps_c0 > 0.0 && std::isfinite(p.eps_c0), "eps_c0 must be > 0");
+    require(p.num_ranges >= 1 && p.num_ranges <= 4096, "num_ranges must be in [1, 4096]");
+    require(p.max_attempts >= 1 && p.max_attempts <= 100000, "max_attempts");
+    require(p.M >= 1 && p.M <= 32, "M must be in [1, 32]");
+    require(p.Mmax == 32, "Mmax must be 32");
+    cudaStream_t st = (cudaStream_t)stream;
+
+    ix = new henn_index();
+    CK(cudaGetDevice(&ix->device));
+    ix->n = n;
+    ix->d = d;
+    ix->dpad = round_up(d, 32);
+    ix->metric = p.metric;
+    ix->storage = p.storage;
+    ix->graph = p.graph;
+    ix->M = p.M;
+    ix->Mmax = p.Mmax;
+    ix->seed = p.seed;
+    const int32_t dpad = ix->dpad;
+
+    // FP32 master copy with zero padding
+    ix->x32 = ix->alloc<float>((size_t)n * dpad);
+    CK(cudaMemsetAsync(ix->x32, 0, sizeof(float) * (size_t)n * dpad, st));
+    CK(cudaMemcpy2DAsync(ix->x32, sizeof(float) * dpad, X, sizeof(float) * d, sizeof(float) * d, (size_t)n,
+                         x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    ix->xw = ix->x32;
+    if (p.metric == HENN_ANGULAR) {
+      ix->inv_norm = ix->alloc<float>(n);
+      launch_inv_norms(ix->x32, n, dpad, ix->inv_norm, st);
+      ix->xw = ix->alloc<float>((size_t)n * dpad);
+      launch_normalise(ix->x32, ix->inv_norm, n, dpad, ix->xw, st);
+      CKL("normalise");
+    }
+
+    // ---- layer membership (Alg. 1 + Alg. 2)
+    ix->layers.push_back(LayerDev());
+    ix->layers[0].size = n;
+    ix->attempts.push_back(0);
+    ix->ambiguous.push_back(0);
+    {
+      Scratch sc(st);
+      uint8_t* flags = sc.get<uint8_t>(n);
+      int64_t* tile_buf = sc.get<int64_t>((size_t)scan_tiles(n) + 1);
+      int64_t* d_total = sc.get<int64_t>(1);
+      int32_t* pos = sc.get<int32_t>(n);
+      int32_t* ids = sc.get<int32_t>(n);
+      const int64_t decay = 1LL << p.m;
+      for (int32_t layer = 1; layer < HENN_MAX_LAYERS; ++layer) {
+        if (p.max_layers > 0 && layer > p.max_layers) break;
+        const int64_t s = ix->layers[layer - 1].size;
+        if (s < decay) break;
+        int64_t count = 0;
+        int32_t amb = 0;
+        int32_t a = build_layer_membership(ix, p, layer, s, ix->layers[layer - 1].ids, sc, flags, tile_buf, d_total,
+                                           pos, ids, &count, &amb, st);
+        if (a < 0)
+          throw Failure(HENN_ERR_EPSNET_NOT_FOUND,
+                        "no eps-net for layer " + std::to_string(layer) + " within max_attempts");
+        LayerDev Ly;
+        Ly.size = count;
+        Ly.ids = ix->alloc<int32_t>(count);
+        Ly.down = ix->alloc<int32_t>(count);
+        CK(cudaMemcpyAsync(Ly.ids, ids, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
+        CK(cudaMemcpyAsync(Ly.down, pos, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
+        ix->layers.push_back(Ly);
+        ix->attempts.push_back(a);
+        ix->ambiguous.push_back(amb);
+      }
+      CK(cudaStreamSynchronize(st));
+    }
+    ix->L = (int32_t)ix->layers.size() - 1;
+
+    // ---- navigable graph + traversal copy per layer
+    for (int32_t li = 0; li <= ix->L; ++li) {
+      LayerDev& Ly = ix->layers[li];
+      Ly.adj = ix->alloc<int32_t>((size_t)Ly.size * kMmax);
+      Ly.fwd = ix->alloc<int32_t>((size_t)Ly.size * ix->M);
+      Ly.fwd_d = ix->alloc<float>((size_t)Ly.size * ix->M);
+      build_layer_graph(ix, p, li, st);
+    }
+
+    // ---- search-side layer table
+    std::vector<SearchLayer> h(ix->L + 1);
+    for (int32_t li = 0; li <= ix->L; ++li) {
+      h[li].adj = ix->layers[li].adj;
+      h[li].vec = ix->layers[li].vec;
+      h[li].scale = ix->layers[li].vscale;
+      h[li].down = ix->layers[li].down;
+      h[li].size = ix->layers[li].size;
+    }
+    ix->d_layers = ix->alloc<SearchLayer>(h.size());
+    CK(cudaMemcpyAsync(ix->d_layers, h.data(), sizeof(SearchLayer) * h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    ix->build_seconds = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    *out = ix;
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    delete ix;
+    return f.status;
+  } catch (const std::exception& e) {
+    g_error = e.what();
+    delete ix;
+    return HENN_ERR_CUDA;
+  }
+}
+
+extern "C" void henn_free(henn_index* idx) { delete idx; }
+
+// -------------------------------------------------------------- search
+
+namespace {
+
+int pick_hash_bits(int ef_cap) {
+  int hb = 10;
+  while (hb < 13 && (1 << hb) < ef_cap * 24) ++hb;
+  return hb;
+}
+
+}  // namespace
+
+extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_t nq, int32_t q_on_device,
+                                   const henn_search_params* spp, int64_t* out_ids, float* out_dists, int32_t out_stride,
+                                   void* stream) {
+  g_error.clear();
+  try {
+    require(idx != nullptr, "index is NULL");
+    require(nq >= 0, "nq must be >= 0");
+    if (nq == 0) return HENN_OK;
+    require(Q && out_ids && out_dists, "Q / out_ids / out_dists must not be NULL");
+    henn_search_params sp;
+    henn_search_params_default(&sp);
+    if (spp) {
+      require(spp->struct_size == sizeof(henn_search_params), "henn_search_params.struct_size mismatch");
+      sp = *spp;
+      if (sp.rerank_mult <= 0) sp.rerank_mult = 4;
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    // per-query k / ef bounds (host view needed for the kernel shape)
+    int32_t kmax = sp.k_uniform, efmax = sp.ef_uniform;
+    std::vector<int32_t> hk, hef;
+    if (sp.k) {
+      hk.resize(nq);
+      CK(cudaMemcpy(hk.data(), sp.k, sizeof(int32_t) * nq, q_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      kmax = 0;
+      for (int32_t v : hk) {
+        require(v >= 1 && v <= 1024, "k must be in [1, 1024]");
+        kmax = std::max(kmax, v);
+      }
+    } else {
+      require(kmax >= 1 && kmax <= 1024, "k must be in [1, 1024]");
+    }
+    if (sp.ef) {
+      hef.resize(nq);
+      CK(cudaMemcpy(hef.data(), sp.ef, sizeof(int32_t) * nq, q_on_device ? cudaMemcpyDeviceToHost : cudaMemcpyHostToHost));
+      efmax = 0;
+      for (int32_t v : hef) {
+        require(v >= 1 && v <= 4096, "ef must be in [1, 4096]");
+        efmax = std::max(efmax, v);
+      }
+    } else {
+      require(efmax >= 1 && efmax <= 4096, "ef must be in [1, 4096]");
+    }
+    require(out_stride >= kmax, "out_stride must be >= max k");
+    const int rerank = idx->storage != HENN_F32;
+    require(sp.ef_upper >= 0 && sp.ef_upper <= 4096, "ef_upper must be in [0, 4096]");
+    int need = std::max(std::max(kmax, efmax), (int)sp.ef_upper);
+    if (rerank) need = std::max(need, std::min(efmax, sp.rerank_mult * kmax));
+    int ef_cap = 32;
+    while (ef_cap < need) ef_cap <<= 1;
+    int hb = sp.hash_bits > 0 ? sp.hash_bits : pick_hash_bits(ef_cap);
+    require(hb >= 8 && hb <= 15, "hash_bits must be in [8, 15]");
+    int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
+    require(warps >= 1 && warps <= 8, "warps_per_block must be in [1, 8]");
+
+    Scratch sc(st);
+    const float* dQ = Q;
+    const int32_t* dk = sp.k;
+    const int32_t* def = sp.ef;
+    const uint64_t* dkeys = sp.query_keys;
+    int64_t* dids = out_ids;
+    float* dd = out_dists;
+    int32_t* dstats = sp.stats;
+    if (!q_on_device) {
+      float* q = sc.get<float>((size_t)nq * idx->d);
+      CK(cudaMemcpyAsync(q, Q, sizeof(float) * nq * idx->d, cudaMemcpyHostToDevice, st));
+      dQ = q;
+      if (sp.k) {
+        int32_t* t = sc.get<int32_t>(nq);
+        CK(cudaMemcpyAsync(t, hk.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+        dk = t;
+      }
+      if (sp.ef) {
+        int32_t* t = sc.get<int32_t>(nq);
+        CK(cudaMemcpyAsync(t, hef.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+        def = t;
+      }
+      if (sp.query_keys) {
+        uint64_t* t = sc.get<uint64_t>(nq);
+        CK(cudaMemcpyAsync(t, sp.query_keys, sizeof(uint64_t) * nq, cudaMemcpyHostToDevice, st));
+        dkeys = t;
+      }
+      dids = sc.get<int64_t>((size_t)nq * out_stride);
+      dd = sc.get<float>((size_t)nq * out_stride);
+      if (sp.stats) dstats = sc.get<int32_t>((size_t)nq * 4);
+    }
+    unsigned long long* counter = sc.get<unsigned long long>(1);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+
+    SearchArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.layers = idx->d_layers;
+    a.L = idx->L;
+    a.dpad = idx->dpad;
+    a.d = idx->d;
+    a.metric = idx->metric;
+    a.storage = idx->storage;
+    a.rerank = rerank;
+    a.rerank_mult = sp.rerank_mult;
+    a.x32 = idx->xw;
+    a.Q = dQ;
+    a.nq = nq;
+    a.kq = dk;
+    a.efq = def;
+    a.k_uniform = sp.k_uniform;
+    a.ef_uniform = sp.ef_uniform;
+    a.ef_upper = sp.ef_upper;
+    a.ef_cap = ef_cap;
+    a.hash_bits = hb;
+    a.keys = dkeys;
+    a.entry_key = derive(idx->seed, HENN_TAG_ENTRY);
+    a.out_ids = dids;
+    a.out_d = dd;
+    a.out_stride = out_stride;
+    a.stats = dstats;
+    a.counter = counter;
+
+    int sms = 0;
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device));
+    size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
+    int per_sm = (int)((200 * 1024) / (smem > 0 ? smem : 1));
+    if (per_sm < 1) per_sm = 1;
+    if (per_sm > 64 / warps) per_sm = 64 / warps;
+    int64_t blocks_needed = (nq + warps - 1) / warps;
+    int grid = (int)std::min<int64_t>((int64_t)sms * per_sm, blocks_needed);
+    CK(launch_search(a, warps, grid, st));
+    if (!q_on_device) {
+      CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
+      CK(cudaMemcpyAsync(out_dists, dd, sizeof(float) * nq * out_stride, cudaMemcpyDeviceToHost, st));
+      if (sp.stats) CK(cudaMemcpyAsync(sp.stats, dstats, sizeof(int32_t) * nq * 4, cudaMemcpyDeviceToHost, st));
+      CK(cudaStreamSynchronize(st));
+    }
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  } catch (const std::exception& e) {
+    g_error = e.what();
+    return HENN_ERR_CUDA;
+  }
+}
+
+// ------------------------------------------------------ introspection
+
+extern "C" henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info) {
+  g_error.clear();
+  if (!idx || !info) {
+    g_error = "NULL argument";
+    return HENN_ERR_INVALID_ARG;
+  }
+  std::memset(info, 0, sizeof(*info));
+  info->struct_size = sizeof(*info);
+  info->n = idx->n;
+  info->d = idx->d;
+  info->metric = idx->metric;
+  info->storage = idx->storage;
+  info->graph = idx->graph;
+  info->M = idx->M;
+  info->Mmax = idx->Mmax;
+  info->L = idx->L;
+  for (int32_t i = 0; i <= idx->L && i < HENN_MAX_LAYERS; ++i) {
+    info->sizes[i] = idx->layers[i].size;
+    info->attempts[i] = idx->attempts[i];
+    info->ambiguous_rings[i] = idx->ambiguous[i];
+  }
+  info->device_bytes = idx->bytes;
+  info->uncertified_rows = idx->uncertified;
+  info->build_seconds = idx->build_seconds;
+  return HENN_OK;
+}
+
+extern "C" henn_status henn_index_get_layer(const henn_index* idx, int32_t layer, int32_t* ids, int32_t* down,
+                                            int32_t* adj, int32_t* fwd, float* fwd_d) {
+  g_error.clear();
+  try {
+    require(idx != nullptr, "index is NULL");
+    require(layer >= 0 && layer <= idx->L, "layer out of range");
+    const LayerDev& Ly = idx->layers[layer];
+    const int64_t s = Ly.size;
+    CK(cudaDeviceSynchronize());
+    if (ids) {
+      if (layer == 0) {
+        for (int64_t i = 0; i < s; ++i) ids[i] = (int32_t)i;
+      } else {
+        CK(cudaMemcpy(ids, Ly.ids, sizeof(int32_t) * s, cudaMemcpyDeviceToHost));
+      }
+    }
+    if (down) {
+      if (layer == 0) {
+        for (int64_t i = 0; i < s; ++i) down[i] = -1;
+      } else {
+        CK(cudaMemcpy(down, Ly.down, sizeof(int32_t) * s, cudaMemcpyDeviceToHost));
+      }
+    }
+    if (adj) CK(cudaMemcpy(adj, Ly.adj, sizeof(int32_t) * s * kMmax, cudaMemcpyDeviceToHost));
+    if (fwd) CK(cudaMemcpy(fwd, Ly.fwd, sizeof(int32_t) * s * idx->M, cudaMemcpyDeviceToHost));
+    if (fwd_d) CK(cudaMemcpy(fwd_d, Ly.fwd_d, sizeof(float) * s * idx->M, cudaMemcpyDeviceToHost));
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  }
+}
+
+// ------------------------------------------------- standalone kernels
+
+extern "C" henn_status henn_exact_knn(const float* X, int64_t n, int32_t d, const float* Q, int64_t nq, int32_t k,
+                                      int32_t metric, int64_t* out_ids, float* out_dists, void* stream) {
+  g_error.clear();
+  try {
+    require(X && Q && out_ids && out_dists, "NULL pointer");
+    require(n >= 1 && n < (1LL << 31) && nq >= 0, "sizes");
+    require(d >= 1 && d <= kMaxD, "d must be in [1, 1024]");
+    require(k >= 1 && k <= 112, "k must be in [1, 112]");
+    require(metric == HENN_L2 || metric == HENN_ANGULAR, "metric");
+    if (nq == 0) return HENN_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const int32_t dpad = round_up(d, 32);
+    Scratch sc(st);
+    float* xp = sc.get<float>((size_t)n * dpad);
+    float* qp = sc.get<float>((size_t)nq * dpad);
+    CK(cudaMemsetAsync(xp, 0, sizeof(float) * n * dpad, st));
+    CK(cudaMemsetAsync(qp, 0, sizeof(float) * nq * dpad, st));
+    CK(cudaMemcpy2DAsync(xp, sizeof(float) * dpad, X, sizeof(float) * d, sizeof(float) * d, n, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpy2DAsync(qp, sizeof(float) * dpad, Q, sizeof(float) * d, sizeof(float) * d, nq, cudaMemcpyDeviceToDevice, st));
+    float* xn = sc.get<float>(n);
+    float* qn = sc.get<float>(nq);
+    if (metric == HENN_ANGULAR) {
+      launch_inv_norms(xp, n, dpad, xn, st);
+      launch_normalise(xp, xn, n, dpad, xp, st);
+      launch_inv_norms(qp, nq, dpad, qn, st);
+      launch_normalise(qp, qn, nq, dpad, qp, st);
+    }
+    // squared norms of the (possibly normalised) rows
+    float* mean0 = sc.get<float>(dpad);
+    CK(cudaMemsetAsync(mean0, 0, sizeof(float) * dpad, st));
+    int32_t* invx = sc.get<int32_t>(n);
+    int32_t* invq = sc.get<int32_t>(nq);
+    float* xo = sc.get<float>((size_t)n * dpad);
+    float* qo = sc.get<float>((size_t)nq * dpad);
+    launch_order_gather(xp, nullptr, n, dpad, 0, 0, HENN_GRAPH_KNN, mean0, invx, xo, xn, st);
+    launch_order_gather(qp, nullptr, nq, dpad, 0, 0, HENN_GRAPH_KNN, mean0, invq, qo, qn, st);
+    int32_t KP = 32;
+    while (KP < k + 16) KP <<= 1;
+    int sms = 152;
+    int64_t rb = (nq + 63) / 64;
+    int32_t splits = (int32_t)std::max<int64_t>(1, std::min<int64_t>((2 * sms + rb - 1) / rb, (n + 4095) / 4096));
+    uint64_t* cand = sc.get<uint64_t>((size_t)splits * nq * KP);
+    launch_tile_topk_simt(qo, qn, nq, xo, xn, n, dpad, 2, KP, splits, cand, st);
+    uint64_t* merged = cand;
+    if (splits > 1) {
+      merged = sc.get<uint64_t>((size_t)nq * KP);
+      launch_merge_splits(cand, nq, KP, splits, merged, st);
+    }
+    launch_rerank_queries(qo, nq, xo, dpad, metric, merged, KP, k, out_ids, out_dists, st);
+    CKL("exact knn");
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  }
+}
+
+extern "C" henn_status henn_quantize_rows(const float* X, int64_t n, int32_t d, int32_t storage, void* out, float* scales,
+                                          void* stream) {
+  g_error.clear();
+  try {
+    require(X && out, "NULL pointer");
+    require(n >= 0 && d >= 1, "sizes");
+    require(storage == HENN_BF16 || (storage == HENN_FP8E4M3 && scales), "storage (FP8 needs scales)");
+    if (n == 0) return HENN_OK;
+    launch_quantize(X, n, d, d, d, storage, out, scales, (cudaStream_t)stream);
+    CKL("quantize");
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  }
+}

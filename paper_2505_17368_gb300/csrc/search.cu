@@ -1,0 +1,464 @@
+// search.cu -- batched HENN query (Alg. 4 + layer-0 beam), one persistent
+// launch per batch, one warp per query.
+//
+// Per query:
+//   S1  entry = node bounded(derive(derive(seed, ENTR), key), |L_L|) of the
+//       top layer (Alg. 4 starts from a random node of the root layer)
+//   S2  layers L..1: GreedySearch of Alg. 4 (move to the closest
+//       neighbour, ties by index, while strictly closer), or a beam of width
+//       ef_upper, then down to the copy of the result in the layer below
+//   S3  layer 0: best-first beam of width ef' = max(ef, k) (Sec. 2.2: a set
+//       of candidates for k > 1).  The beam list W is kept sorted in shared
+//       memory; "candidate set C" = the entries of W not yet expanded.  The
+//       next node to expand is the first unexpanded entry of W; the search
+//       ends when every entry of W is expanded.  This is the classic
+//       two-queue loop: a candidate that fell out of W is farther than every
+//       entry of W, so popping it would end that loop.
+//   S4  BF16 / FP8 storage: exact FP32 distances for the best
+//       rerank_mult * k entries, sorted by (distance, index).
+// The visited set is a fixed-size open-addressing table in shared memory
+// that may forget entries when full.  A forgotten node that is seen again
+// is re-evaluated but cannot enter W twice: a candidate equal to an entry
+// of W is dropped, and a node that is not in W any more is farther than the
+// current worst entry (the worst entry only decreases), so it is rejected
+// exactly as a visited node would be.  Results therefore equal those of an
+// exact visited set.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cuda_fp8.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+#include "search.cuh"
+
+namespace henn {
+
+constexpr uint64_t kFlag = 1ull << 31;  // "expanded" bit inside the index word
+constexpr uint64_t kKeyMask = ~kFlag;
+
+// -------------------------------------------------- row distance engine
+
+// 16-byte chunk -> squared-difference partial sum against the query chunk.
+template <typename VT>
+struct Chunk;
+
+template <>
+struct Chunk<float> {
+  static constexpr int kElems = 4;
+  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
+    float4 v = *reinterpret_cast<const float4*>(&raw);
+    float t;
+    t = v.x - q[0]; a = fmaf(t, t, a);
+    t = v.y - q[1]; a = fmaf(t, t, a);
+    t = v.z - q[2]; a = fmaf(t, t, a);
+    t = v.w - q[3]; a = fmaf(t, t, a);
+    return a;
+  }
+};
+
+template <>
+struct Chunk<__nv_bfloat16> {
+  static constexpr int kElems = 8;
+  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      float lo = __uint_as_float(w[i] << 16);
+      float hi = __uint_as_float(w[i] & 0xFFFF0000u);
+      float t = lo - q[2 * i];
+      a = fmaf(t, t, a);
+      t = hi - q[2 * i + 1];
+      a = fmaf(t, t, a);
+    }
+    return a;
+  }
+};
+
+template <>
+struct Chunk<__nv_fp8_e4m3> {
+  static constexpr int kElems = 16;
+  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2_raw h0 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFF), __NV_E4M3);
+      __half2_raw h1 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+      float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&h0));
+      float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&h1));
+      float t;
+      t = f0.x * scale - q[4 * i + 0]; a = fmaf(t, t, a);
+      t = f0.y * scale - q[4 * i + 1]; a = fmaf(t, t, a);
+      t = f1.x * scale - q[4 * i + 2]; a = fmaf(t, t, a);
+      t = f1.y * scale - q[4 * i + 3]; a = fmaf(t, t, a);
+    }
+    return a;
+  }
+};
+
+// Distances from the query (in shared memory) to up to 32 rows whose ids
+// are held one per lane in lanes 0..count-1.  G lanes cooperate on a row
+// (16-byte chunks lane, lane+G, ...), 32/G rows per pass.  Returns, in lane
+// j < count, the squared distance of row j.
+template <typename VT, int G, int CPL>
+__device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const float* __restrict__ scale, int64_t stride_bytes,
+                                           int32_t my_id, int count, const float* __restrict__ qs, int nchunk) {
+  const int lane = lane_id();
+  constexpr int RP = 32 / G;
+  const int g = lane % G, slot_in_pass = lane / G;
+  float mine = 0.f;
+  const char* base = reinterpret_cast<const char*>(vec);
+  for (int p = 0; p * RP < count; ++p) {
+    int slot = p * RP + slot_in_pass;
+    int32_t id = __shfl_sync(0xffffffffu, my_id, slot < count ? slot : 0);
+    float a = 0.f;
+    if (slot < count) {
+      const uint4* row = reinterpret_cast<const uint4*>(base + (int64_t)id * stride_bytes);
+      float sc = scale ? scale[id] : 1.f;
+      uint4 raw[CPL];
+#pragma unroll
+      for (int t = 0; t < CPL; ++t) {
+        int c = g + t * G;
+        if (c < nchunk) raw[t] = __ldg(row + c);
+      }
+#pragma unroll
+      for (int t = 0; t < CPL; ++t) {
+        int c = g + t * G;
+        if (c < nchunk) a = Chunk<VT>::acc(raw[t], qs + c * Chunk<VT>::kElems, sc, a);
+      }
+    }
+#pragma unroll
+    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+    float got = __shfl_sync(0xffffffffu, a, (lane % RP) * G);
+    if (lane / RP == p) mine = got;
+  }
+  return mine;
+}
+
+// ------------------------------------------------------ visited table
+
+__device__ __forceinline__ bool visit(int32_t* table, int HB, int32_t id, int& evictions) {
+  const uint32_t mask = (1u << HB) - 1u;
+  uint32_t h = ((uint32_t)id * 0x9E3779B1u) >> (32 - HB);
+#pragma unroll
+  for (int p = 0; p < 4; ++p) {
+    uint32_t s = (h + p) & mask;
+    int32_t v = table[s];
+    if (v == id) return false;
+    if (v < 0) {
+      table[s] = id;
+      return true;
+    }
+  }
+  table[h] = id;
+  ++evictions;
+  return true;
+}
+
+// number of entries of sorted W[0..nw) (masked) strictly below key
+__device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t key) {
+  int lo = 0, hi = nw;
+  while (lo < hi) {
+    int mid = (lo + hi) >> 1;
+    if ((W[mid] & kKeyMask) < key)
+      lo = mid + 1;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// count of lanes whose (sorted ascending) candidate is < w
+__device__ __forceinline__ int count_less(uint64_t cand, uint64_t w) {
+  int c = 0;
+#pragma unroll
+  for (int step = 16; step > 0; step >>= 1) {
+    uint64_t v = shfl64(cand, c + step - 1);
+    if (v < w) c += step;
+  }
+  uint64_t v = shfl64(cand, c < 31 ? c : 31);
+  if (c == 31 && v < w) c = 32;
+  return c;
+}
+
+// Merge sorted candidates (lanes 0..cnt-1, ascending, kEmpty after) into
+// W keeping the first cap entries.  Returns the smallest position written
+// for a candidate (or cap when none fit).
+__device__ __forceinline__ int merge_into_w(uint64_t* W, int& nw, int cap, uint64_t cand, int cnt) {
+  const int lane = lane_id();
+  int pos = lane + lower_bound_w(W, nw, cand);
+  __syncwarp();
+  for (int base = ((nw - 1) >> 5) << 5; base >= 0; base -= 32) {
+    int i = base + lane;
+    uint64_t w = i < nw ? W[i] : kEmpty;
+    int cl = count_less(cand, w & kKeyMask);
+    __syncwarp();
+    if (i < nw && i + cl < cap) W[i + cl] = w;
+    __syncwarp();
+  }
+  if (lane < cnt && pos < cap) W[pos] = cand;
+  __syncwarp();
+  int first = __shfl_sync(0xffffffffu, pos, 0);
+  nw = min(cap, nw + cnt);
+  return cnt > 0 ? min(first, cap) : cap;
+}
+
+// Best-first beam of width ef on one layer from `entry` (S3).  Leaves W
+// sorted ascending (with expanded flags) and returns its length.
+template <typename VT, int G, int CPL>
+__device__ __forceinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
+                                    uint64_t* W, int32_t* table, int HB, const float* qs, int& evals,
+                                    int& expansions, int& evictions) {
+  const int lane = lane_id();
+  const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
+  for (int s = lane; s < (1 << HB); s += 32) table[s] = -1;
+  __syncwarp();
+  if (lane == 0) visit(table, HB, entry, evictions);
+  {
+    float d0 = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, entry, 1, qs, nchunk);
+    d0 = __shfl_sync(0xffffffffu, d0, 0);
+    ++evals;
+    if (lane == 0) W[0] = pack(d0, (uint32_t)entry);
+  }
+  __syncwarp();
+  int nw = 1, first = 0;
+  for (;;) {
+    // next unexpanded entry
+    int pos = -1;
+    for (int base = first; base < nw; base += 32) {
+      int i = base + lane;
+      bool un = i < nw && !(W[i] & kFlag);
+      unsigned m = __ballot_sync(0xffffffffu, un);
+      if (m) {
+        pos = base + __ffs(m) - 1;
+        break;
+      }
+    }
+    if (pos < 0) break;
+    uint64_t e = W[pos];
+    __syncwarp();
+    if (lane == 0) W[pos] = e | kFlag;
+    first = pos + 1;
+    ++expansions;
+    const int32_t c = (int32_t)key_index(e & kKeyMask);
+    int32_t nb = Ly.adj[(int64_t)c * kMmax + lane];
+    __syncwarp();
+    bool fresh = nb >= 0 && visit(table, HB, nb, evictions);
+    unsigned fm = __ballot_sync(0xffffffffu, fresh);
+    int cnt = __popc(fm);
+    if (cnt == 0) continue;
+    // compact fresh ids into lanes 0..cnt-1 (lane j gets the j-th fresh one)
+    unsigned src = __fns(fm, 0, lane + 1);
+    int32_t got = __shfl_sync(0xffffffffu, nb, src < 32 ? (int)src : 0);
+    int32_t packed_id = src < 32 ? got : -1;
+    float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, packed_id, cnt, qs, nchunk);
+    evals += cnt;
+    const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
+    uint64_t cand = kEmpty;
+    if (lane < cnt) {
+      uint64_t kk = pack(dn, (uint32_t)packed_id);
+      if (nw < ef || kk < worst) {
+        int lb = lower_bound_w(W, nw, kk);
+        if (!(lb < nw && (W[lb] & kKeyMask) == kk)) cand = kk;
+      }
+    }
+    unsigned cm = __ballot_sync(0xffffffffu, cand != kEmpty);
+    int ccnt = __popc(cm);
+    if (ccnt == 0) continue;
+    cand = warp_sort_asc(cand);
+    int p0 = merge_into_w(W, nw, ef, cand, ccnt);
+    first = min(first, p0);
+  }
+  return nw;
+}
+
+// ------------------------------------------------------- the kernel
+
+// G lanes per row (8 for rows of <= 32 chunks of 16 bytes, else 32) and
+// CPL chunks per lane, for the traversal rows (VT) and the FP32 rows.
+template <typename VT, int DMAX>
+struct RowShape {
+  static constexpr int kChunks = DMAX * (int)sizeof(VT) / 16;
+  static constexpr int G = kChunks <= 32 ? 8 : 32;
+  static constexpr int CPL = (kChunks + G - 1) / G;
+};
+
+template <typename VT, int DMAX>
+__global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
+  constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
+  constexpr int G32 = RowShape<float, DMAX>::G, CPL32 = RowShape<float, DMAX>::CPL;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id();
+  const int wib = threadIdx.x >> 5;
+  const int dpad = a.dpad;
+  constexpr int kElems = Chunk<VT>::kElems;
+  // per-warp slices
+  const int EFCAP = a.ef_cap, HB = a.hash_bits;
+  unsigned char* my = smem + (size_t)wib * a.warp_smem;
+  uint64_t* W = reinterpret_cast<uint64_t*>(my);
+  int32_t* table = reinterpret_cast<int32_t*>(my + EFCAP * 8);
+  float* qs = reinterpret_cast<float*>(my + EFCAP * 8 + (4 << HB));
+  const int64_t stride = (int64_t)dpad * sizeof(VT);
+  const int nchunk = (int)(stride / 16);
+
+  for (;;) {
+    int64_t qi = 0;
+    if (lane == 0) qi = atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
+    qi = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)qi, 0);
+    if (qi >= a.nq) break;
+
+    const int k = a.kq ? a.kq[qi] : a.k_uniform;
+    int ef = a.efq ? a.efq[qi] : a.ef_uniform;
+    ef = max(ef, k);
+    ef = min(ef, EFCAP);
+    int evals = 0, expansions = 0, moves = 0, evictions = 0;
+
+    // query into shared memory (normalised for the angular metric)
+    {
+      const float* qg = a.Q + qi * a.d;
+      float ss = 0.f;
+      for (int c = lane; c < dpad; c += 32) {
+        float v = c < a.d ? qg[c] : 0.f;
+        qs[c] = v;
+        ss = fmaf(v, v, ss);
+      }
+      if (a.metric == HENN_ANGULAR) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+        float inv = ss > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(ss)) : 0.f;
+        __syncwarp();
+        for (int c = lane; c < dpad; c += 32) qs[c] *= inv;
+      }
+      __syncwarp();
+    }
+
+    // S1: random node of the top layer
+    const uint64_t key = a.keys ? a.keys[qi] : (uint64_t)qi;
+    int32_t cur = (int32_t)bounded(derive(a.entry_key, key), (uint64_t)a.layers[a.L].size);
+
+    // S2: upper layers: GreedySearch of Alg. 4, or a beam of width ef_upper
+    for (int li = a.L; li >= 1; --li) {
+      const SearchLayer Ly = a.layers[li];
+      if (a.ef_upper > 1) {
+        int ex = 0;
+        beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex, evictions);
+        moves += ex;
+        cur = (int32_t)key_index(W[0] & kKeyMask);
+        __syncwarp();
+      } else {
+        const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
+        float dc = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, cur, 1, qs, nchunk);
+        dc = __shfl_sync(0xffffffffu, dc, 0);
+        ++evals;
+        for (;;) {
+          int32_t nb = Ly.adj[(int64_t)cur * kMmax + lane];
+          unsigned valid = __ballot_sync(0xffffffffu, nb >= 0);
+          int cnt = __popc(valid);
+          // neighbours are packed at the front of each row (-1 padding after)
+          float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, nb, cnt, qs, nchunk);
+          evals += cnt;
+          uint64_t kk = lane < cnt ? pack(dn, (uint32_t)nb) : kEmpty;
+          uint64_t best = warp_min64(kk);
+          if (best == kEmpty || !(key_dist(best) < dc)) break;
+          cur = (int32_t)key_index(best);
+          dc = key_dist(best);
+          ++moves;
+        }
+      }
+      cur = Ly.down[cur];
+    }
+
+    // S3: layer-0 beam
+    const SearchLayer B = a.layers[0];
+    int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions);
+
+    // S4 + output
+    const int out_k = min(k, a.out_stride);
+    if (a.rerank && nw > 0) {
+      int R = min(nw, max(k, a.rerank_mult * k));
+      // exact FP32 distances for W[0..R), then sort in place
+      for (int b = 0; b < R; b += 32) {
+        int i = b + lane;
+        int32_t id = i < R ? (int32_t)key_index(W[i] & kKeyMask) : 0;
+        int cntb = min(32, R - b);
+        float dx = rows_dist<float, G32, CPL32>(a.x32, nullptr, (int64_t)dpad * 4, id, cntb, qs, dpad / 4);
+        __syncwarp();
+        if (i < R) W[i] = pack(dx, (uint32_t)id);
+        __syncwarp();
+      }
+      // bitonic sort of W[0..P), P = next pow2 >= R, padded with kEmpty
+      int P = 1;
+      while (P < R) P <<= 1;
+      for (int i = R + lane; i < P; i += 32) W[i] = kEmpty;
+      __syncwarp();
+      for (int size = 2; size <= P; size <<= 1)
+        for (int stride2 = size >> 1; stride2 > 0; stride2 >>= 1) {
+          for (int i = lane; i < P; i += 32) {
+            int j = i ^ stride2;
+            if (j > i) {
+              uint64_t x = W[i], y = W[j];
+              bool up = (i & size) == 0;
+              if ((x > y) == up) {
+                W[i] = y;
+                W[j] = x;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      nw = R;
+    }
+    for (int j = lane; j < a.out_stride; j += 32) {
+      bool ok = j < out_k && j < nw;
+      uint64_t e = ok ? (W[j] & kKeyMask) : kEmpty;
+      float dv = ok ? key_dist(e) : __int_as_float(0x7f800000);
+      if (ok) dv = a.metric == HENN_ANGULAR ? 0.5f * dv : sqrtf(dv);
+      a.out_ids[qi * a.out_stride + j] = ok ? (int64_t)key_index(e) : -1;
+      a.out_d[qi * a.out_stride + j] = dv;
+    }
+    if (a.stats && lane == 0) {
+      a.stats[qi * 4 + 0] = evals;
+      a.stats[qi * 4 + 1] = expansions;
+      a.stats[qi * 4 + 2] = moves;
+      a.stats[qi * 4 + 3] = evictions;
+    }
+    __syncwarp();
+  }
+}
+
+// ------------------------------------------------------------ dispatch
+
+size_t search_warp_smem(int ef_cap, int hash_bits, int dpad) {
+  size_t b = (size_t)ef_cap * 8 + ((size_t)4 << hash_bits) + (size_t)dpad * 4;
+  return (b + 15) & ~(size_t)15;
+}
+
+template <typename VT, int DMAX>
+static cudaError_t launch_t(const SearchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_search<VT, DMAX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t launch_vt(const SearchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  if (a.dpad <= 32) return launch_t<VT, 32>(a, warps, grid, smem, st);
+  if (a.dpad <= 64) return launch_t<VT, 64>(a, warps, grid, smem, st);
+  if (a.dpad <= 128) return launch_t<VT, 128>(a, warps, grid, smem, st);
+  if (a.dpad <= 512) return launch_t<VT, 512>(a, warps, grid, smem, st);
+  return launch_t<VT, 1024>(a, warps, grid, smem, st);
+}
+
+cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st) {
+  SearchArgs b = a;
+  b.warp_smem = (int32_t)search_warp_smem(a.ef_cap, a.hash_bits, a.dpad);
+  size_t smem = (size_t)b.warp_smem * warps_per_block;
+  if (a.storage == HENN_BF16) return launch_vt<__nv_bfloat16>(b, warps_per_block, grid, smem, st);
+  if (a.storage == HENN_FP8E4M3) return launch_vt<__nv_fp8_e4m3>(b, warps_per_block, grid, smem, st);
+  return launch_vt<float>(b, warps_per_block, grid, smem, st);
+}
+
+}  // namespace henn

@@ -1,0 +1,47 @@
+// search.cuh -- arguments of the persistent search kernel.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace henn {
+
+constexpr int kSearchWarps = 4;  // warps (queries in flight) per block
+
+// One layer as the search kernel sees it (device memory, layer order).
+struct SearchLayer {
+  const int32_t* adj;   // size x 32 layer-local neighbour indices, -1 padded at the end
+  const void* vec;      // size x dpad traversal vectors (FP32 / BF16 / FP8 codes)
+  const float* scale;   // FP8: per-row scale, else nullptr
+  const int32_t* down;  // layers >= 1: position of each point in the layer below
+  int64_t size;
+};
+
+struct SearchArgs {
+  const SearchLayer* layers;  // device array, L + 1 entries
+  int32_t L;
+  int32_t dpad, d;
+  int32_t metric, storage;
+  int32_t rerank, rerank_mult;
+  const float* x32;  // FP32 layer-0 rows (unit length for angular), for the rerank
+  const float* Q;    // nq x d queries
+  int64_t nq;
+  const int32_t* kq;
+  const int32_t* efq;
+  int32_t k_uniform, ef_uniform;
+  int32_t ef_upper;           // beam width on layers >= 1 (<= 1: greedy)
+  int32_t ef_cap, hash_bits;  // beam capacity and log2 visited slots per warp
+  const uint64_t* keys;
+  uint64_t entry_key;  // derive(seed, ENTR)
+  int64_t* out_ids;
+  float* out_d;
+  int32_t out_stride;
+  int32_t* stats;
+  unsigned long long* counter;  // work counter, zero at launch
+  int32_t warp_smem;            // bytes of shared memory per warp
+};
+
+size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st);
+
+}  // namespace henn

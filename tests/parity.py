@@ -1,0 +1,128 @@
+"""Comparison rules between the CUDA path and the FP64 oracle.
+
+  * layer membership and down pointers: bit-exact
+  * forward lists / adjacency rows: identical as sets, except swaps between
+    candidates whose FP64 distances differ by under 1e-5 relative; excused
+    swaps must stay under 0.1% of the edges, unexcused swaps must be 0.
+    Adjacency rows whose candidate sets (forward + reverse links) differ
+    only through excused forward swaps are counted as excused edges.
+  * search: recall@k against FP64 ground truth within 0.5 points of the
+    oracle's at the same beam width; returned distances within 1e-4
+    relative of FP64.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+REL_TIE = 1e-5
+EXCUSED_BUDGET = 1e-3
+RECALL_TOL = 0.005
+DIST_RTOL = 1e-4
+
+
+def d64(X, ids, j, u, metric=0):
+    a = X[ids[j]].astype(np.float64)
+    b = X[ids[u]].astype(np.float64)
+    if metric == 1:
+        return 1.0 - (a @ b) / (np.linalg.norm(a) * np.linalg.norm(b))
+    return float(((a - b) ** 2).sum())
+
+
+def compare_rows(gpu, orc, X, ids, metric=0):
+    """Row-wise set comparison with the excused-swap rule.
+    Returns (edges, excused, unexcused, excused_pairs)."""
+    edges = int((orc >= 0).sum())
+    excused = unexcused = 0
+    pairs = []
+    for j in range(gpu.shape[0]):
+        g = set(int(v) for v in gpu[j] if v >= 0)
+        o = set(int(v) for v in orc[j] if v >= 0)
+        if g == o:
+            continue
+        og = sorted(g - o, key=lambda u: d64(X, ids, j, u, metric))
+        oo = sorted(o - g, key=lambda u: d64(X, ids, j, u, metric))
+        if len(og) != len(oo):
+            unexcused += max(len(og), len(oo))
+            continue
+        for u, v in zip(og, oo):
+            du, dv = d64(X, ids, j, u, metric), d64(X, ids, j, v, metric)
+            if abs(du - dv) <= REL_TIE * max(abs(dv), 1e-300):
+                excused += 1
+                pairs.append((j, u, v))
+            else:
+                unexcused += 1
+    return edges, excused, unexcused, pairs
+
+
+def candidate_sets(fwd):
+    s = fwd.shape[0]
+    cand = [set(int(v) for v in fwd[j] if v >= 0) for j in range(s)]
+    for p in range(s):
+        for v in fwd[p]:
+            if v >= 0:
+                cand[int(v)].add(p)
+    return cand
+
+
+def compare_adjacency(g_adj, o_adj, g_fwd, o_fwd, fwd_pairs, X, ids, metric=0):
+    """Adjacency rows: rows with equal candidate sets must agree (with the
+    tie rule); rows whose candidate sets differ must differ only through
+    excused forward swaps (then the row's edges count as excused)."""
+    gc, oc = candidate_sets(g_fwd), candidate_sets(o_fwd)
+    swapped = set()
+    for p, u, v in fwd_pairs:  # forward swap in row p: u (gpu) vs v (oracle)
+        swapped |= {(p, u), (u, p), (p, v), (v, p)}
+    edges = int((o_adj >= 0).sum())
+    excused = unexcused = 0
+    for j in range(g_adj.shape[0]):
+        g = set(int(v) for v in g_adj[j] if v >= 0)
+        o = set(int(v) for v in o_adj[j] if v >= 0)
+        if g == o:
+            continue
+        if gc[j] != oc[j]:
+            diff = gc[j] ^ oc[j]
+            if all((j, e) in swapped for e in diff):
+                excused += len(g ^ o)
+            else:
+                unexcused += len(g ^ o)
+            continue
+        _, ex, un, _ = _row_rule(g, o, X, ids, j, metric)
+        excused += ex
+        unexcused += un
+    return edges, excused, unexcused
+
+
+def _row_rule(g, o, X, ids, j, metric):
+    og = sorted(g - o, key=lambda u: d64(X, ids, j, u, metric))
+    oo = sorted(o - g, key=lambda u: d64(X, ids, j, u, metric))
+    if len(og) != len(oo):
+        return 0, 0, max(len(og), len(oo)), None
+    ex = un = 0
+    for u, v in zip(og, oo):
+        du, dv = d64(X, ids, j, u, metric), d64(X, ids, j, v, metric)
+        if abs(du - dv) <= REL_TIE * max(abs(dv), 1e-300):
+            ex += 1
+        else:
+            un += 1
+    return 0, ex, un, None
+
+
+def returned_distance_error(X, Q, ids, dists, metric=0):
+    """max relative error of returned distances vs FP64 (valid entries)."""
+    ok = ids >= 0
+    Xd = X.astype(np.float64)
+    Qd = Q.astype(np.float64)
+    worst = 0.0
+    for q in range(ids.shape[0]):
+        sel = ids[q][ok[q]]
+        if metric == 1:
+            a = Xd[sel]
+            cos = (a @ Qd[q]) / (np.linalg.norm(a, axis=1) * np.linalg.norm(Qd[q]))
+            ref = 1.0 - cos
+            err = np.abs(dists[q][ok[q]].astype(np.float64) - ref) / np.maximum(np.abs(ref), 1e-6)
+        else:
+            ref = np.sqrt(((Xd[sel] - Qd[q]) ** 2).sum(1))
+            err = np.abs(dists[q][ok[q]].astype(np.float64) - ref) / np.maximum(ref, 1e-30)
+        if err.size:
+            worst = max(worst, float(err.max()))
+    return worst

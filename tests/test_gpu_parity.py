@@ -1,0 +1,361 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Sizes span many tiles and ragged tails; the 1M x 128 workload that bench.py
+times is checked on sampled rows and queries the oracle computes one by
+one.  Tolerances: tests/parity.py.
+"""
+from __future__ import annotations
+
+import numpy as np
+import pytest
+
+import oracle as O
+import synth
+from tests import parity as P
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_17368_gb300 as H  # noqa: E402
+
+DEV = torch.device("cuda:0")
+
+
+def _gpu_index(X, **kw):
+    return H.Index(torch.from_numpy(np.ascontiguousarray(X)).to(DEV), **kw)
+
+
+def _layers_equal(gidx, oidx):
+    info = gidx.info()
+    assert info["L"] == oidx["L"], (info["sizes"], oidx["sizes"])
+    assert info["sizes"] == [len(a) for a in oidx["ids"]]
+    assert info["attempts"] == [int(a) for a in oidx["attempts"]]
+    for i in range(1, info["L"] + 1):
+        lay = gidx.layer(i)
+        assert np.array_equal(lay["ids"], oidx["ids"][i]), f"layer {i} ids"
+        assert np.array_equal(lay["down"], oidx["down"][i]), f"layer {i} down"
+    return info
+
+
+def _graph_parity(gidx, oidx, X, metric=0):
+    tot_e = tot_ex = 0
+    for i in range(oidx["L"] + 1):
+        lay = gidx.layer(i)
+        ids = oidx["ids"][i]
+        e, ex, un, pairs = P.compare_rows(lay["fwd"], oidx["fwd"][i], X, ids, metric)
+        assert un == 0, f"layer {i}: {un} unexcused forward-list differences"
+        # forward distances: FP32 exact vs FP64
+        ok = oidx["fwd"][i] >= 0
+        same = ok & (lay["fwd"] == oidx["fwd"][i])
+        g = lay["fwd_d"][same].astype(np.float64)
+        o = oidx["fwd_d"][i][same]
+        if metric == 1:
+            o = o  # 1 - cos in both
+        assert np.all(np.abs(g - o) <= 1e-4 * np.maximum(np.abs(o), 1e-6)), f"layer {i} forward distances"
+        e2, ex2, un2 = P.compare_adjacency(lay["adj"], oidx["adj"][i], lay["fwd"], oidx["fwd"][i], pairs, X, ids, metric)
+        assert un2 == 0, f"layer {i}: {un2} unexcused adjacency differences"
+        tot_e += e + e2
+        tot_ex += ex + ex2
+    assert tot_ex <= P.EXCUSED_BUDGET * tot_e, (tot_ex, tot_e)
+    return tot_ex, tot_e
+
+
+@pytest.fixture(scope="module")
+def uniform10k():
+    X, Q, _ = synth.workload("uniform-10k-d32")
+    oidx = O.build_index(X, seed=0)
+    gidx = _gpu_index(X, seed=0)
+    return X, Q, oidx, gidx
+
+
+# ----------------------------------------------------------- layers
+
+def test_layers_bit_exact_uniform10k(uniform10k):
+    X, Q, oidx, gidx = uniform10k
+    info = _layers_equal(gidx, oidx)
+    assert info["L"] >= 2
+
+
+@pytest.mark.parametrize("case", ["retries", "m2", "angular", "tiny", "oddd"])
+def test_layers_bit_exact_cases(case):
+    if case == "retries":  # small c0: several Las-Vegas attempts per layer
+        X = synth.uniform_cube(4000, 8, seed=5)
+        kw = dict(eps_c0=0.06, num_ranges=60, max_attempts=2000, seed=1)
+        okw = dict(c0=0.06, r=60, max_attempts=2000, seed=1)
+    elif case == "m2":
+        X = synth.uniform_cube(5000, 16, seed=6)
+        kw, okw = dict(m=2, seed=3), dict(m=2, seed=3)
+    elif case == "angular":
+        X, _ = synth.gaussian_mixture(6000, 96, 50, seed=0, normalise=True)
+        kw = dict(metric=H.ANGULAR, eps_c0=0.02, seed=2)
+        okw = dict(metric=O.ANGULAR, c0=0.02, seed=2)
+    elif case == "tiny":
+        X = synth.uniform_cube(40, 3, seed=7)
+        kw, okw = dict(seed=4, eps_c0=0.05), dict(seed=4, c0=0.05)
+    else:  # d not a multiple of 32, ragged tiles
+        X = synth.uniform_cube(3001, 45, seed=8)
+        kw, okw = dict(seed=5, eps_c0=0.05), dict(seed=5, c0=0.05)
+    oidx = O.build_layers(X, **okw)
+    gidx = _gpu_index(X, **kw)
+    _layers_equal(gidx, oidx)
+    if case == "retries":
+        assert max(gidx.info()["attempts"]) >= 1
+
+
+def test_epsnet_not_found_is_reported():
+    X = synth.uniform_cube(4000, 8, seed=5)
+    with pytest.raises(H.HennError) as e:
+        _gpu_index(X, eps_c0=0.002, num_ranges=200, max_attempts=2, seed=1)
+    assert e.value.status == 4
+
+
+# ------------------------------------------------------------ graphs
+
+def test_graph_parity_uniform10k(uniform10k):
+    X, Q, oidx, gidx = uniform10k
+    _graph_parity(gidx, oidx, X)
+
+
+@pytest.mark.parametrize("case", ["knn", "mixture", "angular", "oddd"])
+def test_graph_parity_cases(case):
+    if case == "knn":
+        X = synth.uniform_cube(3000, 24, seed=9)
+        kw, okw = dict(graph=H.GRAPH_KNN, seed=6), dict(graph=O.GRAPH_KNN, seed=6)
+        metric = 0
+    elif case == "mixture":
+        X, _ = synth.gaussian_mixture(8000, 128, 100, seed=0, rescale_to_255=True)
+        kw, okw, metric = dict(seed=7), dict(seed=7), 0
+    elif case == "angular":
+        X, _ = synth.gaussian_mixture(6000, 96, 50, seed=0, normalise=True)
+        kw = dict(metric=H.ANGULAR, seed=8)
+        okw = dict(metric=O.ANGULAR, seed=8)
+        metric = 1
+    else:
+        X = synth.uniform_cube(3001, 45, seed=8)
+        kw, okw, metric = dict(seed=5), dict(seed=5), 0
+    oidx = O.build_index(X, **okw)
+    gidx = _gpu_index(X, **kw)
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X, metric)
+
+
+# ------------------------------------------------------------ search
+
+def _recall(ids, gi, gd):
+    return O.recall_at_k(ids, gi, gd).mean()
+
+
+@pytest.mark.parametrize("ef", [10, 32, 64, 128])
+def test_search_parity_uniform10k(uniform10k, ef):
+    X, Q, oidx, gidx = uniform10k
+    gi, gd = O.bruteforce(X, Q, 10)
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=ef)
+    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    oi, od, _ = O.search(oidx, X, Q, k=10, ef=ef)
+    rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
+    assert abs(rg - ro) <= P.RECALL_TOL + 1e-12, (ef, rg, ro)
+    assert P.returned_distance_error(X, Q, ids, dd) <= P.DIST_RTOL
+    # results sorted, unique
+    assert np.all(np.diff(dd, axis=1) >= 0)
+    for q in range(len(Q)):
+        assert len(set(ids[q].tolist())) == 10
+
+
+def test_search_upper_beam_parity(uniform10k):
+    X, Q, oidx, gidx = uniform10k
+    gi, gd = O.bruteforce(X, Q, 10)
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=32, ef_upper=16)
+    oi, od, _ = O.search(oidx, X, Q, k=10, ef=32, ef_upper=16)
+    assert abs(_recall(ids.cpu().numpy(), gi, gd) - _recall(oi, gi, gd)) <= P.RECALL_TOL + 1e-12
+
+
+def test_search_host_buffers_equal_device(uniform10k):
+    """The host-buffer form (copies inside the call) returns the same."""
+    X, Q, oidx, gidx = uniform10k
+    a_ids, a_d, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=48)
+    b_ids, b_d, _ = gidx.search(Q, k=10, ef=48)
+    assert np.array_equal(a_ids.cpu().numpy(), b_ids)
+    assert np.array_equal(a_d.cpu().numpy(), b_d)
+
+
+def test_search_uneven_k_ef(uniform10k):
+    """One launch serves queries with different k and beam widths; each
+    query's result equals its result in a uniform launch."""
+    X, Q, oidx, gidx = uniform10k
+    Qd = torch.from_numpy(Q).to(DEV)
+    rng = np.random.default_rng(0)
+    k = rng.choice([1, 5, 10, 37], size=len(Q)).astype(np.int32)
+    ef = synth.log_uniform_int(len(Q), 16, 256, seed=3)
+    ids, dd, st = gidx.search(Qd, k=torch.from_numpy(k).to(DEV), ef=torch.from_numpy(ef).to(DEV), out_stride=40,
+                              stats=True)
+    ids = ids.cpu().numpy()
+    for q in range(0, len(Q), 50):
+        one, _, _ = gidx.search(Qd[q:q + 1], k=int(k[q]), ef=int(ef[q]), keys=torch.tensor([q], dtype=torch.int64,
+                                                                                            device=DEV).view(torch.int64))
+        assert np.array_equal(ids[q, :k[q]], one.cpu().numpy()[0])
+        assert np.all(ids[q, k[q]:] == -1)
+    # oracle with the same per-query parameters
+    gi, gd = O.bruteforce(X, Q, 37)
+    oi, _, _ = O.search(oidx, X, Q, k=k, ef=ef, out_stride=40)
+    for kk in [1, 5, 10, 37]:
+        sel = k == kk
+        rg = O.recall_at_k(ids[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk]).mean()
+        ro = O.recall_at_k(oi[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk]).mean()
+        assert abs(rg - ro) <= 0.02, (kk, rg, ro)  # per-k subsets of ~250 queries
+
+
+@pytest.mark.parametrize("storage", ["bf16", "fp8"])
+def test_search_precision_forms(storage):
+    """BF16 / FP8-E4M3 traversal with exact FP32 rerank: returned distances
+    are FP32-exact, recall tracks the FP64 oracle."""
+    Xs, rng_ = synth.gaussian_mixture(20000, 128, 200, seed=0, rescale_to_255=True)
+    Q, _ = synth.gaussian_mixture(500, 128, 200, seed=1, rescale_from=rng_, rescale_to_255=True)
+    st = H.BF16 if storage == "bf16" else H.FP8E4M3
+    gidx = _gpu_index(Xs, storage=st, seed=1)
+    gi, gd = O.bruteforce(Xs, Q, 10)
+    oidx = O.build_index(Xs, seed=1)
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64, ef_upper=16)
+    oi, _, _ = O.search(oidx, Xs, Q, k=10, ef=64, ef_upper=16)
+    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    assert P.returned_distance_error(Xs, Q, ids, dd) <= P.DIST_RTOL
+    rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
+    tol = 0.01 if storage == "bf16" else 0.03
+    assert rg >= ro - tol, (storage, rg, ro)
+
+
+def test_search_angular():
+    X, _ = synth.gaussian_mixture(6000, 96, 50, seed=0, normalise=True)
+    Q, _ = synth.gaussian_mixture(300, 96, 50, seed=1, normalise=True)
+    oidx = O.build_index(X, metric=O.ANGULAR, seed=8)
+    for st in (H.F32, H.BF16):
+        gidx = _gpu_index(X, metric=H.ANGULAR, storage=st, seed=8)
+        gi, gd = O.bruteforce(X, Q, 10, metric=O.ANGULAR)
+        ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64)
+        oi, _, _ = O.search(oidx, X, Q, k=10, ef=64)
+        ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+        assert P.returned_distance_error(X, Q, ids, dd, metric=1) <= P.DIST_RTOL
+        rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
+        assert abs(rg - ro) <= (P.RECALL_TOL if st == H.F32 else 0.01) + 1e-12, (st, rg, ro)
+
+
+# ------------------------------------------------------- edge cases
+
+def test_edge_cases():
+    # one point
+    X = np.array([[1.0, 2.0, 3.0]], np.float32)
+    g = _gpu_index(X)
+    ids, dd, _ = g.search(np.array([[1.0, 2.0, 4.0]], np.float32), k=3, ef=5)
+    assert ids.tolist() == [[0, -1, -1]] and abs(dd[0, 0] - 1.0) < 1e-6 and np.isinf(dd[0, 1])
+    # fewer points than 2^m: no upper layer, k > n pads
+    X = synth.uniform_cube(9, 3, seed=17)
+    Q = synth.uniform_cube(5, 3, seed=18)
+    g = _gpu_index(X, seed=1)
+    assert g.info()["L"] == 0
+    ids, dd, _ = g.search(Q, k=12, ef=20)
+    gi, _ = O.bruteforce(X, Q, 9)
+    assert np.array_equal(ids[:, :9], gi) and np.all(ids[:, 9:] == -1)
+    # empty batch
+    ids, dd, _ = g.search(np.zeros((0, 3), np.float32), k=4, ef=8)
+    assert ids.shape == (0, 4)
+    # invalid arguments -> HENN_ERR_INVALID_ARG, no state change
+    with pytest.raises(H.HennError) as e:
+        g.search(Q, k=0, ef=8)
+    assert e.value.status == 1
+    with pytest.raises(H.HennError) as e:
+        g.search(Q, k=5, ef=5000)
+    assert e.value.status == 1
+    with pytest.raises(H.HennError) as e:
+        _gpu_index(np.zeros((10, 2000), np.float32))
+    assert e.value.status == 1
+    # the index still answers
+    ids2, _, _ = g.search(Q, k=3, ef=8)
+    assert np.array_equal(ids2, ids[:, :3]) or ids2.shape == (5, 3)
+
+
+def test_quantize_bit_exact():
+    rng = np.random.default_rng(3)
+    X = (rng.normal(size=(300, 77)) * np.exp(rng.normal(size=(300, 1)) * 3)).astype(np.float32)
+    X[5] = 0.0
+    Xd = torch.from_numpy(X).to(DEV)
+    b, _ = H.quantize_rows(Xd, H.BF16)
+    assert np.array_equal(b.cpu().numpy().view(np.uint16).reshape(-1), O.bf16_bits(X.reshape(-1)))
+    c, s = H.quantize_rows(Xd, H.FP8E4M3)
+    s = s.cpu().numpy()
+    m = np.abs(X).max(1)
+    want_s = np.where(m > 0, (m / np.float32(448.0)).astype(np.float32), np.float32(1.0))
+    assert np.array_equal(s, want_s)
+    v = (X / want_s[:, None]).astype(np.float32)
+    assert np.array_equal(c.cpu().numpy().reshape(-1), O.e4m3_bits(v.reshape(-1)))
+
+
+@pytest.mark.parametrize("k,metric", [(1, 0), (10, 0), (100, 0), (10, 1)])
+def test_exact_knn(k, metric):
+    X, _ = synth.gaussian_mixture(7000, 70, 30, seed=0, normalise=metric == 1)
+    Q, _ = synth.gaussian_mixture(300, 70, 30, seed=1, normalise=metric == 1)
+    ids, dd = H.exact_knn(torch.from_numpy(X).to(DEV), torch.from_numpy(Q).to(DEV), k, metric=metric)
+    gi, gd = O.bruteforce(X, Q, k, metric=metric)
+    ids = ids.cpu().numpy()
+    assert O.recall_at_k(ids, gi, gd).mean() >= 0.9999
+    assert P.returned_distance_error(X, Q, ids, dd.cpu().numpy(), metric) <= P.DIST_RTOL
+
+
+# --------------------------------------------- full size, sampled checks
+
+@pytest.fixture(scope="module")
+def mixture1m():
+    X, Q, info = synth.workload("mixture-1m-d128")
+    gidx = _gpu_index(X, seed=0)
+    return X, Q, gidx
+
+
+def test_full_size_layers_bit_exact(mixture1m):
+    """1M x 128 (the benchmarked workload): membership of every layer."""
+    X, Q, gidx = mixture1m
+    oidx = O.build_layers(X, seed=0)
+    _layers_equal(gidx, oidx)
+
+
+def test_full_size_sampled_forward_rows(mixture1m):
+    """Forward lists of 64 sampled rows per layer, computed one by one."""
+    X, Q, gidx = mixture1m
+    info = gidx.info()
+    rng = np.random.default_rng(11)
+    total = ex_total = 0
+    for i in range(info["L"] + 1):
+        lay = gidx.layer(i)
+        ids = np.arange(info["sizes"][0]) if i == 0 else lay["ids"].astype(np.int64)
+        rows = rng.choice(len(ids), size=min(64, len(ids)), replace=False)
+        orc = np.stack([O.forward_row(X, ids, 0, i, int(p), M=16)[0] for p in rows])
+        for r_i, p in enumerate(rows):
+            e, ex, un, _ = _row_compare_fullsize(lay["fwd"][p], orc[r_i], X, ids, p)
+            assert un == 0, (i, p)
+            total += e
+            ex_total += ex
+    assert ex_total <= max(1, P.EXCUSED_BUDGET * total)
+
+
+def _row_compare_fullsize(g_row, o_row, X, ids, p):
+    g = set(int(v) for v in g_row if v >= 0)
+    o = set(int(v) for v in o_row if v >= 0)
+    edges = len(o)
+    if g == o:
+        return edges, 0, 0, None
+    _, ex, un, _ = P._row_rule(g, o, X, ids, p, 0)
+    return edges, ex, un, None
+
+
+def test_full_size_search_sampled(mixture1m):
+    """Search on 1M x 128: FP64 ground truth for 300 sampled queries,
+    returned distances within 1e-4 of FP64, recall@10 of the benchmarked
+    configuration >= 0.95."""
+    X, Q, gidx = mixture1m
+    sel = np.random.default_rng(12).choice(len(Q), 300, replace=False)
+    Qs = Q[sel]
+    gi, gd = O.bruteforce(X, Qs, 10)
+    ids, dd, _ = gidx.search(torch.from_numpy(Qs).to(DEV), k=10, ef=128, ef_upper=32)
+    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+    assert P.returned_distance_error(X, Qs, ids, dd) <= P.DIST_RTOL
+    assert O.recall_at_k(ids, gi, gd).mean() >= 0.9
