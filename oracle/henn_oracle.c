@@ -196,13 +196,21 @@ int32_t ho_verify(const float* X, int32_t d, int32_t metric, const int64_t* prev
   } else {
     uint64_t bc = ho_derive(ho_derive(ho_derive(seed, HO_TAG_RCENTRE), (uint64_t)layer), (uint64_t)attempt);
     uint64_t bs = ho_derive(ho_derive(ho_derive(seed, HO_TAG_RSTART), (uint64_t)layer), (uint64_t)attempt);
-    for (int32_t q = 0; q < r; ++q) {
-      int64_t c = (int64_t)ho_bounded(ho_derive(bc, (uint64_t)q), (uint64_t)s);
-      int64_t a0 = (int64_t)ho_bounded(ho_derive(bs, (uint64_t)q), (uint64_t)(s - w + 1));
-      centre_order(X, d, metric, prev, s, c, dist, sorted);
-      int ok = ring_hit(dist, sorted, a0, w, net_pos, nnet);
-      if (ring_ok) ring_ok[q] = (uint8_t)ok;
-      if (!ok) all = 0;
+#pragma omp parallel reduction(& : all)
+    {
+      double* tdist = (double*)malloc(sizeof(double) * (size_t)s);
+      pair_t* tsorted = (pair_t*)malloc(sizeof(pair_t) * (size_t)s);
+#pragma omp for schedule(dynamic, 1)
+      for (int32_t q = 0; q < r; ++q) {
+        int64_t c = (int64_t)ho_bounded(ho_derive(bc, (uint64_t)q), (uint64_t)s);
+        int64_t a0 = (int64_t)ho_bounded(ho_derive(bs, (uint64_t)q), (uint64_t)(s - w + 1));
+        centre_order(X, d, metric, prev, s, c, tdist, tsorted);
+        int ok = ring_hit(tdist, tsorted, a0, w, net_pos, nnet);
+        if (ring_ok) ring_ok[q] = (uint8_t)ok;
+        if (!ok) all = 0;
+      }
+      free(tdist);
+      free(tsorted);
     }
   }
   free(dist);
