@@ -36,8 +36,10 @@ import synth  # noqa: E402
 
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
-EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
-EF_UPPER_SWEEP = [1, 16, 32]
+EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
+# (ef_upper, descend_all): beam width on the upper layers, and whether each
+# layer is entered at all candidates of the layer above
+UPPER_SWEEP = [(1, 0), (16, 0), (32, 0), (64, 0), (16, 1), (32, 1), (64, 1)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -156,7 +158,7 @@ def _recall(found, gt):
     return float(np.mean(hits)) / gt.shape[1]
 
 
-def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, want_events=True):
+def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0):
     import torch
 
     H = sys.modules["paper_2505_17368_gb300"]
@@ -164,7 +166,7 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, want_events=
     ids = torch.empty((nq, K), dtype=torch.int64, device=Qd.device)
     dd = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
     for _ in range(warmup):
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, stream=stream, out=(ids, dd))
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, stream=stream, out=(ids, dd))
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
@@ -173,28 +175,32 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, want_events=
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, stream=stream, out=(ids, dd))
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, stream=stream, out=(ids, dd))
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     return times, ids
 
 
-def _cpu_oracle_leg(workload_n: int, ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1):
+def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1):
     """The FP64 oracle (as it stands) on the host cores: its own index on
-    the first n_sample points of the workload stream, then the same beam
-    configuration on nq_sample queries.  Returns (qps, cores, seconds)."""
+    the first n_sample points of the workload stream (built with all
+    cores), then the same beam configuration answering nq_sample queries
+    one after another on one core (the paper's sequential-query protocol).
+    Returns (qps, cores used by the timed search, seconds per step)."""
     import oracle
 
     X, Q, _ = synth.workload(WORKLOAD, n=n_sample, nq=nq_sample)
+    oracle.set_threads(len(os.sched_getaffinity(0)))
     idx = oracle.build_index(X, seed=0)
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    oracle.set_threads(1)
     secs = []
     for _ in range(steps):
         t0 = time.perf_counter()
         oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu)
         secs.append(time.perf_counter() - t0)
-    return nq_sample / statistics.median(secs), cores, secs
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    return nq_sample / statistics.median(secs), 1, secs
 
 
 def run_reference(args):
@@ -205,9 +211,9 @@ def run_reference(args):
     n_sample, nq_sample = args.ref_n, args.ref_nq
     for _ in range(args.warmup):
         pass  # the oracle has no warm-up state; its index is built once below
-    qps, cores, secs = _cpu_oracle_leg(1_000_000, ef, efu, n_sample, nq_sample, steps=args.steps)
+    qps, cores, secs = _cpu_oracle_leg(ef, efu, n_sample, nq_sample, steps=args.steps)
     sample = (f"FP64 oracle index on the first {n_sample} of the 1M mixture points (same generator), "
-              f"{nq_sample} queries per step, ef={ef}, ef_upper={efu}, k={K}")
+              f"{nq_sample} queries per step answered sequentially on one core, ef={ef}, ef_upper={efu}, k={K}")
     line = {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
@@ -252,25 +258,27 @@ def run_ours(args):
     gt, _ = H.exact_knn(Xd, Qd, K)
     gt = gt.cpu().numpy()
     # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
-    def sweep(index):
+    def sweep(index, tag):
         best = None
-        for efu in EF_UPPER_SWEEP:
+        for efu, da in UPPER_SWEEP:
             for ef in EF_SWEEP:
-                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream)
+                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream, descend_all=da)
                 r = _recall(ids.cpu().numpy(), gt)
+                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef={ef} recall@10={r:.4f} "
+                      f"ms={1e3 * min(t):.3f}", file=sys.stderr, flush=True)
                 if r >= RECALL_TARGET:
-                    if best is None or min(t) < best[2]:
-                        best = (ef, efu, min(t), r)
+                    if best is None or min(t) < best[3]:
+                        best = (ef, efu, da, min(t), r)
                     break
         return best
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
-    chosen = sweep(idx_bf16)
-    plain = sweep(idx_f32)
+    chosen = sweep(idx_bf16, "bf16")
+    plain = sweep(idx_f32, "f32")
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, _, rec = chosen
+    ef, efu, da, _, rec = chosen
     # ---- algorithmic bytes per launch from the kernel's own counters
-    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, stats=True)
+    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, stats=True)
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
     R = min(4 * K, ef)
@@ -280,7 +288,7 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(_smi_id(dev, local)) as clk:
-        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream)
+        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -289,8 +297,8 @@ def run_ours(args):
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
     # plain FP32 comparator, same procedure
-    p_ef, p_efu, _, p_rec = plain
-    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream)
+    p_ef, p_efu, p_da, _, p_rec = plain
+    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da)
     plain_qps = args.nq / statistics.median(p_times)
     # one launch per query, FP32 (latency form), on a sample
     ns = min(200, args.nq)
@@ -298,7 +306,7 @@ def run_ours(args):
     for q in range(ns):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, stream=stream)
+        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, stream=stream)
         e1.record(stream)
         e1.synchronize()
         t_one.append(e0.elapsed_time(e1) / 1e3)
@@ -308,7 +316,7 @@ def run_ours(args):
     e2e_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, stream=stream)
+        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, stream=stream)
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
@@ -322,9 +330,11 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
+            "descend_all": da,
             "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
-            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "recall_at_10": p_rec},
+            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da,
+                          "recall_at_10": p_rec},
             "plain_f32_per_query_launch_qps": per_query_qps,
             "parallelism": f"replicas{ws}",
         },
@@ -339,11 +349,12 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        qps, cores, secs = _cpu_oracle_leg(args.n, ef, efu, args.cpu_n, args.cpu_nq)
+        qps, cores, secs = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq)
         line["cpu_baseline"] = {
             "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
-                       f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, {sum(secs):.1f} s of search"),
+                       f"{args.cpu_nq} queries answered sequentially on one core, ef={ef}, ef_upper={efu}, "
+                       f"{sum(secs):.1f} s of search"),
         }
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -381,12 +392,12 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
-    ap.add_argument("--cpu-n", type=int, default=20_000)
-    ap.add_argument("--cpu-nq", type=int, default=2_000)
-    ap.add_argument("--ref-n", type=int, default=20_000)
-    ap.add_argument("--ref-nq", type=int, default=1_000)
-    ap.add_argument("--ref-ef", type=int, default=128)
-    ap.add_argument("--ref-ef-upper", type=int, default=32)
+    ap.add_argument("--cpu-n", type=int, default=50_000)
+    ap.add_argument("--cpu-nq", type=int, default=10_000)
+    ap.add_argument("--ref-n", type=int, default=50_000)
+    ap.add_argument("--ref-nq", type=int, default=2_000)
+    ap.add_argument("--ref-ef", type=int, default=64)
+    ap.add_argument("--ref-ef-upper", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:

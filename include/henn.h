@@ -143,6 +143,9 @@ typedef struct {
   int32_t hash_bits;          /* log2 visited-set slots per query, 0 = autotuned    */
   int32_t ef_upper;           /* beam width on layers >= 1; 0 or 1 = GreedySearch of
                                  Alg. 4 (default 1)                                 */
+  int32_t descend_all;        /* with ef_upper > 1: enter each layer at the copies of
+                                 all candidates of the layer above instead of the
+                                 best one only (default 0)                          */
 } henn_search_params;
 
 void henn_search_params_default(henn_search_params* sp);

@@ -51,6 +51,8 @@ def lib():
         if _lib is None:
             _lib = C.CDLL(build())
             L = _lib
+            L.ho_set_threads.restype = None
+            L.ho_set_threads.argtypes = [C.c_int32]
             L.ho_mix64.restype = C.c_uint64
             L.ho_mix64.argtypes = [C.c_uint64]
             L.ho_derive.restype = C.c_uint64
@@ -116,6 +118,11 @@ def lib():
 
 def _f32(X):
     return np.ascontiguousarray(X, dtype=np.float32)
+
+
+def set_threads(n: int) -> None:
+    """OpenMP threads for the oracle's row / query loops."""
+    lib().ho_set_threads(int(n))
 
 
 # ----------------------------------------------------------------- RNG

@@ -45,6 +45,7 @@ extern "C" {
 #define HO_GRAPH_NSW 0
 #define HO_GRAPH_KNN 1
 
+void ho_set_threads(int32_t n);
 uint64_t ho_mix64(uint64_t z);
 uint64_t ho_derive(uint64_t h, uint64_t w);
 uint64_t ho_bounded(uint64_t u, uint64_t s);

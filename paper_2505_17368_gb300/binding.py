@@ -86,6 +86,7 @@ class SearchParams(C.Structure):
         ("warps_per_block", C.c_int32),
         ("hash_bits", C.c_int32),
         ("ef_upper", C.c_int32),
+        ("descend_all", C.c_int32),
     ]
 
 
@@ -255,7 +256,7 @@ class Index:
         return dict(ids=ids, down=down, adj=adj, fwd=fwd, fwd_d=fwd_d)
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
-               warps_per_block=0, hash_bits=0, ef_upper=1, stream=None, out=None):
+               warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, stream=None, out=None):
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
@@ -290,6 +291,7 @@ class Index:
         sp.warps_per_block = int(warps_per_block)
         sp.hash_bits = int(hash_bits)
         sp.ef_upper = int(ef_upper)
+        sp.descend_all = int(descend_all)
         if keys is not None:
             p, _, kk = _ptr(keys)
             sp.query_keys = p

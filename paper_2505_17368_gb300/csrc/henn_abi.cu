@@ -268,9 +268,30 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
   const int32_t KP = M <= 16 ? 32 : (M <= 48 ? 64 : 128);
   uint64_t* cand = sc.get<uint64_t>((size_t)s * KP);
   const int32_t mode = ix->graph == HENN_GRAPH_KNN ? 1 : 0;
-  launch_tile_topk_simt(xo, norms, s, xo, norms, s, dpad, mode, KP, 1, cand, st);
-  CKL("distance tiles");
-  const double tile_u = (dpad + 8.0) * std::ldexp(1.0, -24);
+  const bool tc_ok = tc_tiles_supported(dpad, KP);
+  if (p.tiles == HENN_TILES_TCGEN05 && !tc_ok)
+    throw Failure(HENN_ERR_UNSUPPORTED, "tcgen05 tiles need d <= 128 and M <= 16");
+  const bool use_tc = tc_ok && p.tiles == HENN_TILES_TCGEN05;
+  double tile_u;
+  if (use_tc) {
+    const int32_t dk = (dpad + 63) / 64 * 64;
+    void* hi = sc.get<uint16_t>((size_t)s * dk);
+    void* lo = sc.get<uint16_t>((size_t)s * dk);
+    int32_t* err = sc.get<int32_t>(1);
+    CK(cudaMemsetAsync(err, 0, sizeof(int32_t), st));
+    CK(launch_tile_topk_tc(xo, norms, s, dpad, mode, cand, hi, lo, err, st));
+    int32_t herr = 0;
+    CK(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    if (herr) throw Failure(HENN_ERR_TIMEOUT, "tensor-core tile pipeline wait timed out (code " + std::to_string(herr) + ")");
+    // split BF16 products (3 * 2^-18 each) plus FP32 accumulation over 3 * dk
+    // terms, doubled for non-IEEE accumulation inside the tensor core
+    tile_u = 3.0 * std::ldexp(1.0, -18) + 2.0 * (3.0 * dk + 8.0) * std::ldexp(1.0, -24);
+  } else {
+    launch_tile_topk_simt(xo, norms, s, xo, norms, s, dpad, mode, KP, 1, cand, st);
+    CKL("distance tiles");
+    tile_u = (dpad + 8.0) * std::ldexp(1.0, -24);
+  }
   int32_t* unc = sc.get<int32_t>((size_t)s + 1);
   CK(cudaMemsetAsync(unc, 0, sizeof(int32_t), st));
   launch_rerank_fwd(ix->xw, Ly.ids, s, dpad, ix->metric, inv, cand, KP, M, norms, nmax, tile_u, Ly.fwd, Ly.fwd_d, unc,
@@ -516,7 +537,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     int hb = sp.hash_bits > 0 ? sp.hash_bits : pick_hash_bits(ef_cap);
     require(hb >= 8 && hb <= 15, "hash_bits must be in [8, 15]");
     int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
-    require(warps >= 1 && warps <= 8, "warps_per_block must be in [1, 8]");
+    require(warps >= 1 && warps <= kSearchWarps, "warps_per_block must be in [1, 4]");
 
     Scratch sc(st);
     const float* dQ = Q;
@@ -570,6 +591,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.k_uniform = sp.k_uniform;
     a.ef_uniform = sp.ef_uniform;
     a.ef_upper = sp.ef_upper;
+    a.descend_all = sp.descend_all;
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.keys = dkeys;

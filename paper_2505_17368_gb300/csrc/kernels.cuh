@@ -66,6 +66,11 @@ void launch_tile_topk_simt(const float* A, const float* An, int64_t na, const fl
                            uint64_t* out, cudaStream_t st);
 void launch_merge_splits(const uint64_t* in, int64_t rows, int32_t KP, int32_t splits, uint64_t* out,
                          cudaStream_t st);
+// knn_tc.cu: the same tiles on tcgen05 tensor cores (split BF16, KP = 32,
+// dpad <= 128); scratch_hi / scratch_lo hold s * roundup(dpad, 64) BF16
+bool tc_tiles_supported(int32_t dpad, int32_t KP);
+cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, int32_t dpad, int32_t mode,
+                                uint64_t* out, void* scratch_hi, void* scratch_lo, int32_t* err, cudaStream_t st);
 // exact FP32 rerank of layer candidates -> forward lists (layer-local ids)
 void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t dpad, int32_t metric,
                        const int32_t* inv, const uint64_t* cand, int32_t KP, int32_t M, const float* norms,

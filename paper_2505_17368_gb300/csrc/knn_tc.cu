@@ -1,0 +1,429 @@
+// knn_tc.cu -- construction distance tiles on the 5th-generation tensor
+// cores (tcgen05 + TMA + TMEM), with the running top-KP per row fused into
+// the epilogue.  Same contract as the SIMT engine in knn.cu: rows and
+// columns are a layer's centred vectors in insertion order, the tile value
+// is |a|^2 + |b|^2 - 2<a,b>, column c is valid for row r iff c < r (causal,
+// NSW) or c != r (kNN graph), and every row keeps its KP smallest
+// (distance, column) keys.
+//
+// Precision: each FP32 operand is split into x = hi + lo with hi =
+// bf16(x), lo = bf16(x - hi); the tile accumulates hi.hi + lo.hi + hi.lo in
+// FP32 (kind::f16, BF16 inputs), a relative error of about 3 * 2^-18 per
+// product plus the FP32 accumulation, so the certified candidate pool of
+// the exact FP32 rerank stays small.
+//
+// Layout of one CTA (192 threads): warp 0 issues TMA loads, warp 1 owns
+// TMEM and issues the MMAs (one thread), warps 2-5 drain the accumulators
+// (TMEM lanes 32*(w%4)..+31 = rows of the 128-row block).  The A block (128
+// rows, hi and lo planes, d <= 128) stays in shared memory; B tiles (256
+// columns x 64 values of one plane) stream through a 3-stage ring.  Two
+// 256-column FP32 accumulators in TMEM let the epilogue of tile t overlap
+// the MMAs of tile t+1.  Every wait is bounded; a timeout sets an error
+// flag and the CTA releases its TMEM and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <stdint.h>
+
+#include "common.cuh"
+#include "kernels.cuh"
+
+namespace henn {
+
+namespace tc {
+
+constexpr int BM = 128;          // rows per block (TMEM lanes)
+constexpr int BN = 256;          // columns per tile (UMMA N)
+constexpr int BK = 64;           // BF16 values per 128-byte swizzle row
+constexpr int NS = 3;            // B pipeline stages
+constexpr int A_CHUNK = BM * BK * 2;  // 16 KB
+constexpr int B_CHUNK = BN * BK * 2;  // 32 KB
+constexpr int MAX_KC = 2;        // dpad <= 128: at most 2 chunks of 64 per plane
+constexpr int KP = 32;
+constexpr int S_LD = 33;
+constexpr long long kSpinLimit = 1ll << 24;
+
+struct Smem {
+  // 1024-byte aligned operand buffers first
+  uint8_t a[2 * MAX_KC][A_CHUNK];  // hi chunks then lo chunks
+  uint8_t b[NS][B_CHUNK];
+  uint64_t lists[BM][KP];          // running top-KP per row
+  float s[4][32][S_LD];            // epilogue transposition, one slab per warp
+  uint64_t full[NS], empty[NS], tfull[2], tempty[2], afull;
+  uint32_t tmem_base;
+  int abort;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false on timeout.
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+  const uint32_t addr = smem_u32(bar);
+  for (long long i = 0; i < kSpinLimit; ++i) {
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(addr), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if ((i & 1023) == 1023 && *abort_flag) return false;
+  }
+  return false;
+}
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
+          smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(smem_u32(bar)), "r"(x), "r"(y)
+      : "memory");
+}
+
+// Shared-memory matrix descriptor: K-major operand, 128-byte swizzle,
+// 8-row groups 1024 bytes apart (stride byte offset), version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void* p) {
+  uint64_t addr = smem_u32(p);
+  uint64_t d = 0;
+  d |= (addr >> 4) & 0x3FFFull;              // start address
+  d |= (uint64_t)(16 >> 4) << 16;            // leading byte offset (unused for SW128 K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;          // stride byte offset
+  d |= 1ull << 46;                           // descriptor version
+  d |= 2ull << 61;                           // SWIZZLE_128B
+  return d;
+}
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
+                            ((uint32_t)(BM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+  asm volatile(
+      "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+      " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
+      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      : "memory");
+}
+
+__device__ __forceinline__ void mma_commit(uint64_t* bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
+  uint32_t r[32];
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// One row's list in shared memory <-> warp registers (lane holds one key).
+__device__ __forceinline__ void list_insert_smem(uint64_t* row_list, uint64_t key) {
+  const int lane = lane_id();
+  uint64_t v = row_list[lane];
+  uint64_t up = __shfl_up_sync(0xffffffffu, v, 1);
+  bool dup = __any_sync(0xffffffffu, v == key);
+  if (dup) return;
+  uint64_t nv = v;
+  if (!(v < key)) nv = (lane == 0 || up < key) ? key : up;
+  row_list[lane] = nv;
+  __syncwarp();
+}
+
+}  // namespace tc
+
+using namespace tc;
+
+__global__ void __launch_bounds__(192, 1)
+    k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
+                   const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                   const float* __restrict__ norms, int64_t s, int32_t kc, int32_t mode,
+                   uint64_t* __restrict__ out, int32_t* __restrict__ err) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int64_t nrb = (s + BM - 1) / BM;
+  const int64_t rb = (mode == 0) ? (nrb - 1 - blockIdx.x) : blockIdx.x;
+  const int64_t r0 = rb * BM;
+  const int64_t cend = (mode == 0) ? min(s, r0 + BM) : s;
+  const int nt = (int)((cend + BN - 1) / BN);
+  const int chunks_per_tile = 2 * kc;  // (B_hi, B_lo) per 64-wide slice
+
+  if (threadIdx.x == 0) {
+    for (int i = 0; i < NS; ++i) {
+      tc::mbar_init(&sm.full[i], 1);
+      tc::mbar_init(&sm.empty[i], 1);
+    }
+    for (int i = 0; i < 2; ++i) {
+      tc::mbar_init(&sm.tfull[i], 1);
+      tc::mbar_init(&sm.tempty[i], 4);
+    }
+    tc::mbar_init(&sm.afull, 1);
+    sm.abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+  }
+  for (int i = threadIdx.x; i < BM * KP; i += blockDim.x) (&sm.lists[0][0])[i] = kEmpty;
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(&sm.tmem_base)));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  tc::fence_before();
+  __syncthreads();
+  tc::fence_after();
+  const uint32_t tmem = sm.tmem_base;
+  volatile int* abort_flag = &sm.abort;
+
+  if (warp == 0) {
+    // ---------------- TMA producer
+    if (lane == 0) {
+      tc::mbar_expect_tx(&sm.afull, (uint32_t)(2 * kc * A_CHUNK));
+      for (int c = 0; c < kc; ++c) {
+        tc::tma_load_2d(sm.a[c], &ta_hi, &sm.afull, c * BK, (int)r0);
+        tc::tma_load_2d(sm.a[MAX_KC + c], &ta_lo, &sm.afull, c * BK, (int)r0);
+      }
+      long long it = 0;
+      bool ok = true;
+      for (int t = 0; t < nt && ok; ++t) {
+        for (int j = 0; j < chunks_per_tile && ok; ++j, ++it) {
+          const int st = (int)(it % NS);
+          const uint32_t ph = (uint32_t)((it / NS) & 1);
+          if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::mbar_expect_tx(&sm.full[st], (uint32_t)B_CHUNK);
+          const int slice = j >> 1;
+          tc::tma_load_2d(sm.b[st], (j & 1) ? &tb_lo : &tb_hi, &sm.full[st], slice * BK, t * BN);
+        }
+      }
+      if (!ok) {
+        atomicOr(err, 1);
+        sm.abort = 1;
+      }
+    }
+  } else if (warp == 1) {
+    // ---------------- MMA issuer
+    if (lane == 0) {
+      bool ok = tc::mbar_wait(&sm.afull, 0, abort_flag);
+      long long it = 0;
+      for (int t = 0; t < nt && ok; ++t) {
+        const int as = t & 1;
+        const uint32_t aph = (uint32_t)((t >> 1) & 1);
+        if (!tc::mbar_wait(&sm.tempty[as], aph ^ 1u, abort_flag)) {
+          ok = false;
+          break;
+        }
+        tc::fence_after();
+        const uint32_t dt = tmem + (uint32_t)(as * BN);
+        uint32_t acc = 0;
+        for (int j = 0; j < chunks_per_tile; ++j, ++it) {
+          const int st = (int)(it % NS);
+          const uint32_t ph = (uint32_t)((it / NS) & 1);
+          if (!tc::mbar_wait(&sm.full[st], ph, abort_flag)) {
+            ok = false;
+            break;
+          }
+          tc::fence_after();
+          const int slice = j >> 1;
+          const bool b_is_lo = (j & 1);
+#pragma unroll
+          for (int k = 0; k < BK / 16; ++k) {
+            const uint64_t bd = tc::smem_desc(sm.b[st] + k * 32);
+            // B_hi pairs with A_hi and A_lo; B_lo pairs with A_hi
+            tc::mma_bf16(dt, tc::smem_desc(sm.a[slice] + k * 32), bd, acc);
+            acc = 1;
+            if (!b_is_lo) tc::mma_bf16(dt, tc::smem_desc(sm.a[MAX_KC + slice] + k * 32), bd, 1);
+          }
+          tc::mma_commit(&sm.empty[st]);
+        }
+        if (!ok) break;
+        tc::mma_commit(&sm.tfull[as]);
+      }
+      if (!ok) {
+        atomicOr(err, 2);
+        sm.abort = 1;
+      }
+    }
+  } else {
+    // ---------------- epilogue: warps 2..5
+    const int ew = warp - 2;
+    const int sub = warp & 3;  // TMEM sub-partition of this warp
+    const int row_l = 32 * sub + lane;
+    const int64_t grow = r0 + row_l;
+    const float nrow = grow < s ? norms[grow] : 0.f;
+    float thr = __int_as_float(0x7f800000);
+    bool ok = true;
+    for (int t = 0; t < nt; ++t) {
+      const int as = t & 1;
+      const uint32_t aph = (uint32_t)((t >> 1) & 1);
+      if (!tc::mbar_wait(&sm.tfull[as], aph, abort_flag)) {
+        ok = false;
+        break;
+      }
+      tc::fence_after();
+#pragma unroll 1
+      for (int q = 0; q < BN / 32; ++q) {
+        const int64_t c0 = (int64_t)t * BN + q * 32;
+        float v[32];
+        tc::tmem_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN + q * 32), v);
+        if (c0 >= cend) continue;  // warp-uniform
+        bool surv = false;
+#pragma unroll
+        for (int j = 0; j < 32; ++j) {
+          const int64_t col = c0 + j;
+          bool valid = grow < s && col < s;
+          if (mode == 0) valid = valid && col < grow;
+          if (mode == 1) valid = valid && col != grow;
+          float dv = __int_as_float(0x7f800000);
+          if (valid) dv = fmaxf(nrow + __ldg(norms + col) - 2.f * v[j], 0.f);
+          v[j] = dv;
+          surv |= valid && dv <= thr;
+        }
+        unsigned m = __ballot_sync(0xffffffffu, surv);
+        if (!m) continue;
+        if (surv) {
+#pragma unroll
+          for (int j = 0; j < 32; ++j) sm.s[ew][lane][j] = v[j];
+        }
+        __syncwarp();
+        while (m) {
+          const int i = __ffs(m) - 1;
+          m &= m - 1;
+          uint64_t* lst = sm.lists[32 * sub + i];
+          const float dv = sm.s[ew][i][lane];
+          const uint64_t key = isinf(dv) ? kEmpty : pack(dv, (uint32_t)(c0 + lane));
+          uint64_t worst = lst[31];
+          unsigned bm = __ballot_sync(0xffffffffu, key < worst);
+          while (bm) {
+            const int src = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const uint64_t x = shfl64(key, src);
+            if (x < worst) {
+              tc::list_insert_smem(lst, x);
+              worst = lst[31];
+            }
+          }
+          const float nthr = worst == kEmpty ? __int_as_float(0x7f800000) : key_dist(worst);
+          if (lane == i) thr = nthr;
+        }
+        __syncwarp();
+      }
+      tc::fence_before();
+      __syncwarp();
+      if (lane == 0) tc::mbar_arrive(&sm.tempty[as]);
+    }
+    if (!ok) {
+      if (lane == 0) atomicOr(err, 4);
+      sm.abort = 1;
+    }
+    // write this warp's 32 rows
+    for (int i = 0; i < 32; ++i) {
+      const int64_t gr = r0 + 32 * sub + i;
+      if (gr < s) out[gr * KP + lane] = sm.lists[32 * sub + i][lane];
+    }
+  }
+  tc::fence_before();
+  __syncthreads();
+  if (sm.abort) {
+    // let any bulk copy still in flight land before the CTA leaves
+    __nanosleep(100000);
+  }
+  if (warp == 1) {
+    tc::fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 512;" ::"r"(tmem));
+  }
+}
+
+// ------------------------------------------------------------- host side
+
+__global__ void k_split_bf16(const float* __restrict__ x, int64_t s, int32_t dpad, int32_t dk,
+                             __nv_bfloat16* __restrict__ hi, __nv_bfloat16* __restrict__ lo) {
+  const int64_t total = s * dk;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / dk;
+    const int32_t k = (int32_t)(i - r * dk);
+    const float v = k < dpad ? x[r * dpad + k] : 0.f;
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    hi[i] = h;
+    lo[i] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
+static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk, int box_rows) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)dk, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)dk * 2};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
+bool tc_tiles_supported(int32_t dpad, int32_t KPv) { return dpad <= BK * MAX_KC && KPv == KP; }
+
+size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
+
+cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, int32_t dpad, int32_t mode,
+                                uint64_t* out, void* scratch_hi, void* scratch_lo, int32_t* err, cudaStream_t st) {
+  const int32_t dk = ((dpad + BK - 1) / BK) * BK;
+  __nv_bfloat16* hi = static_cast<__nv_bfloat16*>(scratch_hi);
+  __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(scratch_lo);
+  k_split_bf16<<<152 * 8, 256, 0, st>>>(xo, s, dpad, dk, hi, lo);
+  CUtensorMap mah, mal, mbh, mbl;
+  if (!make_map(&mah, hi, s, dk, BM) || !make_map(&mal, lo, s, dk, BM) || !make_map(&mbh, hi, s, dk, BN) ||
+      !make_map(&mbl, lo, s, dk, BN))
+    return cudaErrorInvalidValue;
+  const size_t smem = tc_smem_bytes();
+  cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  const int64_t nrb = (s + BM - 1) / BM;
+  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, norms, s, dk / BK, mode, out, err);
+  return cudaGetLastError();
+}
+
+}  // namespace henn

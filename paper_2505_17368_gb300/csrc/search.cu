@@ -99,39 +99,54 @@ struct Chunk<__nv_fp8_e4m3> {
 
 // Distances from the query (in shared memory) to up to 32 rows whose ids
 // are held one per lane in lanes 0..count-1.  G lanes cooperate on a row
-// (16-byte chunks lane, lane+G, ...), 32/G rows per pass.  Returns, in lane
+// (16-byte chunks lane, lane+G, ...), 32/G rows per pass.  The loads of PB
+// passes are all issued before any arithmetic, so one neighbour list costs
+// one or two memory round trips instead of one per pass.  Returns, in lane
 // j < count, the squared distance of row j.
 template <typename VT, int G, int CPL>
 __device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const float* __restrict__ scale, int64_t stride_bytes,
                                            int32_t my_id, int count, const float* __restrict__ qs, int nchunk) {
   const int lane = lane_id();
   constexpr int RP = 32 / G;
+  constexpr int PB0 = 8 / CPL;                     // passes per batch: <= 8 chunks in flight per lane
+  constexpr int PB = PB0 < 1 ? 1 : (PB0 > 32 / RP ? 32 / RP : PB0);
   const int g = lane % G, slot_in_pass = lane / G;
   float mine = 0.f;
   const char* base = reinterpret_cast<const char*>(vec);
-  for (int p = 0; p * RP < count; ++p) {
-    int slot = p * RP + slot_in_pass;
-    int32_t id = __shfl_sync(0xffffffffu, my_id, slot < count ? slot : 0);
-    float a = 0.f;
-    if (slot < count) {
-      const uint4* row = reinterpret_cast<const uint4*>(base + (int64_t)id * stride_bytes);
-      float sc = scale ? scale[id] : 1.f;
-      uint4 raw[CPL];
+  for (int p0 = 0; p0 * RP < count; p0 += PB) {
+    uint4 raw[PB][CPL];
+    float sc[PB];
 #pragma unroll
-      for (int t = 0; t < CPL; ++t) {
-        int c = g + t * G;
-        if (c < nchunk) raw[t] = __ldg(row + c);
-      }
+    for (int pb = 0; pb < PB; ++pb) {
+      const int slot = (p0 + pb) * RP + slot_in_pass;
+      const int32_t id = __shfl_sync(0xffffffffu, my_id, slot < count ? slot : 0);
+      sc[pb] = 1.f;
+      if (slot < count) {
+        const uint4* row = reinterpret_cast<const uint4*>(base + (int64_t)id * stride_bytes);
+        if (scale) sc[pb] = __ldg(scale + id);
 #pragma unroll
-      for (int t = 0; t < CPL; ++t) {
-        int c = g + t * G;
-        if (c < nchunk) a = Chunk<VT>::acc(raw[t], qs + c * Chunk<VT>::kElems, sc, a);
+        for (int t = 0; t < CPL; ++t) {
+          const int c = g + t * G;
+          if (c < nchunk) raw[pb][t] = __ldg(row + c);
+        }
       }
     }
 #pragma unroll
-    for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
-    float got = __shfl_sync(0xffffffffu, a, (lane % RP) * G);
-    if (lane / RP == p) mine = got;
+    for (int pb = 0; pb < PB; ++pb) {
+      const int slot = (p0 + pb) * RP + slot_in_pass;
+      float a = 0.f;
+      if (slot < count) {
+#pragma unroll
+        for (int t = 0; t < CPL; ++t) {
+          const int c = g + t * G;
+          if (c < nchunk) a = Chunk<VT>::acc(raw[pb][t], qs + c * Chunk<VT>::kElems, sc[pb], a);
+        }
+      }
+#pragma unroll
+      for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
+      const float got = __shfl_sync(0xffffffffu, a, (lane % RP) * G);
+      if (lane / RP == p0 + pb) mine = got;
+    }
   }
   return mine;
 }
@@ -206,23 +221,31 @@ __device__ __forceinline__ int merge_into_w(uint64_t* W, int& nw, int cap, uint6
 
 // Best-first beam of width ef on one layer from `entry` (S3).  Leaves W
 // sorted ascending (with expanded flags) and returns its length.
+// nseed > 0: W[0..nseed) already holds sorted, unexpanded entries (the
+// copies of the layer above's candidates) and `entry` is ignored.
 template <typename VT, int G, int CPL>
-__device__ __forceinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
+__device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
                                     uint64_t* W, int32_t* table, int HB, const float* qs, int& evals,
-                                    int& expansions, int& evictions) {
+                                    int& expansions, int& evictions, int nseed = 0) {
   const int lane = lane_id();
   const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
   for (int s = lane; s < (1 << HB); s += 32) table[s] = -1;
   __syncwarp();
-  if (lane == 0) visit(table, HB, entry, evictions);
-  {
+  int nw;
+  if (nseed > 0) {
+    nw = min(nseed, ef);
+    if (lane == 0)
+      for (int j = 0; j < nw; ++j) visit(table, HB, (int32_t)key_index(W[j] & kKeyMask), evictions);
+  } else {
+    if (lane == 0) visit(table, HB, entry, evictions);
     float d0 = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, entry, 1, qs, nchunk);
     d0 = __shfl_sync(0xffffffffu, d0, 0);
     ++evals;
     if (lane == 0) W[0] = pack(d0, (uint32_t)entry);
+    nw = 1;
   }
   __syncwarp();
-  int nw = 1, first = 0;
+  int first = 0;
   for (;;) {
     // next unexpanded entry
     int pos = -1;
@@ -243,6 +266,18 @@ __device__ __forceinline__ int beam(const SearchLayer& Ly, int64_t stride, int n
     ++expansions;
     const int32_t c = (int32_t)key_index(e & kKeyMask);
     int32_t nb = Ly.adj[(int64_t)c * kMmax + lane];
+    // the next unexpanded entry is the likely next expansion: pull its
+    // adjacency line towards the SM while this one is processed
+    if (lane == 0 && pos + 1 < nw) {
+      for (int j = pos + 1; j < nw && j < pos + 8; ++j) {
+        const uint64_t f = W[j];
+        if (!(f & kFlag)) {
+          const int32_t* nxt = Ly.adj + (int64_t)key_index(f & kKeyMask) * kMmax;
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
+          break;
+        }
+      }
+    }
     __syncwarp();
     bool fresh = nb >= 0 && visit(table, HB, nb, evictions);
     unsigned fm = __ballot_sync(0xffffffffu, fresh);
@@ -285,7 +320,7 @@ struct RowShape {
 };
 
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(128, 4) k_search(const SearchArgs a) {
   constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
   constexpr int G32 = RowShape<float, DMAX>::G, CPL32 = RowShape<float, DMAX>::CPL;
   extern __shared__ __align__(16) unsigned char smem[];
@@ -338,13 +373,24 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
     int32_t cur = (int32_t)bounded(derive(a.entry_key, key), (uint64_t)a.layers[a.L].size);
 
     // S2: upper layers: GreedySearch of Alg. 4, or a beam of width ef_upper
+    int nseed = 0;
     for (int li = a.L; li >= 1; --li) {
       const SearchLayer Ly = a.layers[li];
       if (a.ef_upper > 1) {
         int ex = 0;
-        beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex, evictions);
+        int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex,
+                                  evictions, nseed);
         moves += ex;
         cur = (int32_t)key_index(W[0] & kKeyMask);
+        if (a.descend_all) {
+          // the layer below is entered at the copies of every candidate;
+          // down pointers are increasing, so the (distance, index) order holds
+          for (int j = lane; j < nw; j += 32) {
+            uint64_t e = W[j] & kKeyMask;
+            W[j] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(e)];
+          }
+          nseed = nw;
+        }
         __syncwarp();
       } else {
         const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
@@ -371,7 +417,7 @@ __global__ void __launch_bounds__(256) k_search(const SearchArgs a) {
 
     // S3: layer-0 beam
     const SearchLayer B = a.layers[0];
-    int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions);
+    int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions, nseed);
 
     // S4 + output
     const int out_k = min(k, a.out_stride);

