@@ -63,7 +63,8 @@ typedef enum {
   HENN_ERR_CUDA = 3,             /* a CUDA runtime call or kernel failed              */
   HENN_ERR_EPSNET_NOT_FOUND = 4, /* Alg. 2 found no eps-net within max_attempts       */
   HENN_ERR_TIMEOUT = 5,          /* a bounded device wait ran out                     */
-  HENN_ERR_UNSUPPORTED = 6       /* valid request this build cannot serve             */
+  HENN_ERR_UNSUPPORTED = 6,      /* valid request this build cannot serve             */
+  HENN_ERR_BUSY = 7              /* serving: no request slot or ring space right now  */
 } henn_status;
 
 typedef enum { HENN_L2 = 0, HENN_ANGULAR = 1 } henn_metric;
@@ -75,7 +76,8 @@ typedef enum { HENN_F32 = 0, HENN_BF16 = 1, HENN_FP8E4M3 = 2 } henn_storage;
 /* Navigable graph of each layer (App. C; App. F "Navigation Graphs"). */
 typedef enum { HENN_GRAPH_NSW = 0, HENN_GRAPH_KNN = 1 } henn_graph;
 
-/* Engine for the construction distance tiles. */
+/* Engine for the construction distance tiles: AUTO = tcgen05 where it
+ * applies (d <= 128, M <= 16), else SIMT FP32. */
 typedef enum { HENN_TILES_AUTO = 0, HENN_TILES_SIMT = 1, HENN_TILES_TCGEN05 = 2 } henn_tiles;
 
 /* ------------------------------------------------------------------ build */
@@ -221,6 +223,63 @@ henn_status henn_exact_knn(const float* X, int64_t n, int32_t d, const float* Q,
  */
 henn_status henn_quantize_rows(const float* X, int64_t n, int32_t d, int32_t storage, void* out,
                                float* scales, void* stream);
+
+/* ---------------------------------------------------------------- serving */
+
+/*
+ * Continuous batching (the serving loop).  A server owns one persistent
+ * kernel that answers queries from a ring of work items in HBM: requests
+ * (a batch of query rows with their own k and beam width) are admitted
+ * while their rows fit the ring and a request slot is free, published to
+ * the running kernel, and answered as warps free up, overlapping with the
+ * requests already on the device.  A query's result depends only on the
+ * query, its k, ef and key, so it is the same whatever else is in flight.
+ * Each query is answered exactly as henn_search answers it (Alg. 4 + beam).
+ *
+ * Budgets fixed at creation: ring_rows (HBM: ring_rows * (4 d + 12 max_k)
+ * bytes), max_requests slots, max_k, max_ef (the shared-memory class of the
+ * kernel: requests with a wider beam are refused).  Host memory passed to
+ * submit / poll is read / written during the call only.  Calls are
+ * thread-safe.  The kernel leaves after idle_ms without work and is
+ * relaunched by the next submit or poll.
+ */
+typedef struct {
+  uint32_t struct_size;
+  int32_t ring_rows;     /* queries in flight at most (default 65536)           */
+  int32_t max_requests;  /* request slots (default 1024)                        */
+  int32_t max_k;         /* largest k, also the result row width (default 100)  */
+  int32_t max_ef;        /* largest beam width (default 512)                    */
+  int32_t ef_upper;      /* as in henn_search_params (default 1)                */
+  int32_t descend_all;   /* as in henn_search_params (default 0)                */
+  int32_t rerank_mult;   /* as in henn_search_params (default 4)                */
+  int32_t idle_ms;       /* kernel idle exit, milliseconds (default 20)         */
+} henn_serve_params;
+
+typedef struct henn_server henn_server; /* opaque */
+
+void henn_serve_params_default(henn_serve_params* p);
+
+/* Creates a server for `idx` (which must outlive it).  Errors:
+ * HENN_ERR_INVALID_ARG, HENN_ERR_OOM, HENN_ERR_CUDA. */
+henn_status henn_serve_create(const henn_index* idx, const henn_serve_params* p, henn_server** out);
+
+/* Submits nq query rows (host, nq x d float32) with one k and ef, and
+ * optional per-query entry keys (host, NULL = request id * 2^20 + row).
+ * On success *request_id identifies the request.  HENN_ERR_BUSY when the
+ * ring or the request slots are full (poll and retry); HENN_ERR_INVALID_ARG
+ * for nq < 1, nq > ring_rows, k outside [1, max_k], ef outside [1, max_ef]. */
+henn_status henn_serve_submit(henn_server* s, const float* Q, int32_t nq, int32_t k, int32_t ef,
+                              const uint64_t* keys, int64_t* request_id);
+
+/* Non-blocking: *done = 0 while the request runs; when it has finished,
+ * *done = 1 and its results are copied to out_ids / out_dists (host, nq x
+ * k, layout as henn_search), and the request's ring rows are released.
+ * HENN_ERR_INVALID_ARG for an unknown or already collected request. */
+henn_status henn_serve_poll(henn_server* s, int64_t request_id, int32_t* done, int64_t* out_ids,
+                            float* out_dists);
+
+/* Stops the kernel (waits for it) and frees the server.  NULL is a no-op. */
+void henn_serve_destroy(henn_server* s);
 
 /* Message of the last failure on this host thread ("" if none). */
 const char* henn_last_error(void);

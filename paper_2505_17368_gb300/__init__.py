@@ -6,7 +6,7 @@ package is the Python binding.  `build()` compiles the library in tree.
 """
 from .binding import (  # noqa: F401
     ANGULAR, BF16, F32, FP8E4M3, GRAPH_KNN, GRAPH_NSW, L2, TILES_AUTO, TILES_SIMT, TILES_TCGEN05,
-    HennError, Index, exact_knn, load, quantize_rows,
+    HennError, Index, Server, exact_knn, load, quantize_rows,
 )
 
 

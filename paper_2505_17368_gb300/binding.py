@@ -33,7 +33,9 @@ STATUS = {
     4: "HENN_ERR_EPSNET_NOT_FOUND",
     5: "HENN_ERR_TIMEOUT",
     6: "HENN_ERR_UNSUPPORTED",
+    7: "HENN_ERR_BUSY",
 }
+BUSY = 7
 
 EXPORTS = [
     "henn_build_params_default",
@@ -46,6 +48,11 @@ EXPORTS = [
     "henn_exact_knn",
     "henn_quantize_rows",
     "henn_last_error",
+    "henn_serve_params_default",
+    "henn_serve_create",
+    "henn_serve_submit",
+    "henn_serve_poll",
+    "henn_serve_destroy",
 ]
 
 
@@ -87,6 +94,20 @@ class SearchParams(C.Structure):
         ("hash_bits", C.c_int32),
         ("ef_upper", C.c_int32),
         ("descend_all", C.c_int32),
+    ]
+
+
+class ServeParams(C.Structure):
+    _fields_ = [
+        ("struct_size", C.c_uint32),
+        ("ring_rows", C.c_int32),
+        ("max_requests", C.c_int32),
+        ("max_k", C.c_int32),
+        ("max_ef", C.c_int32),
+        ("ef_upper", C.c_int32),
+        ("descend_all", C.c_int32),
+        ("rerank_mult", C.c_int32),
+        ("idle_ms", C.c_int32),
     ]
 
 
@@ -145,6 +166,16 @@ def load(path: str | None = None):
         L.henn_exact_knn.restype = i32
         L.henn_quantize_rows.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         L.henn_quantize_rows.restype = i32
+        L.henn_serve_params_default.argtypes = [C.POINTER(ServeParams)]
+        L.henn_serve_params_default.restype = None
+        L.henn_serve_create.argtypes = [vp, C.POINTER(ServeParams), C.POINTER(vp)]
+        L.henn_serve_create.restype = i32
+        L.henn_serve_submit.argtypes = [vp, vp, i32, i32, i32, vp, C.POINTER(i64)]
+        L.henn_serve_submit.restype = i32
+        L.henn_serve_poll.argtypes = [vp, i64, C.POINTER(i32), vp, vp]
+        L.henn_serve_poll.restype = i32
+        L.henn_serve_destroy.argtypes = [vp]
+        L.henn_serve_destroy.restype = None
         L.henn_last_error.argtypes = []
         L.henn_last_error.restype = C.c_char_p
         _lib = L
@@ -317,6 +348,61 @@ class Index:
                              _stream(stream)))
         del keep, kq
         return ids, dists, st
+
+
+class Server:
+    """Continuous-batching server over an Index (henn_serve_*).  submit()
+    returns a request id, or None when the ring / slots are full (retry
+    after polling); poll() returns None while the request runs, else
+    (ids int64 [nq, k], dists float32 [nq, k])."""
+
+    def __init__(self, index: "Index", ring_rows=65536, max_requests=1024, max_k=100, max_ef=512, ef_upper=1,
+                 descend_all=0, rerank_mult=4, idle_ms=20):
+        L = load()
+        p = ServeParams()
+        L.henn_serve_params_default(C.byref(p))
+        p.ring_rows, p.max_requests, p.max_k, p.max_ef = ring_rows, max_requests, max_k, max_ef
+        p.ef_upper, p.descend_all, p.rerank_mult, p.idle_ms = ef_upper, descend_all, rerank_mult, idle_ms
+        h = C.c_void_p()
+        _check(L.henn_serve_create(index.handle, C.byref(p), C.byref(h)))
+        self._h = h
+        self._index = index  # the index must outlive the server
+        self._meta = {}
+
+    def submit(self, Q, k=10, ef=64, keys=None):
+        Q = np.ascontiguousarray(Q, dtype=np.float32)
+        kk = None if keys is None else np.ascontiguousarray(keys, dtype=np.uint64)
+        rid = C.c_int64()
+        st = load().henn_serve_submit(self._h, C.c_void_p(Q.ctypes.data), Q.shape[0], int(k), int(ef),
+                                      None if kk is None else C.c_void_p(kk.ctypes.data), C.byref(rid))
+        if st == BUSY:
+            return None
+        _check(st)
+        self._meta[rid.value] = (Q.shape[0], int(k))
+        return rid.value
+
+    def poll(self, rid):
+        nq, k = self._meta[rid]
+        ids = np.empty((nq, k), np.int64)
+        dd = np.empty((nq, k), np.float32)
+        done = C.c_int32()
+        _check(load().henn_serve_poll(self._h, int(rid), C.byref(done), C.c_void_p(ids.ctypes.data),
+                                      C.c_void_p(dd.ctypes.data)))
+        if not done.value:
+            return None
+        del self._meta[rid]
+        return ids, dd
+
+    def close(self):
+        if getattr(self, "_h", None) is not None and self._h.value:
+            load().henn_serve_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def exact_knn(X, Q, k, metric=L2, stream=None):

@@ -12,7 +12,9 @@
 #include <chrono>
 #include <cmath>
 #include <cstring>
+#include <deque>
 #include <exception>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -271,7 +273,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
   const bool tc_ok = tc_tiles_supported(dpad, KP);
   if (p.tiles == HENN_TILES_TCGEN05 && !tc_ok)
     throw Failure(HENN_ERR_UNSUPPORTED, "tcgen05 tiles need d <= 128 and M <= 16");
-  const bool use_tc = tc_ok && p.tiles == HENN_TILES_TCGEN05;
+  const bool use_tc = tc_ok && p.tiles != HENN_TILES_SIMT;
   double tile_u;
   if (use_tc) {
     const int32_t dk = (dpad + 63) / 64 * 64;
@@ -477,10 +479,40 @@ extern "C" void henn_free(henn_index* idx) { delete idx; }
 
 namespace {
 
+// Visited-table slots per query: about 16 per beam entry (a beam of ef
+// visits roughly 10 new nodes per expansion); the table may forget entries
+// without changing results, so it is sized for occupancy, not for
+// completeness.
 int pick_hash_bits(int ef_cap) {
   int hb = 10;
-  while (hb < 13 && (1 << hb) < ef_cap * 24) ++hb;
+  while (hb < 13 && (1 << hb) < ef_cap * 16) ++hb;
   return hb;
+}
+
+}  // namespace
+
+namespace {
+
+void fill_search_args(const henn_index* idx, SearchArgs& a) {
+  std::memset(&a, 0, sizeof(a));
+  a.layers = idx->d_layers;
+  a.L = idx->L;
+  a.dpad = idx->dpad;
+  a.d = idx->d;
+  a.metric = idx->metric;
+  a.storage = idx->storage;
+  a.rerank = idx->storage != HENN_F32;
+  a.x32 = idx->xw;
+  a.entry_key = derive(idx->seed, HENN_TAG_ENTRY);
+}
+
+int persistent_grid(int device, int warps, size_t smem) {
+  int sms = 0;
+  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
+  int per_sm = (int)((200 * 1024) / (smem > 0 ? smem : 1));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 64 / warps) per_sm = 64 / warps;
+  return sms * per_sm;
 }
 
 }  // namespace
@@ -574,16 +606,8 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
 
     SearchArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.layers = idx->d_layers;
-    a.L = idx->L;
-    a.dpad = idx->dpad;
-    a.d = idx->d;
-    a.metric = idx->metric;
-    a.storage = idx->storage;
-    a.rerank = rerank;
+    fill_search_args(idx, a);
     a.rerank_mult = sp.rerank_mult;
-    a.x32 = idx->xw;
     a.Q = dQ;
     a.nq = nq;
     a.kq = dk;
@@ -595,21 +619,15 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.keys = dkeys;
-    a.entry_key = derive(idx->seed, HENN_TAG_ENTRY);
     a.out_ids = dids;
     a.out_d = dd;
     a.out_stride = out_stride;
     a.stats = dstats;
     a.counter = counter;
 
-    int sms = 0;
-    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, idx->device));
     size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
-    int per_sm = (int)((200 * 1024) / (smem > 0 ? smem : 1));
-    if (per_sm < 1) per_sm = 1;
-    if (per_sm > 64 / warps) per_sm = 64 / warps;
     int64_t blocks_needed = (nq + warps - 1) / warps;
-    int grid = (int)std::min<int64_t>((int64_t)sms * per_sm, blocks_needed);
+    int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
     CK(launch_search(a, warps, grid, st));
     if (!q_on_device) {
       CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
@@ -764,3 +782,274 @@ extern "C" henn_status henn_quantize_rows(const float* X, int64_t n, int32_t d, 
     return f.status;
   }
 }
+
+// ------------------------------------------------------------- serving
+
+struct henn_server {
+  const henn_index* idx = nullptr;
+  henn_serve_params p;
+  ServeArgs args;
+  int warps = kSearchWarps, grid = 0;
+  cudaStream_t kst = nullptr, cst = nullptr;
+  // device
+  float* qring = nullptr;
+  ServeDesc* desc = nullptr;
+  int64_t* oids = nullptr;
+  float* od = nullptr;
+  long long* published = nullptr;
+  unsigned long long* taken = nullptr;
+  int* stop = nullptr;
+  // mapped host memory
+  int* done_h = nullptr;
+  int* done_d = nullptr;
+  // host bookkeeping
+  struct Req {
+    int64_t id = 0, start = 0;
+    int32_t nq = 0, k = 0;
+    bool active = false, collected = false;
+  };
+  std::vector<Req> slots;
+  std::deque<int32_t> order;  // slots in submission order (ring reclamation)
+  std::vector<ServeDesc> hdesc;
+  int64_t head = 0, tail = 0, next_id = 1;
+  bool launched = false;
+  std::mutex mu;
+
+  ~henn_server() {
+    if (stop) {
+      int one = 1;
+      cudaMemcpyAsync(stop, &one, sizeof(int), cudaMemcpyHostToDevice, cst);
+      cudaStreamSynchronize(cst);
+    }
+    if (kst) cudaStreamSynchronize(kst);
+    for (void* q : {(void*)qring, (void*)desc, (void*)oids, (void*)od, (void*)published, (void*)taken, (void*)stop})
+      if (q) cudaFree(q);
+    if (done_h) cudaFreeHost(done_h);
+    if (kst) cudaStreamDestroy(kst);
+    if (cst) cudaStreamDestroy(cst);
+  }
+
+  // relaunch the kernel when it has ended and published items are waiting
+  void ensure_running() {
+    if (launched) {
+      cudaError_t q = cudaStreamQuery(kst);
+      if (q == cudaErrorNotReady) return;
+      CK(q);
+      unsigned long long tk = 0;
+      CK(cudaMemcpyAsync(&tk, taken, sizeof(tk), cudaMemcpyDeviceToHost, cst));
+      CK(cudaStreamSynchronize(cst));
+      if ((int64_t)tk >= head) return;
+    } else if (head == 0) {
+      return;
+    }
+    CK(launch_serve(args, warps, grid, kst));
+    launched = true;
+  }
+
+  void copy_ring(void* ring, const void* src, size_t row_bytes, int64_t start, int32_t n, cudaMemcpyKind kind,
+                 bool to_ring) {
+    const int64_t cap = p.ring_rows;
+    const int64_t s0 = start % cap;
+    const int64_t n1 = std::min<int64_t>(n, cap - s0);
+    char* r = static_cast<char*>(ring);
+    const char* h = static_cast<const char*>(src);
+    if (to_ring) {
+      CK(cudaMemcpyAsync(r + s0 * row_bytes, h, n1 * row_bytes, kind, cst));
+      if (n > n1) CK(cudaMemcpyAsync(r, h + n1 * row_bytes, (n - n1) * row_bytes, kind, cst));
+    }
+  }
+};
+
+extern "C" void henn_serve_params_default(henn_serve_params* p) {
+  if (!p) return;
+  std::memset(p, 0, sizeof(*p));
+  p->struct_size = sizeof(*p);
+  p->ring_rows = 65536;
+  p->max_requests = 1024;
+  p->max_k = 100;
+  p->max_ef = 512;
+  p->ef_upper = 1;
+  p->descend_all = 0;
+  p->rerank_mult = 4;
+  p->idle_ms = 20;
+}
+
+extern "C" henn_status henn_serve_create(const henn_index* idx, const henn_serve_params* pp, henn_server** out) {
+  g_error.clear();
+  if (out) *out = nullptr;
+  henn_server* sv = nullptr;
+  try {
+    require(idx && out, "NULL argument");
+    henn_serve_params p;
+    henn_serve_params_default(&p);
+    if (pp) {
+      require(pp->struct_size == sizeof(henn_serve_params), "henn_serve_params.struct_size mismatch");
+      p = *pp;
+    }
+    require(p.ring_rows >= 1 && p.ring_rows <= (1 << 26), "ring_rows must be in [1, 2^26]");
+    require(p.max_requests >= 1 && p.max_requests <= (1 << 20), "max_requests must be in [1, 2^20]");
+    require(p.max_k >= 1 && p.max_k <= 1024, "max_k must be in [1, 1024]");
+    require(p.max_ef >= 1 && p.max_ef <= 1024, "max_ef must be in [1, 1024]");
+    require(p.ef_upper >= 0 && p.ef_upper <= 1024, "ef_upper must be in [0, 1024]");
+    require(p.idle_ms >= 1 && p.idle_ms <= 10000, "idle_ms must be in [1, 10000]");
+    if (p.rerank_mult <= 0) p.rerank_mult = 4;
+    sv = new henn_server();
+    sv->idx = idx;
+    sv->p = p;
+    CK(cudaStreamCreateWithFlags(&sv->kst, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&sv->cst, cudaStreamNonBlocking));
+    const int64_t cap = p.ring_rows;
+    CK(cudaMalloc(&sv->qring, sizeof(float) * cap * idx->d));
+    CK(cudaMalloc(&sv->desc, sizeof(ServeDesc) * cap));
+    CK(cudaMalloc(&sv->oids, sizeof(int64_t) * cap * p.max_k));
+    CK(cudaMalloc(&sv->od, sizeof(float) * cap * p.max_k));
+    CK(cudaMalloc(&sv->published, sizeof(long long)));
+    CK(cudaMalloc(&sv->taken, sizeof(unsigned long long)));
+    CK(cudaMalloc(&sv->stop, sizeof(int)));
+    CK(cudaMemset(sv->published, 0, sizeof(long long)));
+    CK(cudaMemset(sv->taken, 0, sizeof(unsigned long long)));
+    CK(cudaMemset(sv->stop, 0, sizeof(int)));
+    CK(cudaHostAlloc(&sv->done_h, sizeof(int) * p.max_requests, cudaHostAllocMapped));
+    CK(cudaHostGetDevicePointer((void**)&sv->done_d, sv->done_h, 0));
+    std::memset(sv->done_h, 0, sizeof(int) * p.max_requests);
+    sv->slots.resize(p.max_requests);
+    // kernel shape: the shared-memory class of the widest admitted beam
+    const int need = std::max(std::max(p.max_k, p.max_ef), std::max(p.ef_upper, std::min(p.max_ef, p.rerank_mult * p.max_k)));
+    int ef_cap = 32;
+    while (ef_cap < need) ef_cap <<= 1;
+    const int hb = pick_hash_bits(ef_cap);
+    SearchArgs& a = sv->args.base;
+    fill_search_args(idx, a);
+    a.rerank_mult = p.rerank_mult;
+    a.ef_upper = p.ef_upper;
+    a.descend_all = p.descend_all;
+    a.ef_cap = ef_cap;
+    a.hash_bits = hb;
+    a.out_stride = p.max_k;
+    sv->args.qring = sv->qring;
+    sv->args.desc = sv->desc;
+    sv->args.cap = cap;
+    sv->args.out_ids = sv->oids;
+    sv->args.out_d = sv->od;
+    sv->args.published = sv->published;
+    sv->args.taken = sv->taken;
+    sv->args.stop = sv->stop;
+    sv->args.done = sv->done_d;
+    sv->args.idle_ns = (long long)p.idle_ms * 1000000ll;
+    sv->grid = persistent_grid(idx->device, sv->warps, search_warp_smem(ef_cap, hb, idx->dpad) * sv->warps);
+    CK(cudaDeviceSynchronize());
+    *out = sv;
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    delete sv;
+    return f.status;
+  }
+}
+
+extern "C" henn_status henn_serve_submit(henn_server* sv, const float* Q, int32_t nq, int32_t k, int32_t ef,
+                                         const uint64_t* keys, int64_t* request_id) {
+  g_error.clear();
+  try {
+    require(sv && Q && request_id, "NULL argument");
+    require(nq >= 1 && nq <= sv->p.ring_rows, "nq must be in [1, ring_rows]");
+    require(k >= 1 && k <= sv->p.max_k, "k must be in [1, max_k]");
+    require(ef >= 1 && ef <= sv->p.max_ef, "ef must be in [1, max_ef]");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    int32_t slot = -1;
+    for (int32_t i = 0; i < (int32_t)sv->slots.size(); ++i)
+      if (!sv->slots[i].active) {
+        slot = i;
+        break;
+      }
+    if (slot < 0 || sv->head - sv->tail + nq > sv->p.ring_rows) {
+      g_error = "serving budget full (request slots or ring rows)";
+      return HENN_ERR_BUSY;
+    }
+    const int64_t id = sv->next_id++;
+    const int64_t start = sv->head;
+    sv->hdesc.resize(nq);
+    for (int32_t i = 0; i < nq; ++i) {
+      sv->hdesc[i].slot = slot;
+      sv->hdesc[i].k = k;
+      sv->hdesc[i].ef = ef;
+      sv->hdesc[i].pad = 0;
+      sv->hdesc[i].key = keys ? keys[i] : ((uint64_t)id << 20) + (uint64_t)i;
+    }
+    sv->copy_ring(sv->qring, Q, sizeof(float) * sv->idx->d, start, nq, cudaMemcpyHostToDevice, true);
+    sv->copy_ring(sv->desc, sv->hdesc.data(), sizeof(ServeDesc), start, nq, cudaMemcpyHostToDevice, true);
+    __atomic_store_n(&sv->done_h[slot], 0, __ATOMIC_RELEASE);
+    long long pub = start + nq;
+    // same stream as the ring copies: the kernel sees the new count only
+    // after the rows and descriptors have landed
+    CK(cudaMemcpyAsync(sv->published, &pub, sizeof(pub), cudaMemcpyHostToDevice, sv->cst));
+    CK(cudaStreamSynchronize(sv->cst));
+    sv->head = pub;
+    henn_server::Req& r = sv->slots[slot];
+    r.id = id;
+    r.start = start;
+    r.nq = nq;
+    r.k = k;
+    r.active = true;
+    r.collected = false;
+    sv->order.push_back(slot);
+    sv->ensure_running();
+    *request_id = id;
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  }
+}
+
+extern "C" henn_status henn_serve_poll(henn_server* sv, int64_t request_id, int32_t* done, int64_t* out_ids,
+                                       float* out_dists) {
+  g_error.clear();
+  try {
+    require(sv && done && out_ids && out_dists, "NULL argument");
+    std::lock_guard<std::mutex> lock(sv->mu);
+    int32_t slot = -1;
+    for (int32_t i = 0; i < (int32_t)sv->slots.size(); ++i)
+      if (sv->slots[i].active && !sv->slots[i].collected && sv->slots[i].id == request_id) {
+        slot = i;
+        break;
+      }
+    require(slot >= 0, "unknown or already collected request");
+    henn_server::Req& r = sv->slots[slot];
+    sv->ensure_running();
+    if (__atomic_load_n(&sv->done_h[slot], __ATOMIC_ACQUIRE) < r.nq) {
+      *done = 0;
+      return HENN_OK;
+    }
+    const int64_t cap = sv->p.ring_rows;
+    const int64_t s0 = r.start % cap;
+    const int64_t n1 = std::min<int64_t>(r.nq, cap - s0);
+    const size_t spitch_i = sizeof(int64_t) * sv->p.max_k, spitch_f = sizeof(float) * sv->p.max_k;
+    CK(cudaMemcpy2DAsync(out_ids, sizeof(int64_t) * r.k, sv->oids + s0 * sv->p.max_k, spitch_i, sizeof(int64_t) * r.k,
+                         n1, cudaMemcpyDeviceToHost, sv->cst));
+    CK(cudaMemcpy2DAsync(out_dists, sizeof(float) * r.k, sv->od + s0 * sv->p.max_k, spitch_f, sizeof(float) * r.k, n1,
+                         cudaMemcpyDeviceToHost, sv->cst));
+    if (r.nq > n1) {
+      CK(cudaMemcpy2DAsync(out_ids + n1 * r.k, sizeof(int64_t) * r.k, sv->oids, spitch_i, sizeof(int64_t) * r.k,
+                           r.nq - n1, cudaMemcpyDeviceToHost, sv->cst));
+      CK(cudaMemcpy2DAsync(out_dists + n1 * r.k, sizeof(float) * r.k, sv->od, spitch_f, sizeof(float) * r.k,
+                           r.nq - n1, cudaMemcpyDeviceToHost, sv->cst));
+    }
+    CK(cudaStreamSynchronize(sv->cst));
+    r.collected = true;
+    // release ring rows in submission order
+    while (!sv->order.empty() && sv->slots[sv->order.front()].collected) {
+      henn_server::Req& f = sv->slots[sv->order.front()];
+      sv->tail = f.start + f.nq;
+      f.active = false;
+      sv->order.pop_front();
+    }
+    *done = 1;
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  }
+}
+
+extern "C" void henn_serve_destroy(henn_server* sv) { delete sv; }

@@ -158,15 +158,12 @@ __device__ __forceinline__ bool visit(int32_t* table, int HB, int32_t id, int& e
   uint32_t h = ((uint32_t)id * 0x9E3779B1u) >> (32 - HB);
 #pragma unroll
   for (int p = 0; p < 4; ++p) {
-    uint32_t s = (h + p) & mask;
-    int32_t v = table[s];
-    if (v == id) return false;
-    if (v < 0) {
-      table[s] = id;
-      return true;
-    }
+    const uint32_t s = (h + p) & mask;
+    const int32_t old = atomicCAS(table + s, -1, id);  // lanes of one row never share an id
+    if (old == -1) return true;
+    if (old == id) return false;
   }
-  table[h] = id;
+  table[h] = id;  // full neighbourhood: forget the resident entry
   ++evictions;
   return true;
 }
@@ -182,41 +179,6 @@ __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t
       hi = mid;
   }
   return lo;
-}
-
-// count of lanes whose (sorted ascending) candidate is < w
-__device__ __forceinline__ int count_less(uint64_t cand, uint64_t w) {
-  int c = 0;
-#pragma unroll
-  for (int step = 16; step > 0; step >>= 1) {
-    uint64_t v = shfl64(cand, c + step - 1);
-    if (v < w) c += step;
-  }
-  uint64_t v = shfl64(cand, c < 31 ? c : 31);
-  if (c == 31 && v < w) c = 32;
-  return c;
-}
-
-// Merge sorted candidates (lanes 0..cnt-1, ascending, kEmpty after) into
-// W keeping the first cap entries.  Returns the smallest position written
-// for a candidate (or cap when none fit).
-__device__ __forceinline__ int merge_into_w(uint64_t* W, int& nw, int cap, uint64_t cand, int cnt) {
-  const int lane = lane_id();
-  int pos = lane + lower_bound_w(W, nw, cand);
-  __syncwarp();
-  for (int base = ((nw - 1) >> 5) << 5; base >= 0; base -= 32) {
-    int i = base + lane;
-    uint64_t w = i < nw ? W[i] : kEmpty;
-    int cl = count_less(cand, w & kKeyMask);
-    __syncwarp();
-    if (i < nw && i + cl < cap) W[i + cl] = w;
-    __syncwarp();
-  }
-  if (lane < cnt && pos < cap) W[pos] = cand;
-  __syncwarp();
-  int first = __shfl_sync(0xffffffffu, pos, 0);
-  nw = min(cap, nw + cnt);
-  return cnt > 0 ? min(first, cap) : cap;
 }
 
 // Best-first beam of width ef on one layer from `entry` (S3).  Leaves W
@@ -290,19 +252,41 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, packed_id, cnt, qs, nchunk);
     evals += cnt;
     const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
-    uint64_t cand = kEmpty;
-    if (lane < cnt) {
-      uint64_t kk = pack(dn, (uint32_t)packed_id);
-      if (nw < ef || kk < worst) {
-        int lb = lower_bound_w(W, nw, kk);
-        if (!(lb < nw && (W[lb] & kKeyMask) == kk)) cand = kk;
-      }
+    uint64_t kk = lane < cnt ? pack(dn, (uint32_t)packed_id) : kEmpty;
+    bool take = kk < worst;
+    // a node can reach W twice only if the visited table forgot it
+    if (__any_sync(0xffffffffu, evictions > 0) && take) {
+      const int lb = lower_bound_w(W, nw, kk);
+      if (lb < nw && (W[lb] & kKeyMask) == kk) take = false;
     }
-    unsigned cm = __ballot_sync(0xffffffffu, cand != kEmpty);
-    int ccnt = __popc(cm);
+    const unsigned cm = __ballot_sync(0xffffffffu, take);
+    const int ccnt = __popc(cm);
     if (ccnt == 0) continue;
-    cand = warp_sort_asc(cand);
-    int p0 = merge_into_w(W, nw, ef, cand, ccnt);
+    // candidates to lanes 0..ccnt-1; rank among them; position in the new W
+    const unsigned csrc = __fns(cm, 0, lane + 1);
+    const uint64_t moved = shfl64(kk, csrc < 32 ? (int)csrc : 0);
+    const uint64_t cand = lane < ccnt ? moved : kEmpty;
+    int rank = 0;
+    for (int j = 0; j < ccnt; ++j) rank += shfl64(cand, j) < cand;
+    const int cpos = lane < ccnt ? lower_bound_w(W, nw, cand) + rank : 0x7fffffff;
+    int p0 = cpos;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) p0 = min(p0, __shfl_xor_sync(0xffffffffu, p0, o));
+    // entries at or after p0 shift right by the number of smaller candidates
+    __syncwarp();
+    for (int base = ((nw - 1) >> 5) << 5; base >= (p0 & ~31); base -= 32) {
+      const int i = base + lane;
+      const bool mv = i < nw && i >= p0;
+      const uint64_t w = mv ? W[i] : kEmpty;
+      int cl = 0;
+      for (int j = 0; j < ccnt; ++j) cl += shfl64(cand, j) < (w & kKeyMask);
+      __syncwarp();
+      if (mv && i + cl < ef) W[i + cl] = w;
+      __syncwarp();
+    }
+    if (lane < ccnt && cpos < ef) W[cpos] = cand;
+    __syncwarp();
+    nw = min(ef, nw + ccnt);
     first = min(first, p0);
   }
   return nw;
@@ -319,157 +303,238 @@ struct RowShape {
   static constexpr int CPL = (kChunks + G - 1) / G;
 };
 
+// S4 + output: exact FP32 rerank of the best rerank_mult * k entries
+// (BF16 / FP8 storage), then the first k of W in (distance, index) order.
+template <int G32, int CPL32>
+__device__ __noinline__ void finish_query(const SearchArgs& a, uint64_t* W, int nw, int k, const float* qs,
+                                          int64_t* out_ids, float* out_d) {
+  const int lane = lane_id();
+  const int dpad = a.dpad;
+  const int out_k = min(k, a.out_stride);
+  if (a.rerank && nw > 0) {
+    int R = min(nw, max(k, a.rerank_mult * k));
+    // exact FP32 distances for W[0..R), then sort in place
+    for (int b = 0; b < R; b += 32) {
+      int i = b + lane;
+      int32_t id = i < R ? (int32_t)key_index(W[i] & kKeyMask) : 0;
+      int cntb = min(32, R - b);
+      float dx = rows_dist<float, G32, CPL32>(a.x32, nullptr, (int64_t)dpad * 4, id, cntb, qs, dpad / 4);
+      __syncwarp();
+      if (i < R) W[i] = pack(dx, (uint32_t)id);
+      __syncwarp();
+    }
+    // bitonic sort of W[0..P), P = next pow2 >= R, padded with kEmpty
+    int P = 1;
+    while (P < R) P <<= 1;
+    for (int i = R + lane; i < P; i += 32) W[i] = kEmpty;
+    __syncwarp();
+    for (int size = 2; size <= P; size <<= 1)
+      for (int stride2 = size >> 1; stride2 > 0; stride2 >>= 1) {
+        for (int i = lane; i < P; i += 32) {
+          int j = i ^ stride2;
+          if (j > i) {
+            uint64_t x = W[i], y = W[j];
+            bool up = (i & size) == 0;
+            if ((x > y) == up) {
+              W[i] = y;
+              W[j] = x;
+            }
+          }
+        }
+        __syncwarp();
+      }
+    nw = R;
+  }
+  for (int j = lane; j < a.out_stride; j += 32) {
+    bool ok = j < out_k && j < nw;
+    uint64_t e = ok ? (W[j] & kKeyMask) : kEmpty;
+    float dv = ok ? key_dist(e) : __int_as_float(0x7f800000);
+    if (ok) dv = a.metric == HENN_ANGULAR ? 0.5f * dv : sqrtf(dv);
+    out_ids[j] = ok ? (int64_t)key_index(e) : -1;
+    out_d[j] = dv;
+  }
+}
+
+// One query, one warp: S1-S4 for the query row `qg` (d floats), writing
+// out_stride results to out_ids / out_d and 4 counters to stats (optional).
+// `my` is this warp's shared-memory slice.
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128, 4) k_search(const SearchArgs a) {
+__device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my, const float* __restrict__ qg, int k,
+                                          int ef, uint64_t key, int64_t* out_ids, float* out_d, int32_t* stats) {
   constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
   constexpr int G32 = RowShape<float, DMAX>::G, CPL32 = RowShape<float, DMAX>::CPL;
-  extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
-  const int wib = threadIdx.x >> 5;
   const int dpad = a.dpad;
-  constexpr int kElems = Chunk<VT>::kElems;
-  // per-warp slices
   const int EFCAP = a.ef_cap, HB = a.hash_bits;
-  unsigned char* my = smem + (size_t)wib * a.warp_smem;
   uint64_t* W = reinterpret_cast<uint64_t*>(my);
   int32_t* table = reinterpret_cast<int32_t*>(my + EFCAP * 8);
   float* qs = reinterpret_cast<float*>(my + EFCAP * 8 + (4 << HB));
   const int64_t stride = (int64_t)dpad * sizeof(VT);
   const int nchunk = (int)(stride / 16);
 
+  ef = max(ef, k);
+  ef = min(ef, EFCAP);
+  int evals = 0, expansions = 0, moves = 0, evictions = 0;
+
+  // query into shared memory (normalised for the angular metric)
+  {
+    float ss = 0.f;
+    for (int c = lane; c < dpad; c += 32) {
+      float v = c < a.d ? __ldcg(qg + c) : 0.f;  // L2 read: serving rings are rewritten
+      qs[c] = v;
+      ss = fmaf(v, v, ss);
+    }
+    if (a.metric == HENN_ANGULAR) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      float inv = ss > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(ss)) : 0.f;
+      __syncwarp();
+      for (int c = lane; c < dpad; c += 32) qs[c] *= inv;
+    }
+    __syncwarp();
+  }
+
+  // S1: random node of the top layer
+  int32_t cur = (int32_t)bounded(derive(a.entry_key, key), (uint64_t)a.layers[a.L].size);
+  // S2: upper layers: GreedySearch of Alg. 4, or a beam of width ef_upper
+  int nseed = 0;
+  for (int li = a.L; li >= 1; --li) {
+    const SearchLayer Ly = a.layers[li];
+    if (a.ef_upper > 1) {
+      int ex = 0;
+      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex,
+                                evictions, nseed);
+      moves += ex;
+      cur = (int32_t)key_index(W[0] & kKeyMask);
+      if (a.descend_all) {
+        // the layer below is entered at the copies of every candidate;
+        // down pointers are increasing, so the (distance, index) order holds
+        for (int j = lane; j < nw; j += 32) {
+          uint64_t e = W[j] & kKeyMask;
+          W[j] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(e)];
+        }
+        nseed = nw;
+      }
+      __syncwarp();
+    } else {
+      const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
+      float dc = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, cur, 1, qs, nchunk);
+      dc = __shfl_sync(0xffffffffu, dc, 0);
+      ++evals;
+      for (;;) {
+        int32_t nb = Ly.adj[(int64_t)cur * kMmax + lane];
+        unsigned valid = __ballot_sync(0xffffffffu, nb >= 0);
+        int cnt = __popc(valid);
+        // neighbours are packed at the front of each row (-1 padding after)
+        float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, nb, cnt, qs, nchunk);
+        evals += cnt;
+        uint64_t kk = lane < cnt ? pack(dn, (uint32_t)nb) : kEmpty;
+        uint64_t best = warp_min64(kk);
+        if (best == kEmpty || !(key_dist(best) < dc)) break;
+        cur = (int32_t)key_index(best);
+        dc = key_dist(best);
+        ++moves;
+      }
+    }
+    cur = Ly.down[cur];
+  }
+
+  // S3: layer-0 beam
+  const SearchLayer B = a.layers[0];
+  int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions, nseed);
+
+  // S4 + output
+  finish_query<G32, CPL32>(a, W, nw, k, qs, out_ids, out_d);
+  if (stats && lane == 0) {
+    stats[0] = evals;
+    stats[1] = expansions;
+    stats[2] = moves;
+    stats[3] = evictions;
+  }
+  __syncwarp();
+}
+
+template <typename VT, int DMAX>
+__global__ void __launch_bounds__(128, 4) k_search(const SearchArgs a) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id();
+  unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * a.warp_smem;
   for (;;) {
     int64_t qi = 0;
     if (lane == 0) qi = atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
     qi = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)qi, 0);
     if (qi >= a.nq) break;
-
     const int k = a.kq ? a.kq[qi] : a.k_uniform;
-    int ef = a.efq ? a.efq[qi] : a.ef_uniform;
-    ef = max(ef, k);
-    ef = min(ef, EFCAP);
-    int evals = 0, expansions = 0, moves = 0, evictions = 0;
-
-    // query into shared memory (normalised for the angular metric)
-    {
-      const float* qg = a.Q + qi * a.d;
-      float ss = 0.f;
-      for (int c = lane; c < dpad; c += 32) {
-        float v = c < a.d ? qg[c] : 0.f;
-        qs[c] = v;
-        ss = fmaf(v, v, ss);
-      }
-      if (a.metric == HENN_ANGULAR) {
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
-        float inv = ss > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(ss)) : 0.f;
-        __syncwarp();
-        for (int c = lane; c < dpad; c += 32) qs[c] *= inv;
-      }
-      __syncwarp();
-    }
-
-    // S1: random node of the top layer
+    const int ef = a.efq ? a.efq[qi] : a.ef_uniform;
     const uint64_t key = a.keys ? a.keys[qi] : (uint64_t)qi;
-    int32_t cur = (int32_t)bounded(derive(a.entry_key, key), (uint64_t)a.layers[a.L].size);
+    run_query<VT, DMAX>(a, my, a.Q + qi * a.d, k, ef, key, a.out_ids + qi * a.out_stride,
+                        a.out_d + qi * a.out_stride, a.stats ? a.stats + qi * 4 : nullptr);
+  }
+}
 
-    // S2: upper layers: GreedySearch of Alg. 4, or a beam of width ef_upper
-    int nseed = 0;
-    for (int li = a.L; li >= 1; --li) {
-      const SearchLayer Ly = a.layers[li];
-      if (a.ef_upper > 1) {
-        int ex = 0;
-        int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex,
-                                  evictions, nseed);
-        moves += ex;
-        cur = (int32_t)key_index(W[0] & kKeyMask);
-        if (a.descend_all) {
-          // the layer below is entered at the copies of every candidate;
-          // down pointers are increasing, so the (distance, index) order holds
-          for (int j = lane; j < nw; j += 32) {
-            uint64_t e = W[j] & kKeyMask;
-            W[j] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(e)];
+// ------------------------------------------------------ serving loop
+
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ long long ld_acquire_gpu(const long long* p) {
+  long long v;
+  asm volatile("ld.acquire.gpu.global.s64 %0, [%1];" : "=l"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Persistent serving kernel.  Work items (one per query) are numbered in
+// arrival order; the host publishes a prefix by raising `published` (device
+// memory, written by a copy after the item's query row and descriptor).  A
+// warp takes the next item only if it is already published (CAS on
+// `taken`), so no warp ever waits while holding an item.  With nothing to
+// take, a warp polls with back-off until `stop` is raised or it has been
+// idle for idle_ns, then leaves; the host relaunches the kernel when new
+// items are published and it has ended.  A finished query bumps its
+// request's counter in mapped host memory after a system-scope fence.
+template <typename VT, int DMAX>
+__global__ void __launch_bounds__(128, 4) k_serve(const ServeArgs s) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id();
+  unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * s.base.warp_smem;
+  for (;;) {
+    long long t = -1;
+    if (lane == 0) {
+      const uint64_t t0 = global_ns();
+      unsigned backoff = 256;
+      for (long long spin = 0; spin < (1ll << 26); ++spin) {
+        const long long p = ld_acquire_gpu(s.published);
+        const unsigned long long tk = *reinterpret_cast<volatile unsigned long long*>(s.taken);
+        if ((long long)tk < p) {
+          if (atomicCAS(s.taken, tk, tk + 1ull) == tk) {
+            t = (long long)tk;
+            break;
           }
-          nseed = nw;
+          continue;
         }
-        __syncwarp();
-      } else {
-        const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
-        float dc = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, cur, 1, qs, nchunk);
-        dc = __shfl_sync(0xffffffffu, dc, 0);
-        ++evals;
-        for (;;) {
-          int32_t nb = Ly.adj[(int64_t)cur * kMmax + lane];
-          unsigned valid = __ballot_sync(0xffffffffu, nb >= 0);
-          int cnt = __popc(valid);
-          // neighbours are packed at the front of each row (-1 padding after)
-          float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, nb, cnt, qs, nchunk);
-          evals += cnt;
-          uint64_t kk = lane < cnt ? pack(dn, (uint32_t)nb) : kEmpty;
-          uint64_t best = warp_min64(kk);
-          if (best == kEmpty || !(key_dist(best) < dc)) break;
-          cur = (int32_t)key_index(best);
-          dc = key_dist(best);
-          ++moves;
-        }
+        if (*reinterpret_cast<const volatile int*>(s.stop)) break;
+        if (global_ns() - t0 > (uint64_t)s.idle_ns) break;
+        __nanosleep(backoff);
+        if (backoff < 8192) backoff <<= 1;
       }
-      cur = Ly.down[cur];
     }
-
-    // S3: layer-0 beam
-    const SearchLayer B = a.layers[0];
-    int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions, nseed);
-
-    // S4 + output
-    const int out_k = min(k, a.out_stride);
-    if (a.rerank && nw > 0) {
-      int R = min(nw, max(k, a.rerank_mult * k));
-      // exact FP32 distances for W[0..R), then sort in place
-      for (int b = 0; b < R; b += 32) {
-        int i = b + lane;
-        int32_t id = i < R ? (int32_t)key_index(W[i] & kKeyMask) : 0;
-        int cntb = min(32, R - b);
-        float dx = rows_dist<float, G32, CPL32>(a.x32, nullptr, (int64_t)dpad * 4, id, cntb, qs, dpad / 4);
-        __syncwarp();
-        if (i < R) W[i] = pack(dx, (uint32_t)id);
-        __syncwarp();
-      }
-      // bitonic sort of W[0..P), P = next pow2 >= R, padded with kEmpty
-      int P = 1;
-      while (P < R) P <<= 1;
-      for (int i = R + lane; i < P; i += 32) W[i] = kEmpty;
-      __syncwarp();
-      for (int size = 2; size <= P; size <<= 1)
-        for (int stride2 = size >> 1; stride2 > 0; stride2 >>= 1) {
-          for (int i = lane; i < P; i += 32) {
-            int j = i ^ stride2;
-            if (j > i) {
-              uint64_t x = W[i], y = W[j];
-              bool up = (i & size) == 0;
-              if ((x > y) == up) {
-                W[i] = y;
-                W[j] = x;
-              }
-            }
-          }
-          __syncwarp();
-        }
-      nw = R;
-    }
-    for (int j = lane; j < a.out_stride; j += 32) {
-      bool ok = j < out_k && j < nw;
-      uint64_t e = ok ? (W[j] & kKeyMask) : kEmpty;
-      float dv = ok ? key_dist(e) : __int_as_float(0x7f800000);
-      if (ok) dv = a.metric == HENN_ANGULAR ? 0.5f * dv : sqrtf(dv);
-      a.out_ids[qi * a.out_stride + j] = ok ? (int64_t)key_index(e) : -1;
-      a.out_d[qi * a.out_stride + j] = dv;
-    }
-    if (a.stats && lane == 0) {
-      a.stats[qi * 4 + 0] = evals;
-      a.stats[qi * 4 + 1] = expansions;
-      a.stats[qi * 4 + 2] = moves;
-      a.stats[qi * 4 + 3] = evictions;
-    }
+    t = __shfl_sync(0xffffffffu, t, 0);
+    if (t < 0) break;
+    const int64_t slot = t % s.cap;
+    const int32_t req = __ldcg(&s.desc[slot].slot);
+    const int32_t k = __ldcg(&s.desc[slot].k);
+    const int32_t ef = __ldcg(&s.desc[slot].ef);
+    const uint64_t key = __ldcg(&s.desc[slot].key);
+    run_query<VT, DMAX>(s.base, my, s.qring + slot * s.base.d, k, ef, key, s.out_ids + slot * s.base.out_stride,
+                        s.out_d + slot * s.base.out_stride, nullptr);
     __syncwarp();
+    if (lane == 0) {
+      __threadfence_system();
+      atomicAdd_system(s.done + req, 1);
+    }
   }
 }
 
@@ -496,6 +561,33 @@ static cudaError_t launch_vt(const SearchArgs& a, int warps, int grid, size_t sm
   if (a.dpad <= 128) return launch_t<VT, 128>(a, warps, grid, smem, st);
   if (a.dpad <= 512) return launch_t<VT, 512>(a, warps, grid, smem, st);
   return launch_t<VT, 1024>(a, warps, grid, smem, st);
+}
+
+template <typename VT, int DMAX>
+static cudaError_t launch_serve_t(const ServeArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  auto kern = k_serve<VT, DMAX>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, warps * 32, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t launch_serve_vt(const ServeArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
+  if (a.base.dpad <= 32) return launch_serve_t<VT, 32>(a, warps, grid, smem, st);
+  if (a.base.dpad <= 64) return launch_serve_t<VT, 64>(a, warps, grid, smem, st);
+  if (a.base.dpad <= 128) return launch_serve_t<VT, 128>(a, warps, grid, smem, st);
+  if (a.base.dpad <= 512) return launch_serve_t<VT, 512>(a, warps, grid, smem, st);
+  return launch_serve_t<VT, 1024>(a, warps, grid, smem, st);
+}
+
+cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st) {
+  ServeArgs b = a;
+  b.base.warp_smem = (int32_t)search_warp_smem(a.base.ef_cap, a.base.hash_bits, a.base.dpad);
+  size_t smem = (size_t)b.base.warp_smem * warps_per_block;
+  if (a.base.storage == HENN_BF16) return launch_serve_vt<__nv_bfloat16>(b, warps_per_block, grid, smem, st);
+  if (a.base.storage == HENN_FP8E4M3) return launch_serve_vt<__nv_fp8_e4m3>(b, warps_per_block, grid, smem, st);
+  return launch_serve_vt<float>(b, warps_per_block, grid, smem, st);
 }
 
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st) {

@@ -42,7 +42,29 @@ struct SearchArgs {
   int32_t warp_smem;            // bytes of shared memory per warp
 };
 
+// One published work item of the serving loop (one query).
+struct ServeDesc {
+  int32_t slot;  // request slot whose counter the query bumps
+  int32_t k, ef, pad;
+  uint64_t key;  // entry-node key
+};
+
+struct ServeArgs {
+  SearchArgs base;               // index, shapes, beam parameters, out_stride
+  const float* qring;            // cap x d query rows (device)
+  const ServeDesc* desc;         // cap descriptors (device)
+  int64_t cap;                   // ring capacity (items)
+  int64_t* out_ids;              // cap x out_stride (device)
+  float* out_d;                  // cap x out_stride (device)
+  const long long* published;    // items published so far (device, written by copies)
+  unsigned long long* taken;     // items taken so far (device)
+  const int* stop;               // raised to end the loop (device)
+  int* done;                     // per request slot: finished queries (mapped host memory)
+  long long idle_ns;             // a warp leaves after this long without work
+};
+
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st);
 
 }  // namespace henn

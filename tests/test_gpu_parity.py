@@ -71,6 +71,14 @@ def uniform10k():
     return X, Q, oidx, gidx
 
 
+def test_graph_parity_simt_tiles(uniform10k):
+    """The CUDA-core FP32 tile engine (used for d > 128) on the same layers."""
+    X, Q, oidx, _ = uniform10k
+    gidx = _gpu_index(X, seed=0, tiles=H.TILES_SIMT)
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+
+
 # ----------------------------------------------------------- layers
 
 def test_layers_bit_exact_uniform10k(uniform10k):

@@ -1,0 +1,148 @@
+"""Continuous batching (henn_serve_*): requests that arrive while others are
+on the GPU are admitted as ring rows and slots free up, run concurrently in
+one persistent kernel, and each request's results are the same alone and in
+the mix (bitwise: a query's result depends only on the query, k, ef and
+its entry key)."""
+from __future__ import annotations
+
+import threading
+import time
+
+import numpy as np
+import pytest
+
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import paper_2505_17368_gb300 as H  # noqa: E402
+
+
+def _wait(srv, rid, timeout=60.0):
+    t0 = time.time()
+    while True:
+        r = srv.poll(rid)
+        if r is not None:
+            return r
+        assert time.time() - t0 < timeout, "request did not finish"
+        time.sleep(0.0005)
+
+
+@pytest.fixture(scope="module")
+def index_and_queries():
+    X, rng = synth.gaussian_mixture(20000, 64, 100, seed=0, rescale_to_255=True)
+    Q, _ = synth.gaussian_mixture(3000, 64, 100, seed=1, rescale_from=rng, rescale_to_255=True)
+    idx = H.Index(torch.from_numpy(X).cuda(), storage=H.BF16, seed=3)
+    return idx, Q
+
+
+def _requests(nq_total, seed):
+    rng = np.random.default_rng(seed)
+    reqs, at = [], 0
+    while at < nq_total:
+        b = int(min(nq_total - at, np.exp(rng.uniform(0, np.log(400)))))
+        k = int(rng.choice([10, 100]))
+        ef = int(np.exp(rng.uniform(np.log(64), np.log(512))))
+        reqs.append((at, b, k, ef))
+        at += b
+    return reqs
+
+
+def test_alone_equals_in_mix(index_and_queries):
+    idx, Q = index_and_queries
+    reqs = _requests(len(Q), 0)
+    srv = H.Server(idx, ring_rows=2048, max_requests=16, max_k=100, max_ef=512, ef_upper=16)
+    results = {}
+    errors = []
+
+    def client(part):
+        try:
+            for (at, b, k, ef) in part:
+                keys = np.arange(at, at + b, dtype=np.uint64)
+                rid = None
+                while rid is None:
+                    rid = srv.submit(Q[at:at + b], k=k, ef=ef, keys=keys)
+                    if rid is None:
+                        time.sleep(0.0002)
+                results[at] = (rid, b, k, ef)
+            for at, _, _, _ in part:
+                rid = results[at][0]
+                results[at] = results[at][1:] + _wait(srv, rid)
+        except Exception as e:  # pragma: no cover
+            errors.append(e)
+
+    th = [threading.Thread(target=client, args=(reqs[i::4],)) for i in range(4)]
+    for t in th:
+        t.start()
+    for t in th:
+        t.join()
+    assert not errors, errors
+    srv.close()
+    # every request alone, through the batch API with the same keys
+    for at, b, k, ef in reqs:
+        _, _, _, ids_mix, d_mix = results[at]
+        keys = torch.arange(at, at + b, dtype=torch.int64, device="cuda")
+        ids, dd, _ = idx.search(torch.from_numpy(Q[at:at + b]).cuda(), k=k, ef=ef, ef_upper=16, keys=keys)
+        assert np.array_equal(ids.cpu().numpy(), ids_mix), at
+        assert np.array_equal(dd.cpu().numpy(), d_mix), at
+    # and alone in a fresh server
+    srv2 = H.Server(idx, ring_rows=2048, max_requests=4, max_k=100, max_ef=512, ef_upper=16)
+    for at, b, k, ef in reqs[:5]:
+        rid = srv2.submit(Q[at:at + b], k=k, ef=ef, keys=np.arange(at, at + b, dtype=np.uint64))
+        ids, dd = _wait(srv2, rid)
+        assert np.array_equal(ids, results[at][3]) and np.array_equal(dd, results[at][4])
+    srv2.close()
+
+
+def test_admission_budget_and_errors(index_and_queries):
+    idx, Q = index_and_queries
+    srv = H.Server(idx, ring_rows=100, max_requests=2, max_k=10, max_ef=128)
+    with pytest.raises(H.HennError) as e:
+        srv.submit(Q[:101], k=10, ef=64)
+    assert e.value.status == 1
+    with pytest.raises(H.HennError) as e:
+        srv.submit(Q[:5], k=11, ef=64)
+    assert e.value.status == 1
+    with pytest.raises(H.HennError) as e:
+        srv.submit(Q[:5], k=10, ef=129)
+    assert e.value.status == 1
+    a = srv.submit(Q[:60], k=10, ef=64)
+    assert a is not None
+    assert srv.submit(Q[60:120], k=10, ef=64) is None  # ring rows: 60 + 60 > 100
+    b = srv.submit(Q[60:80], k=10, ef=64)
+    assert b is not None
+    assert srv.submit(Q[80:81], k=10, ef=64) is None  # both request slots in use
+    _wait(srv, a)
+    c = srv.submit(Q[80:120], k=10, ef=64)  # rows of a released
+    assert c is not None
+    _wait(srv, b)
+    _wait(srv, c)
+    with pytest.raises(H.HennError):
+        srv.poll(c)  # already collected
+    srv.close()
+
+
+def test_idle_exit_and_relaunch(index_and_queries):
+    idx, Q = index_and_queries
+    srv = H.Server(idx, ring_rows=512, max_requests=8, max_k=10, max_ef=128, idle_ms=2)
+    r1 = srv.submit(Q[:50], k=10, ef=64)
+    ids1, _ = _wait(srv, r1)
+    time.sleep(0.1)  # the kernel has left by now
+    r2 = srv.submit(Q[:50], k=10, ef=64, keys=(np.uint64(r1) << np.uint64(20)) + np.arange(50, dtype=np.uint64))
+    ids2, _ = _wait(srv, r2)
+    assert np.array_equal(ids1, ids2)
+    srv.close()
+
+
+def test_destroy_with_requests_in_flight(index_and_queries):
+    idx, Q = index_and_queries
+    srv = H.Server(idx, ring_rows=4096, max_requests=8, max_k=10, max_ef=512)
+    for i in range(4):
+        srv.submit(Q[i * 500:(i + 1) * 500], k=10, ef=512)
+    t0 = time.time()
+    srv.close()
+    assert time.time() - t0 < 30
