@@ -37,9 +37,11 @@ import synth  # noqa: E402
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
 EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
-# (ef_upper, descend_all): beam width on the upper layers, and whether each
-# layer is entered at all candidates of the layer above
-UPPER_SWEEP = [(1, 0), (16, 0), (32, 0), (64, 0), (16, 1), (32, 1), (64, 1)]
+# (ef_upper, descend_all, ef_l1): beam width on the upper layers, whether
+# each layer is entered at all candidates of the layer above, and the beam
+# width on layer 1 (0 = ef_upper)
+UPPER_SWEEP = [(1, 0, 0), (32, 0, 0), (64, 0, 0), (64, 1, 0), (64, 0, 8), (64, 0, 16), (64, 0, 32), (128, 0, 8),
+               (128, 0, 16), (128, 0, 32), (128, 1, 16)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -158,7 +160,7 @@ def _recall(found, gt):
     return float(np.mean(hits)) / gt.shape[1]
 
 
-def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0):
+def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0):
     import torch
 
     H = sys.modules["paper_2505_17368_gb300"]
@@ -166,7 +168,8 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
     ids = torch.empty((nq, K), dtype=torch.int64, device=Qd.device)
     dd = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
     for _ in range(warmup):
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, stream=stream, out=(ids, dd))
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
+                     out=(ids, dd))
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
@@ -175,14 +178,15 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, stream=stream, out=(ids, dd))
+        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
+                     out=(ids, dd))
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
     return times, ids
 
 
-def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1):
+def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1, l1: int = 0, da: int = 0):
     """The FP64 oracle (as it stands) on the host cores: its own index on
     the first n_sample points of the workload stream (built with all
     cores), then the same beam configuration answering nq_sample queries
@@ -197,7 +201,7 @@ def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int
     secs = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu)
+        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da)
         secs.append(time.perf_counter() - t0)
     oracle.set_threads(len(os.sched_getaffinity(0)))
     return nq_sample / statistics.median(secs), 1, secs
@@ -254,21 +258,22 @@ def run_ours(args):
     idx_f32 = H.Index(Xd, storage=H.F32, seed=0)
     build_f32 = time.perf_counter() - t0
     info = idx_bf16.info()
+    info_f32 = idx_f32.info()
     # ---- exact ground truth on the device
     gt, _ = H.exact_knn(Xd, Qd, K)
     gt = gt.cpu().numpy()
     # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
     def sweep(index, tag):
         best = None
-        for efu, da in UPPER_SWEEP:
+        for efu, da, l1 in UPPER_SWEEP:
             for ef in EF_SWEEP:
-                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream, descend_all=da)
+                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream, descend_all=da, ef_l1=l1)
                 r = _recall(ids.cpu().numpy(), gt)
-                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef={ef} recall@10={r:.4f} "
+                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} ef={ef} recall@10={r:.4f} "
                       f"ms={1e3 * min(t):.3f}", file=sys.stderr, flush=True)
                 if r >= RECALL_TARGET:
-                    if best is None or min(t) < best[3]:
-                        best = (ef, efu, da, min(t), r)
+                    if best is None or min(t) < best[4]:
+                        best = (ef, efu, da, l1, min(t), r)
                     break
         return best
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
@@ -276,9 +281,9 @@ def run_ours(args):
     plain = sweep(idx_f32, "f32")
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, da, _, rec = chosen
+    ef, efu, da, l1, _, rec = chosen
     # ---- algorithmic bytes per launch from the kernel's own counters
-    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, stats=True)
+    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True)
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
     R = min(4 * K, ef)
@@ -288,7 +293,8 @@ def run_ours(args):
         torch.distributed.barrier()
     torch.cuda.synchronize()
     with ClockSampler(_smi_id(dev, local)) as clk:
-        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da)
+        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da,
+                                   ef_l1=l1)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -297,8 +303,9 @@ def run_ours(args):
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
     # plain FP32 comparator, same procedure
-    p_ef, p_efu, p_da, _, p_rec = plain
-    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da)
+    p_ef, p_efu, p_da, p_l1, _, p_rec = plain
+    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da,
+                               ef_l1=p_l1)
     plain_qps = args.nq / statistics.median(p_times)
     # one launch per query, FP32 (latency form), on a sample
     ns = min(200, args.nq)
@@ -306,7 +313,7 @@ def run_ours(args):
     for q in range(ns):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, stream=stream)
+        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, ef_l1=p_l1, stream=stream)
         e1.record(stream)
         e1.synchronize()
         t_one.append(e0.elapsed_time(e1) / 1e3)
@@ -316,7 +323,7 @@ def run_ours(args):
     e2e_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, stream=stream)
+        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stream=stream)
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
@@ -330,15 +337,16 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
-            "descend_all": da,
+            "descend_all": da, "ef_l1": l1,
             "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
-            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da,
+            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
                           "recall_at_10": p_rec},
             "plain_f32_per_query_launch_qps": per_query_qps,
             "parallelism": f"replicas{ws}",
         },
         "build_seconds": build_bf16,
+        "build_roofline": _build_roofline(info),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "frac_nominal": achieved / NOMINAL_HBM_GBS,
                      "traffic": traffic, "peak_source": src,
@@ -349,11 +357,11 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        qps, cores, secs = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq)
+        qps, cores, secs = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq, l1=l1, da=da)
         line["cpu_baseline"] = {
             "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
-                       f"{args.cpu_nq} queries answered sequentially on one core, ef={ef}, ef_upper={efu}, "
+                       f"{args.cpu_nq} queries answered sequentially on one core, ef={ef}, ef_upper={efu}, ef_l1={l1}, descend_all={da}, "
                        f"{sum(secs):.1f} s of search"),
         }
     if rank == 0:
@@ -361,6 +369,25 @@ def run_ours(args):
     if ws > 1:
         torch.distributed.destroy_process_group()
     return 0
+
+
+def _build_roofline(info):
+    """Tensor-pipe roofline of the construction distance tiles: the
+    library times its tile launches with CUDA events on the build stream;
+    algorithmic flops = 2 d per valid (row, column) pair, summed over the
+    layers.  The split-BF16 tcgen05 engine executes three BF16 products per
+    pair (hi.hi + lo.hi + hi.lo), reported as executed_frac."""
+    peaks, src = _peaks()
+    if not info.get("tile_seconds"):
+        return None
+    achieved = info["tile_flops"] / info["tile_seconds"] / 1e12
+    peak = peaks.get("bf16_tflops_sustained", peaks["bf16_tflops"])
+    engine = {1: "simt-fp32", 2: "tcgen05-split-bf16"}.get(info.get("tile_engine"), "unknown")
+    mult = 3.0 if engine.startswith("tcgen05") else 1.0
+    return {"bound": "tensor", "kernel": "k_tile_topk_tc" if mult == 3.0 else "k_tile_topk_simt",
+            "engine": engine, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+            "executed_frac": mult * achieved / peak, "tile_seconds": info["tile_seconds"],
+            "algorithmic_flops": info["tile_flops"], "peak_source": f"{src} bf16 sustained"}
 
 
 def _profile_traffic():

@@ -148,6 +148,7 @@ typedef struct {
   int32_t descend_all;        /* with ef_upper > 1: enter each layer at the copies of
                                  all candidates of the layer above instead of the
                                  best one only (default 0)                          */
+  int32_t ef_l1;              /* beam width on layer 1 only; 0 = ef_upper          */
 } henn_search_params;
 
 void henn_search_params_default(henn_search_params* sp);
@@ -188,6 +189,11 @@ typedef struct {
   int64_t uncertified_rows;                /* rows whose tile candidates had to
                                               be recomputed exactly           */
   double build_seconds;                    /* wall time of henn_build         */
+  double tile_seconds;                     /* device time of the distance-tile
+                                              launches (CUDA events)          */
+  double tile_flops;                       /* their algorithmic flops: 2 d per
+                                              valid (row, column) pair        */
+  int32_t tile_engine;                     /* henn_tiles used for layer 0     */
 } henn_index_info;
 
 henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info);

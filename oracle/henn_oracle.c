@@ -451,17 +451,23 @@ int64_t ho_greedy_layer(const float* X, int32_t d, int32_t metric, const int64_t
  * is sorted ascending.  ids maps layer-local indices to points (NULL for
  * layer 0).  visited has one byte per local index. */
 static void beam_layer(const float* X, int32_t d, int32_t metric, const int64_t* ids, const int32_t* adj,
-                       int32_t Mmax, const float* q, int64_t entry, int32_t ef, uint8_t* visited, int64_t size,
-                       pair_t* C, pair_t* W, int64_t* nw_out, int64_t* evals, int64_t* expansions) {
+                       int32_t Mmax, const float* q, const int64_t* entries, int64_t nentries, int32_t ef,
+                       uint8_t* visited, int64_t size, pair_t* C, pair_t* W, int64_t* nw_out, int64_t* evals,
+                       int64_t* expansions) {
   memset(visited, 0, (size_t)size);
   int64_t nc = 0, nw = 0;
-  double de = ho_dist(q, layer_point(X, d, ids, entry), d, metric);
-  ++*evals;
-  visited[entry] = 1;
-  C[nc].d = de;
-  C[nc++].i = entry;
-  W[nw].d = de;
-  W[nw++].i = entry;
+  /* entries: one node, or the copies of the candidates of the layer above
+   * (best first, at most ef of them) */
+  for (int64_t t = 0; t < nentries && t < ef; ++t) {
+    int64_t entry = entries[t];
+    double de = ho_dist(q, layer_point(X, d, ids, entry), d, metric);
+    ++*evals;
+    visited[entry] = 1;
+    C[nc].d = de;
+    C[nc++].i = entry;
+    W[nw].d = de;
+    W[nw++].i = entry;
+  }
   while (nc > 0) {
     int64_t bi = 0;
     for (int64_t j = 1; j < nc; ++j)
@@ -502,15 +508,16 @@ static void beam_layer(const float* X, int32_t d, int32_t metric, const int64_t*
 /* Query (Sec. 2.2 and Alg. 4): random node of the top layer L_L (Alg. 4
  * prints "root (L_0)"; the text of Sec. 2.2 says the root is L_L), a search
  * per layer, each layer entered at the copy of the previous result.  On
- * layers L..1 the search is Alg. 4's GreedySearch when ef_upper <= 1, else
- * the beam of width ef_upper (reading of Sec. 2.2: a set of candidates at
- * each step) whose best node is taken down.  Layer 0 runs the beam of width
+ * layers L..1 the search is Alg. 4's GreedySearch when the layer's width
+ * is <= 1, else the beam of that width (reading of Sec. 2.2: a set of
+ * candidates at each step) whose best node is taken down; the width is
+ * ef_upper, or ef_l1 on layer 1 when ef_l1 > 0.  Layer 0 runs the beam of width
  * max(ef, k) and returns its first k entries. */
 void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nlayers,
                const int64_t* sizes, const int64_t* ids, const int64_t* down, const int32_t* adj,
                int32_t Mmax, const float* Q, int64_t nq, const int32_t* k, const int32_t* ef,
-               int32_t ef_upper, uint64_t seed, const uint64_t* keys, int64_t* out_ids, double* out_d,
-               int32_t out_stride, int64_t* stats) {
+               int32_t ef_upper, int32_t ef_l1, int32_t descend_all, uint64_t seed, const uint64_t* keys,
+               int64_t* out_ids, double* out_d, int32_t out_stride, int64_t* stats) {
   int32_t L = nlayers - 1;
   /* offsets of each layer inside the concatenated arrays */
   int64_t id_off[66], adj_off[66];
@@ -520,6 +527,7 @@ void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nla
   for (int32_t i = 1; i <= L; ++i) id_off[i + 1] = id_off[i] + sizes[i];
   for (int32_t i = 0; i < L; ++i) adj_off[i + 1] = adj_off[i] + sizes[i] * Mmax;
   int32_t ef_max = ef_upper > 1 ? ef_upper : 1;
+  if (ef_l1 > ef_max) ef_max = ef_l1;
   for (int64_t qi = 0; qi < nq; ++qi) {
     int32_t e = ef[qi] > k[qi] ? ef[qi] : k[qi];
     if (e > ef_max) ef_max = e;
@@ -530,6 +538,7 @@ void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nla
   uint8_t* visited = (uint8_t*)malloc((size_t)n);
   pair_t* C = (pair_t*)malloc(sizeof(pair_t) * (size_t)(n + 1));
   pair_t* W = (pair_t*)malloc(sizeof(pair_t) * (size_t)(ef_max + 1));
+  int64_t* seeds = (int64_t*)malloc(sizeof(int64_t) * (size_t)(ef_max + 1));
 #pragma omp for schedule(dynamic, 1)
   for (int64_t qi = 0; qi < nq; ++qi) {
     const float* q = Q + (size_t)qi * d;
@@ -538,26 +547,38 @@ void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nla
     /* S1: random node of the top layer */
     int64_t e = (int64_t)ho_bounded(ho_derive(entry_key, key), (uint64_t)sizes[L]);
     int64_t entry = e;
-    /* S2: layers L..1, then down to the copy in the layer below */
+    /* S2: layers L..1, then down to the copy in the layer below; with
+     * descend_all the layer below is entered at the copies of all the
+     * candidates of a beam, else at the best one */
+    int64_t nseeds = 1;
+    seeds[0] = e;
     for (int32_t i = L; i >= 1; --i) {
       int64_t c;
-      if (ef_upper <= 1) {
+      const int32_t width = (i == 1 && ef_l1 > 0) ? ef_l1 : ef_upper;
+      if (width <= 1) {
         int64_t h = 0, ev = 0;
-        c = ho_greedy_layer(X, d, metric, ids + id_off[i], adj + adj_off[i], Mmax, q, e, &h, &ev);
+        c = ho_greedy_layer(X, d, metric, ids + id_off[i], adj + adj_off[i], Mmax, q, seeds[0], &h, &ev);
         hops_upper += h;
         evals += ev;
+        seeds[0] = down[id_off[i] + c];
+        nseeds = 1;
       } else {
         int64_t ex = 0;
-        beam_layer(X, d, metric, ids + id_off[i], adj + adj_off[i], Mmax, q, e, ef_upper, visited, sizes[i], C,
-                   W, &nw, &evals, &ex);
+        beam_layer(X, d, metric, ids + id_off[i], adj + adj_off[i], Mmax, q, seeds, nseeds, width, visited,
+                   sizes[i], C, W, &nw, &evals, &ex);
         hops_upper += ex;
-        c = W[0].i;
+        if (descend_all) {
+          for (int64_t t = 0; t < nw; ++t) seeds[t] = down[id_off[i] + W[t].i];
+          nseeds = nw;
+        } else {
+          seeds[0] = down[id_off[i] + W[0].i];
+          nseeds = 1;
+        }
       }
-      e = down[id_off[i] + c];
     }
     /* S3: beam of width ef' = max(ef, k) on layer 0 */
     int32_t efq = ef[qi] > k[qi] ? ef[qi] : k[qi];
-    beam_layer(X, d, metric, NULL, adj, Mmax, q, e, efq, visited, n, C, W, &nw, &evals, &expansions);
+    beam_layer(X, d, metric, NULL, adj, Mmax, q, seeds, nseeds, efq, visited, n, C, W, &nw, &evals, &expansions);
     for (int32_t j = 0; j < out_stride; ++j) {
       int in = j < k[qi] && j < nw;
       out_ids[qi * out_stride + j] = in ? W[j].i : -1;
@@ -570,6 +591,7 @@ void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nla
       stats[qi * 4 + 3] = entry;
     }
   }
+  free(seeds);
   free(W);
   free(C);
   free(visited);

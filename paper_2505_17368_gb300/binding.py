@@ -94,6 +94,7 @@ class SearchParams(C.Structure):
         ("hash_bits", C.c_int32),
         ("ef_upper", C.c_int32),
         ("descend_all", C.c_int32),
+        ("ef_l1", C.c_int32),
     ]
 
 
@@ -128,6 +129,9 @@ class IndexInfo(C.Structure):
         ("device_bytes", C.c_int64),
         ("uncertified_rows", C.c_int64),
         ("build_seconds", C.c_double),
+        ("tile_seconds", C.c_double),
+        ("tile_flops", C.c_double),
+        ("tile_engine", C.c_int32),
     ]
 
 
@@ -272,7 +276,8 @@ class Index:
             attempts=[inf.attempts[i] for i in range(Lc + 1)],
             ambiguous_rings=[inf.ambiguous_rings[i] for i in range(Lc + 1)],
             device_bytes=inf.device_bytes, uncertified_rows=inf.uncertified_rows,
-            build_seconds=inf.build_seconds, M=inf.M, Mmax=inf.Mmax,
+            build_seconds=inf.build_seconds, M=inf.M, Mmax=inf.Mmax, tile_seconds=inf.tile_seconds,
+            tile_flops=inf.tile_flops, tile_engine=inf.tile_engine,
         )
 
     def layer(self, i: int) -> dict:
@@ -287,7 +292,7 @@ class Index:
         return dict(ids=ids, down=down, adj=adj, fwd=fwd, fwd_d=fwd_d)
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
-               warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, stream=None, out=None):
+               warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None):
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
@@ -323,6 +328,7 @@ class Index:
         sp.hash_bits = int(hash_bits)
         sp.ef_upper = int(ef_upper)
         sp.descend_all = int(descend_all)
+        sp.ef_l1 = int(ef_l1)
         if keys is not None:
             p, _, kk = _ptr(keys)
             sp.query_keys = p
@@ -382,7 +388,7 @@ class Server:
         return rid.value
 
     def poll(self, rid):
-        nq, k = self._meta[rid]
+        nq, k = self._meta.get(rid, (1, 1))  # unknown ids: the library reports the error
         ids = np.empty((nq, k), np.int64)
         dd = np.empty((nq, k), np.float32)
         done = C.c_int32()
@@ -390,7 +396,7 @@ class Server:
                                       C.c_void_p(dd.ctypes.data)))
         if not done.value:
             return None
-        del self._meta[rid]
+        self._meta.pop(rid, None)
         return ids, dd
 
     def close(self):

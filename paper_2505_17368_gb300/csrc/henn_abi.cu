@@ -109,6 +109,8 @@ struct henn_index {
   int64_t bytes = 0;
   int64_t uncertified = 0;
   double build_seconds = 0.0;
+  double tile_seconds = 0.0, tile_flops = 0.0;
+  int32_t tile_engine = 0;
   int device = 0;
 
   template <typename T>
@@ -275,6 +277,10 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     throw Failure(HENN_ERR_UNSUPPORTED, "tcgen05 tiles need d <= 128 and M <= 16");
   const bool use_tc = tc_ok && p.tiles != HENN_TILES_SIMT;
   double tile_u;
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  CK(cudaEventCreate(&ev0));
+  CK(cudaEventCreate(&ev1));
+  CK(cudaEventRecord(ev0, st));
   if (use_tc) {
     const int32_t dk = (dpad + 63) / 64 * 64;
     void* hi = sc.get<uint16_t>((size_t)s * dk);
@@ -294,6 +300,16 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     CKL("distance tiles");
     tile_u = (dpad + 8.0) * std::ldexp(1.0, -24);
   }
+  CK(cudaEventRecord(ev1, st));
+  CK(cudaEventSynchronize(ev1));
+  float tile_ms = 0.f;
+  CK(cudaEventElapsedTime(&tile_ms, ev0, ev1));
+  cudaEventDestroy(ev0);
+  cudaEventDestroy(ev1);
+  ix->tile_seconds += tile_ms * 1e-3;
+  const double pairs = mode == 0 ? 0.5 * (double)s * (double)(s - 1) : (double)s * (double)(s - 1);
+  ix->tile_flops += pairs * 2.0 * ix->d;
+  if (li == 0) ix->tile_engine = use_tc ? HENN_TILES_TCGEN05 : HENN_TILES_SIMT;
   int32_t* unc = sc.get<int32_t>((size_t)s + 1);
   CK(cudaMemsetAsync(unc, 0, sizeof(int32_t), st));
   launch_rerank_fwd(ix->xw, Ly.ids, s, dpad, ix->metric, inv, cand, KP, M, norms, nmax, tile_u, Ly.fwd, Ly.fwd_d, unc,
@@ -562,7 +578,8 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     require(out_stride >= kmax, "out_stride must be >= max k");
     const int rerank = idx->storage != HENN_F32;
     require(sp.ef_upper >= 0 && sp.ef_upper <= 4096, "ef_upper must be in [0, 4096]");
-    int need = std::max(std::max(kmax, efmax), (int)sp.ef_upper);
+    require(sp.ef_l1 >= 0 && sp.ef_l1 <= 4096, "ef_l1 must be in [0, 4096]");
+    int need = std::max(std::max(kmax, efmax), std::max((int)sp.ef_upper, (int)sp.ef_l1));
     if (rerank) need = std::max(need, std::min(efmax, sp.rerank_mult * kmax));
     int ef_cap = 32;
     while (ef_cap < need) ef_cap <<= 1;
@@ -616,6 +633,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.ef_uniform = sp.ef_uniform;
     a.ef_upper = sp.ef_upper;
     a.descend_all = sp.descend_all;
+    a.ef_l1 = sp.ef_l1;
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.keys = dkeys;
@@ -671,6 +689,9 @@ extern "C" henn_status henn_index_get_info(const henn_index* idx, henn_index_inf
   info->device_bytes = idx->bytes;
   info->uncertified_rows = idx->uncertified;
   info->build_seconds = idx->build_seconds;
+  info->tile_seconds = idx->tile_seconds;
+  info->tile_flops = idx->tile_flops;
+  info->tile_engine = idx->tile_engine;
   return HENN_OK;
 }
 
@@ -798,6 +819,7 @@ struct henn_server {
   float* od = nullptr;
   long long* published = nullptr;
   unsigned long long* taken = nullptr;
+  unsigned long long* last_active = nullptr;
   int* stop = nullptr;
   // mapped host memory
   int* done_h = nullptr;
@@ -822,7 +844,8 @@ struct henn_server {
       cudaStreamSynchronize(cst);
     }
     if (kst) cudaStreamSynchronize(kst);
-    for (void* q : {(void*)qring, (void*)desc, (void*)oids, (void*)od, (void*)published, (void*)taken, (void*)stop})
+    for (void* q : {(void*)qring, (void*)desc, (void*)oids, (void*)od, (void*)published, (void*)taken,
+                    (void*)last_active, (void*)stop})
       if (q) cudaFree(q);
     if (done_h) cudaFreeHost(done_h);
     if (kst) cudaStreamDestroy(kst);
@@ -842,6 +865,9 @@ struct henn_server {
     } else if (head == 0) {
       return;
     }
+    // all ones = "no activity yet": the first warp to look starts the
+    // kernel's idle clock (see k_serve)
+    CK(cudaMemsetAsync(last_active, 0xFF, sizeof(unsigned long long), kst));
     CK(launch_serve(args, warps, grid, kst));
     launched = true;
   }
@@ -906,6 +932,7 @@ extern "C" henn_status henn_serve_create(const henn_index* idx, const henn_serve
     CK(cudaMalloc(&sv->published, sizeof(long long)));
     CK(cudaMalloc(&sv->taken, sizeof(unsigned long long)));
     CK(cudaMalloc(&sv->stop, sizeof(int)));
+    CK(cudaMalloc(&sv->last_active, sizeof(unsigned long long)));
     CK(cudaMemset(sv->published, 0, sizeof(long long)));
     CK(cudaMemset(sv->taken, 0, sizeof(unsigned long long)));
     CK(cudaMemset(sv->stop, 0, sizeof(int)));
@@ -935,6 +962,7 @@ extern "C" henn_status henn_serve_create(const henn_index* idx, const henn_serve
     sv->args.taken = sv->taken;
     sv->args.stop = sv->stop;
     sv->args.done = sv->done_d;
+    sv->args.last_active = sv->last_active;
     sv->args.idle_ns = (long long)p.idle_ms * 1000000ll;
     sv->grid = persistent_grid(idx->device, sv->warps, search_warp_smem(ef_cap, hb, idx->dpad) * sv->warps);
     CK(cudaDeviceSynchronize());

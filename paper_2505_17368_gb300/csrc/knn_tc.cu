@@ -42,7 +42,7 @@ constexpr int B_CHUNK = BN * BK * 2;  // 32 KB
 constexpr int MAX_KC = 2;        // dpad <= 128: at most 2 chunks of 64 per plane
 constexpr int KP = 32;
 constexpr int S_LD = 33;
-constexpr long long kSpinLimit = 1ll << 24;
+constexpr long long kSpinLimit = 1ll << 18;  // x 20 us hint: seconds at most
 
 struct Smem {
   // 1024-byte aligned operand buffers first
@@ -72,18 +72,20 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false on timeout.
+// Bounded wait for the phase with the given parity; false on timeout.  Each
+// try_wait may suspend the thread for up to 20 us (the suspend-time hint)
+// instead of returning at once, so waiting warps do not take issue slots.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
   const uint32_t addr = smem_u32(bar);
   for (long long i = 0; i < kSpinLimit; ++i) {
     uint32_t done;
     asm volatile(
-        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}\n"
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
         : "=r"(done)
-        : "r"(addr), "r"(parity)
+        : "r"(addr), "r"(parity), "r"(20000)
         : "memory");
     if (done) return true;
-    if ((i & 1023) == 1023 && *abort_flag) return false;
+    if ((i & 63) == 63 && *abort_flag) return false;
   }
   return false;
 }
@@ -280,7 +282,13 @@ __global__ void __launch_bounds__(192, 1)
     const int row_l = 32 * sub + lane;
     const int64_t grow = r0 + row_l;
     const float nrow = grow < s ? norms[grow] : 0.f;
-    float thr = __int_as_float(0x7f800000);
+    // valid columns of this row: [0, lim), minus the row itself for kNN
+    const int32_t lim = grow >= s ? 0 : (int32_t)(mode == 0 ? grow : s);
+    const int32_t self = mode == 1 ? (int32_t)grow : -1;
+    const float kInf = __int_as_float(0x7f800000);
+    // the row's threshold with its own norm folded in:
+    // n_row + n_col - 2v <= thr  <=>  n_col - 2v <= thr - n_row
+    float thr_adj = kInf;
     bool ok = true;
     for (int t = 0; t < nt; ++t) {
       const int as = t & 1;
@@ -296,23 +304,27 @@ __global__ void __launch_bounds__(192, 1)
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN + q * 32), v);
         if (c0 >= cend) continue;  // warp-uniform
-        bool surv = false;
+        const float ncol = (c0 + lane < s) ? __ldg(norms + c0 + lane) : 0.f;
+        // columns c0 + j valid for this row, as a bit mask
+        const int32_t rem = lim - (int32_t)c0;
+        unsigned vmask = rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+        const int32_t so = self - (int32_t)c0;
+        if (so >= 0 && so < 32) vmask &= ~(1u << so);
+        unsigned keep = 0;
 #pragma unroll
         for (int j = 0; j < 32; ++j) {
-          const int64_t col = c0 + j;
-          bool valid = grow < s && col < s;
-          if (mode == 0) valid = valid && col < grow;
-          if (mode == 1) valid = valid && col != grow;
-          float dv = __int_as_float(0x7f800000);
-          if (valid) dv = fmaxf(nrow + __ldg(norms + col) - 2.f * v[j], 0.f);
+          const float nc = __shfl_sync(0xffffffffu, ncol, j);
+          const float dv = fmaf(-2.f, v[j], nc);
           v[j] = dv;
-          surv |= valid && dv <= thr;
+          keep |= (dv <= thr_adj) ? (1u << j) : 0u;
         }
-        unsigned m = __ballot_sync(0xffffffffu, surv);
+        keep &= vmask;
+        unsigned m = __ballot_sync(0xffffffffu, keep != 0);
         if (!m) continue;
-        if (surv) {
+        if (keep) {
 #pragma unroll
-          for (int j = 0; j < 32; ++j) sm.s[ew][lane][j] = v[j];
+          for (int j = 0; j < 32; ++j)
+            sm.s[ew][lane][j] = (keep >> j) & 1u ? fmaxf(nrow + v[j], 0.f) : kInf;
         }
         __syncwarp();
         while (m) {
@@ -332,8 +344,11 @@ __global__ void __launch_bounds__(192, 1)
               worst = lst[31];
             }
           }
-          const float nthr = worst == kEmpty ? __int_as_float(0x7f800000) : key_dist(worst);
-          if (lane == i) thr = nthr;
+          const float nthr = worst == kEmpty ? kInf : key_dist(worst);
+          const float nrow_i = __shfl_sync(0xffffffffu, nrow, i);
+          // slightly permissive: rounding of the folded threshold must not
+          // drop a column the certified pool counts on
+          if (lane == i) thr_adj = nthr - nrow_i + 1e-6f * (fabsf(nthr) + fabsf(nrow_i));
         }
         __syncwarp();
       }

@@ -35,6 +35,16 @@
 
 namespace henn {
 
+// Occupancy / memory-parallelism trade-off of the search kernels: blocks
+// of 4 warps guaranteed per SM (caps registers per thread at
+// 65536 / (128 * min_blocks)) and 16-byte chunks in flight per lane.
+#ifndef HENN_SEARCH_MIN_BLOCKS
+#define HENN_SEARCH_MIN_BLOCKS 4
+#endif
+#ifndef HENN_SEARCH_CHUNKS_IN_FLIGHT
+#define HENN_SEARCH_CHUNKS_IN_FLIGHT 8
+#endif
+
 constexpr uint64_t kFlag = 1ull << 31;  // "expanded" bit inside the index word
 constexpr uint64_t kKeyMask = ~kFlag;
 
@@ -108,7 +118,7 @@ __device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const flo
                                            int32_t my_id, int count, const float* __restrict__ qs, int nchunk) {
   const int lane = lane_id();
   constexpr int RP = 32 / G;
-  constexpr int PB0 = 8 / CPL;                     // passes per batch: <= 8 chunks in flight per lane
+  constexpr int PB0 = HENN_SEARCH_CHUNKS_IN_FLIGHT / CPL;  // passes per batch
   constexpr int PB = PB0 < 1 ? 1 : (PB0 > 32 / RP ? 32 / RP : PB0);
   const int g = lane % G, slot_in_pass = lane / G;
   float mine = 0.f;
@@ -209,14 +219,16 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
   __syncwarp();
   int first = 0;
   for (;;) {
-    // next unexpanded entry
-    int pos = -1;
+    // next unexpanded entry (and the one after it, for the prefetch)
+    int pos = -1, after = -1;
     for (int base = first; base < nw; base += 32) {
       int i = base + lane;
       bool un = i < nw && !(W[i] & kFlag);
       unsigned m = __ballot_sync(0xffffffffu, un);
       if (m) {
         pos = base + __ffs(m) - 1;
+        m &= m - 1;
+        if (m) after = base + __ffs(m) - 1;
         break;
       }
     }
@@ -230,15 +242,9 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     int32_t nb = Ly.adj[(int64_t)c * kMmax + lane];
     // the next unexpanded entry is the likely next expansion: pull its
     // adjacency line towards the SM while this one is processed
-    if (lane == 0 && pos + 1 < nw) {
-      for (int j = pos + 1; j < nw && j < pos + 8; ++j) {
-        const uint64_t f = W[j];
-        if (!(f & kFlag)) {
-          const int32_t* nxt = Ly.adj + (int64_t)key_index(f & kKeyMask) * kMmax;
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
-          break;
-        }
-      }
+    if (lane == 0 && after >= 0) {
+      const int32_t* nxt = Ly.adj + (int64_t)key_index(W[after] & kKeyMask) * kMmax;
+      asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
     }
     __syncwarp();
     bool fresh = nb >= 0 && visit(table, HB, nb, evictions);
@@ -400,9 +406,10 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
   int nseed = 0;
   for (int li = a.L; li >= 1; --li) {
     const SearchLayer Ly = a.layers[li];
-    if (a.ef_upper > 1) {
+    const int width = (li == 1 && a.ef_l1 > 0) ? a.ef_l1 : a.ef_upper;
+    if (width > 1) {
       int ex = 0;
-      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(a.ef_upper, EFCAP), W, table, HB, qs, evals, ex,
+      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(width, EFCAP), W, table, HB, qs, evals, ex,
                                 evictions, nseed);
       moves += ex;
       cur = (int32_t)key_index(W[0] & kKeyMask);
@@ -455,7 +462,7 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 }
 
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128, 4) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
   unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * a.warp_smem;
@@ -496,14 +503,13 @@ __device__ __forceinline__ long long ld_acquire_gpu(const long long* p) {
 // items are published and it has ended.  A finished query bumps its
 // request's counter in mapped host memory after a system-scope fence.
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128, 4) k_serve(const ServeArgs s) {
+__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const ServeArgs s) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
   unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * s.base.warp_smem;
   for (;;) {
     long long t = -1;
     if (lane == 0) {
-      const uint64_t t0 = global_ns();
       unsigned backoff = 256;
       for (long long spin = 0; spin < (1ll << 26); ++spin) {
         const long long p = ld_acquire_gpu(s.published);
@@ -511,12 +517,21 @@ __global__ void __launch_bounds__(128, 4) k_serve(const ServeArgs s) {
         if ((long long)tk < p) {
           if (atomicCAS(s.taken, tk, tk + 1ull) == tk) {
             t = (long long)tk;
+            atomicMax(s.last_active, (unsigned long long)global_ns());
             break;
           }
           continue;
         }
         if (*reinterpret_cast<const volatile int*>(s.stop)) break;
-        if (global_ns() - t0 > (uint64_t)s.idle_ns) break;
+        // leave only when the whole kernel has been without work for
+        // idle_ns, so that all warps leave together and the host relaunches
+        // a full grid next time
+        unsigned long long last = *reinterpret_cast<volatile unsigned long long*>(s.last_active);
+        if (last == ~0ull) {  // first look of a fresh launch: start its clock now
+          atomicCAS(s.last_active, ~0ull, (unsigned long long)global_ns());
+          continue;
+        }
+        if (global_ns() > last + (uint64_t)s.idle_ns) break;
         __nanosleep(backoff);
         if (backoff < 8192) backoff <<= 1;
       }

@@ -31,6 +31,7 @@ struct SearchArgs {
   int32_t k_uniform, ef_uniform;
   int32_t ef_upper;           // beam width on layers >= 1 (<= 1: greedy)
   int32_t descend_all;        // enter each layer at all candidates of the layer above
+  int32_t ef_l1;              // beam width on layer 1 (0: ef_upper)
   int32_t ef_cap, hash_bits;  // beam capacity and log2 visited slots per warp
   const uint64_t* keys;
   uint64_t entry_key;  // derive(seed, ENTR)
@@ -60,7 +61,8 @@ struct ServeArgs {
   unsigned long long* taken;     // items taken so far (device)
   const int* stop;               // raised to end the loop (device)
   int* done;                     // per request slot: finished queries (mapped host memory)
-  long long idle_ns;             // a warp leaves after this long without work
+  unsigned long long* last_active;  // globaltimer of the last item taken (device)
+  long long idle_ns;             // the kernel leaves after this long without work
 };
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);

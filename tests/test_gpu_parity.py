@@ -200,12 +200,16 @@ def test_search_parity_uniform10k(uniform10k, ef):
         assert len(set(ids[q].tolist())) == 10
 
 
-def test_search_upper_beam_parity(uniform10k):
+@pytest.mark.parametrize("efu,l1,da", [(16, 0, 0), (16, 4, 0), (16, 0, 1), (32, 8, 1)])
+def test_search_upper_beam_parity(uniform10k, efu, l1, da):
+    """Beams on the upper layers (width ef_upper, ef_l1 on layer 1, and
+    entering each layer at all candidates of the layer above)."""
     X, Q, oidx, gidx = uniform10k
     gi, gd = O.bruteforce(X, Q, 10)
-    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=32, ef_upper=16)
-    oi, od, _ = O.search(oidx, X, Q, k=10, ef=32, ef_upper=16)
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=32, ef_upper=efu, ef_l1=l1, descend_all=da)
+    oi, od, _ = O.search(oidx, X, Q, k=10, ef=32, ef_upper=efu, ef_l1=l1, descend_all=da)
     assert abs(_recall(ids.cpu().numpy(), gi, gd) - _recall(oi, gi, gd)) <= P.RECALL_TOL + 1e-12
+    assert P.returned_distance_error(X, Q, ids.cpu().numpy(), dd.cpu().numpy()) <= P.DIST_RTOL
 
 
 def test_search_host_buffers_equal_device(uniform10k):

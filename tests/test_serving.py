@@ -60,18 +60,25 @@ def test_alone_equals_in_mix(index_and_queries):
     errors = []
 
     def client(part):
+        # submit as the budget allows; while refused, collect finished
+        # requests (ring rows are released only when a request is collected)
         try:
+            outstanding = []
             for (at, b, k, ef) in part:
                 keys = np.arange(at, at + b, dtype=np.uint64)
-                rid = None
-                while rid is None:
+                while True:
                     rid = srv.submit(Q[at:at + b], k=k, ef=ef, keys=keys)
-                    if rid is None:
-                        time.sleep(0.0002)
-                results[at] = (rid, b, k, ef)
-            for at, _, _, _ in part:
-                rid = results[at][0]
-                results[at] = results[at][1:] + _wait(srv, rid)
+                    if rid is not None:
+                        break
+                    for item in list(outstanding):
+                        r = srv.poll(item[0])
+                        if r is not None:
+                            results[item[1]] = item[2:] + r
+                            outstanding.remove(item)
+                    time.sleep(0.0002)
+                outstanding.append((rid, at, b, k, ef))
+            for rid, at, b, k, ef in outstanding:
+                results[at] = (b, k, ef) + _wait(srv, rid)
         except Exception as e:  # pragma: no cover
             errors.append(e)
 
