@@ -230,6 +230,37 @@ henn_status henn_exact_knn(const float* X, int64_t n, int32_t d, const float* Q,
 henn_status henn_quantize_rows(const float* X, int64_t n, int32_t d, int32_t storage, void* out,
                                float* scales, void* stream);
 
+/*
+ * henn_search_host_noalloc -- henn_search for callers that cannot allocate
+ * device memory.  The paper has no counterpart: this is a deployment
+ * variant of the same batched search (same kernel, same results as
+ * henn_search with host buffers and uniform k / ef).
+ *
+ * Who needs it: processes whose device memory belongs to another allocator
+ * (a serving framework's arena, a deep-learning framework's caching pool)
+ * and code that must not allocate while it runs.  henn_search with host
+ * buffers allocates device staging and a work counter on every call; this
+ * call allocates nothing.  Its scratch -- the work counter, the device copy
+ * of the queries and of the results -- is one file-scope device array of
+ * 16 MiB that every GPU loading the library holds until the process exits.
+ *
+ * Q: nq x d float32 rows (host).  out_ids / out_dists: nq x out_stride
+ * (host), filled as henn_search fills them.  k, ef, ef_upper uniform for
+ * the batch.  The index's device must be current.  The call copies in,
+ * searches, copies out and synchronises `stream` before returning.
+ * Limit: 256 + nq*(4 d) + nq*out_stride*12 bytes (each part rounded up to
+ * 256) must fit in 16 MiB, about 26,000 queries at d = 128, k = 10;
+ * larger batches return HENN_ERR_INVALID_ARG with the byte counts (split
+ * the batch).  The first call on each device looks up the array's device
+ * address (cudaGetSymbolAddress); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (from several host threads or streams) race and must be serialised
+ * by the caller.  Errors as henn_search, message in henn_last_error().
+ */
+henn_status henn_search_host_noalloc(const henn_index* idx, const float* Q, int64_t nq, int32_t k, int32_t ef,
+                                     int32_t ef_upper, int64_t* out_ids, float* out_dists, int32_t out_stride,
+                                     void* stream);
+
 /* ---------------------------------------------------------------- serving */
 
 /*

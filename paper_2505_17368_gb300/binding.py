@@ -53,6 +53,7 @@ EXPORTS = [
     "henn_serve_submit",
     "henn_serve_poll",
     "henn_serve_destroy",
+    "henn_search_host_noalloc",
 ]
 
 
@@ -180,6 +181,8 @@ def load(path: str | None = None):
         L.henn_serve_poll.restype = i32
         L.henn_serve_destroy.argtypes = [vp]
         L.henn_serve_destroy.restype = None
+        L.henn_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, i32, vp]
+        L.henn_search_host_noalloc.restype = i32
         L.henn_last_error.argtypes = []
         L.henn_last_error.restype = C.c_char_p
         _lib = L
@@ -354,6 +357,20 @@ class Index:
                              _stream(stream)))
         del keep, kq
         return ids, dists, st
+
+
+def search_host_noalloc(index: "Index", Q, k=10, ef=64, ef_upper=1, out_stride=None, stream=None):
+    """henn_search_host_noalloc: host queries and results, no device
+    allocation (scratch in the library's fixed 16 MiB device array)."""
+    Q = np.ascontiguousarray(Q, dtype=np.float32)
+    nq = Q.shape[0]
+    stride = int(out_stride or k)
+    ids = np.empty((nq, stride), np.int64)
+    dd = np.empty((nq, stride), np.float32)
+    _check(load().henn_search_host_noalloc(index.handle, C.c_void_p(Q.ctypes.data), nq, int(k), int(ef),
+                                           int(ef_upper), C.c_void_p(ids.ctypes.data), C.c_void_p(dd.ctypes.data),
+                                           stride, _stream(stream)))
+    return ids, dd
 
 
 class Server:

@@ -1081,3 +1081,14 @@ extern "C" henn_status henn_serve_poll(henn_server* sv, int64_t request_id, int3
 }
 
 extern "C" void henn_serve_destroy(henn_server* sv) { delete sv; }
+
+// Internal to the library (C++ linkage, not part of the C ABI): the search
+// arguments of an index and the device it lives on, for other translation
+// units that launch the search kernel.
+namespace henn {
+void index_search_args(const henn_index* idx, SearchArgs& a, int* device) {
+  fill_search_args(idx, a);
+  *device = idx->device;
+}
+void set_last_error(const std::string& msg) { g_error = msg; }
+}  // namespace henn
