@@ -39,10 +39,10 @@ namespace henn {
 // of 4 warps guaranteed per SM (caps registers per thread at
 // 65536 / (128 * min_blocks)) and 16-byte chunks in flight per lane.
 #ifndef HENN_SEARCH_MIN_BLOCKS
-#define HENN_SEARCH_MIN_BLOCKS 4
+#define HENN_SEARCH_MIN_BLOCKS 6
 #endif
 #ifndef HENN_SEARCH_CHUNKS_IN_FLIGHT
-#define HENN_SEARCH_CHUNKS_IN_FLIGHT 8
+#define HENN_SEARCH_CHUNKS_IN_FLIGHT 4
 #endif
 
 constexpr uint64_t kFlag = 1ull << 31;  // "expanded" bit inside the index word
