@@ -45,65 +45,72 @@ namespace henn {
 #define HENN_SEARCH_CHUNKS_IN_FLIGHT 4
 #endif
 
+constexpr int kStageBytes = 32 * 8;     // per-warp staging of one neighbour list
 constexpr uint64_t kFlag = 1ull << 31;  // "expanded" bit inside the index word
 constexpr uint64_t kKeyMask = ~kFlag;
 
 // -------------------------------------------------- row distance engine
 
-// 16-byte chunk -> squared-difference partial sum against the query chunk.
+// (a0, a1) += (x0 - q0)^2, (x1 - q1)^2 with paired FP32 operations
+// (sub / fma on f32x2, each element rounded as its scalar form).
+__device__ __forceinline__ void sqdiff2(float x0, float x1, float q0, float q1, float& a0, float& a1) {
+  asm("{\n\t.reg .b64 xx, qq, tt, aa;\n\t"
+      "mov.b64 xx, {%2, %3};\n\t"
+      "mov.b64 qq, {%4, %5};\n\t"
+      "mov.b64 aa, {%0, %1};\n\t"
+      "sub.rn.f32x2 tt, xx, qq;\n\t"
+      "fma.rn.f32x2 aa, tt, tt, aa;\n\t"
+      "mov.b64 {%0, %1}, aa;\n\t}"
+      : "+f"(a0), "+f"(a1)
+      : "f"(x0), "f"(x1), "f"(q0), "f"(q1));
+}
+
+// 16-byte chunk -> squared-difference partial sums (two accumulators, even
+// and odd elements) against the query chunk q (16-byte aligned, shared
+// memory).
 template <typename VT>
 struct Chunk;
 
 template <>
 struct Chunk<float> {
   static constexpr int kElems = 4;
-  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
-    float4 v = *reinterpret_cast<const float4*>(&raw);
-    float t;
-    t = v.x - q[0]; a = fmaf(t, t, a);
-    t = v.y - q[1]; a = fmaf(t, t, a);
-    t = v.z - q[2]; a = fmaf(t, t, a);
-    t = v.w - q[3]; a = fmaf(t, t, a);
-    return a;
+  __device__ __forceinline__ static void acc(const uint4& raw, const float* q, float, float& a0, float& a1) {
+    const float4 v = *reinterpret_cast<const float4*>(&raw);
+    const float4 qv = *reinterpret_cast<const float4*>(q);
+    sqdiff2(v.x, v.y, qv.x, qv.y, a0, a1);
+    sqdiff2(v.z, v.w, qv.z, qv.w, a0, a1);
   }
 };
 
 template <>
 struct Chunk<__nv_bfloat16> {
   static constexpr int kElems = 8;
-  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
+  __device__ __forceinline__ static void acc(const uint4& raw, const float* q, float, float& a0, float& a1) {
     const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+    const float4 q0 = *reinterpret_cast<const float4*>(q);
+    const float4 q1 = *reinterpret_cast<const float4*>(q + 4);
+    const float qq[8] = {q0.x, q0.y, q0.z, q0.w, q1.x, q1.y, q1.z, q1.w};
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      float lo = __uint_as_float(w[i] << 16);
-      float hi = __uint_as_float(w[i] & 0xFFFF0000u);
-      float t = lo - q[2 * i];
-      a = fmaf(t, t, a);
-      t = hi - q[2 * i + 1];
-      a = fmaf(t, t, a);
-    }
-    return a;
+    for (int i = 0; i < 4; ++i)
+      sqdiff2(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xFFFF0000u), qq[2 * i], qq[2 * i + 1], a0, a1);
   }
 };
 
 template <>
 struct Chunk<__nv_fp8_e4m3> {
   static constexpr int kElems = 16;
-  __device__ __forceinline__ static float acc(const uint4& raw, const float* q, float scale, float a) {
+  __device__ __forceinline__ static void acc(const uint4& raw, const float* q, float scale, float& a0, float& a1) {
     const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
+      const float4 qv = *reinterpret_cast<const float4*>(q + 4 * i);
       __half2_raw h0 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFF), __NV_E4M3);
       __half2_raw h1 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
       float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&h0));
       float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&h1));
-      float t;
-      t = f0.x * scale - q[4 * i + 0]; a = fmaf(t, t, a);
-      t = f0.y * scale - q[4 * i + 1]; a = fmaf(t, t, a);
-      t = f1.x * scale - q[4 * i + 2]; a = fmaf(t, t, a);
-      t = f1.y * scale - q[4 * i + 3]; a = fmaf(t, t, a);
+      sqdiff2(f0.x * scale, f0.y * scale, qv.x, qv.y, a0, a1);
+      sqdiff2(f1.x * scale, f1.y * scale, qv.z, qv.w, a0, a1);
     }
-    return a;
   }
 };
 
@@ -144,14 +151,15 @@ __device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const flo
 #pragma unroll
     for (int pb = 0; pb < PB; ++pb) {
       const int slot = (p0 + pb) * RP + slot_in_pass;
-      float a = 0.f;
+      float a0 = 0.f, a1 = 0.f;
       if (slot < count) {
 #pragma unroll
         for (int t = 0; t < CPL; ++t) {
           const int c = g + t * G;
-          if (c < nchunk) a = Chunk<VT>::acc(raw[pb][t], qs + c * Chunk<VT>::kElems, sc[pb], a);
+          if (c < nchunk) Chunk<VT>::acc(raw[pb][t], qs + c * Chunk<VT>::kElems, sc[pb], a0, a1);
         }
       }
+      float a = a0 + a1;
 #pragma unroll
       for (int o = G / 2; o > 0; o >>= 1) a += __shfl_xor_sync(0xffffffffu, a, o);
       const float got = __shfl_sync(0xffffffffu, a, (lane % RP) * G);
@@ -197,9 +205,11 @@ __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t
 // copies of the layer above's candidates) and `entry` is ignored.
 template <typename VT, int G, int CPL>
 __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
-                                    uint64_t* W, int32_t* table, int HB, const float* qs, int& evals,
-                                    int& expansions, int& evictions, int nseed = 0) {
+                                    uint64_t* W, int32_t* table, int HB, uint64_t* stage, const float* qs,
+                                    int& evals, int& expansions, int& evictions, int nseed = 0) {
   const int lane = lane_id();
+  const unsigned below = (1u << lane) - 1u;  // lanes under this one
+  int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
   const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
   for (int s = lane; s < (1 << HB); s += 32) table[s] = -1;
   __syncwarp();
@@ -252,9 +262,9 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     int cnt = __popc(fm);
     if (cnt == 0) continue;
     // compact fresh ids into lanes 0..cnt-1 (lane j gets the j-th fresh one)
-    unsigned src = __fns(fm, 0, lane + 1);
-    int32_t got = __shfl_sync(0xffffffffu, nb, src < 32 ? (int)src : 0);
-    int32_t packed_id = src < 32 ? got : -1;
+    if (fresh) stage32[__popc(fm & below)] = nb;
+    __syncwarp();
+    const int32_t packed_id = lane < cnt ? stage32[lane] : -1;
     float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, packed_id, cnt, qs, nchunk);
     evals += cnt;
     const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
@@ -268,24 +278,27 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     const unsigned cm = __ballot_sync(0xffffffffu, take);
     const int ccnt = __popc(cm);
     if (ccnt == 0) continue;
-    // candidates to lanes 0..ccnt-1; rank among them; position in the new W
-    const unsigned csrc = __fns(cm, 0, lane + 1);
-    const uint64_t moved = shfl64(kk, csrc < 32 ? (int)csrc : 0);
-    const uint64_t cand = lane < ccnt ? moved : kEmpty;
-    int rank = 0;
-    for (int j = 0; j < ccnt; ++j) rank += shfl64(cand, j) < cand;
-    const int cpos = lane < ccnt ? lower_bound_w(W, nw, cand) + rank : 0x7fffffff;
-    int p0 = cpos;
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) p0 = min(p0, __shfl_xor_sync(0xffffffffu, p0, o));
-    // entries at or after p0 shift right by the number of smaller candidates
+    // candidates, compacted, then sorted into stage[0..ccnt); lane j < ccnt
+    // holds the j-th smallest and its position in the new W
     __syncwarp();
+    if (take) stage[__popc(cm & below)] = kk;
+    __syncwarp();
+    uint64_t cand = lane < ccnt ? stage[lane] : kEmpty;
+    int rank = 0;
+    for (int j = 0; j < ccnt; ++j) rank += stage[j] < cand;
+    __syncwarp();
+    if (lane < ccnt) stage[rank] = cand;
+    __syncwarp();
+    cand = lane < ccnt ? stage[lane] : kEmpty;
+    const int cpos = lane < ccnt ? lower_bound_w(W, nw, cand) + lane : 0x7fffffff;
+    const int p0 = __shfl_sync(0xffffffffu, cpos, 0);
+    // entries at or after p0 shift right by the number of smaller candidates
     for (int base = ((nw - 1) >> 5) << 5; base >= (p0 & ~31); base -= 32) {
       const int i = base + lane;
       const bool mv = i < nw && i >= p0;
       const uint64_t w = mv ? W[i] : kEmpty;
       int cl = 0;
-      for (int j = 0; j < ccnt; ++j) cl += shfl64(cand, j) < (w & kKeyMask);
+      for (int j = 0; j < ccnt; ++j) cl += stage[j] < (w & kKeyMask);
       __syncwarp();
       if (mv && i + cl < ef) W[i + cl] = w;
       __syncwarp();
@@ -374,7 +387,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
   const int EFCAP = a.ef_cap, HB = a.hash_bits;
   uint64_t* W = reinterpret_cast<uint64_t*>(my);
   int32_t* table = reinterpret_cast<int32_t*>(my + EFCAP * 8);
-  float* qs = reinterpret_cast<float*>(my + EFCAP * 8 + (4 << HB));
+  uint64_t* stage = reinterpret_cast<uint64_t*>(my + EFCAP * 8 + (4 << HB));
+  float* qs = reinterpret_cast<float*>(my + EFCAP * 8 + (4 << HB) + kStageBytes);
   const int64_t stride = (int64_t)dpad * sizeof(VT);
   const int nchunk = (int)(stride / 16);
 
@@ -409,7 +423,7 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
     const int width = (li == 1 && a.ef_l1 > 0) ? a.ef_l1 : a.ef_upper;
     if (width > 1) {
       int ex = 0;
-      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(width, EFCAP), W, table, HB, qs, evals, ex,
+      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(width, EFCAP), W, table, HB, stage, qs, evals, ex,
                                 evictions, nseed);
       moves += ex;
       cur = (int32_t)key_index(W[0] & kKeyMask);
@@ -448,7 +462,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 
   // S3: layer-0 beam
   const SearchLayer B = a.layers[0];
-  int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, qs, evals, expansions, evictions, nseed);
+  int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals, expansions, evictions,
+                            nseed);
 
   // S4 + output
   finish_query<G32, CPL32>(a, W, nw, k, qs, out_ids, out_d);
@@ -556,7 +571,7 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const Ser
 // ------------------------------------------------------------ dispatch
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad) {
-  size_t b = (size_t)ef_cap * 8 + ((size_t)4 << hash_bits) + (size_t)dpad * 4;
+  size_t b = (size_t)ef_cap * 8 + ((size_t)4 << hash_bits) + kStageBytes + (size_t)dpad * 4;
   return (b + 15) & ~(size_t)15;
 }
 
