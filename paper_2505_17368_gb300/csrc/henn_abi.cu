@@ -67,6 +67,29 @@ struct Scratch {
   }
 };
 
+// Captures the launches that f() enqueues on st into a CUDA graph and runs
+// it once (st must not be the legacy default stream).  Device memory used
+// inside must be allocated before the capture.
+template <class F>
+void run_captured(cudaStream_t st, F&& f) {
+  cudaGraph_t g = nullptr;
+  cudaGraphExec_t ge = nullptr;
+  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+  try {
+    f();
+  } catch (...) {
+    cudaStreamEndCapture(st, &g);
+    if (g) cudaGraphDestroy(g);
+    throw;
+  }
+  CK(cudaStreamEndCapture(st, &g));
+  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
+  if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
+  if (ge) cudaGraphExecDestroy(ge);
+  cudaGraphDestroy(g);
+  CK(e);
+}
+
 int64_t ring_window(double c0, int32_t d, int64_t s, int32_t m) {
   // eps(s) * s with eps from Eq. 1 (natural log), evaluated as
   // ((c0 * d) * log(s)) * 2^m; heavy rings hold floor(eps*s)+1 points.
@@ -192,29 +215,32 @@ int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32
   std::vector<int64_t> h_start(r);
   int32_t ambiguous = 0;
   for (int32_t a = 0; a < p.max_attempts; ++a) {
-    CK(cudaMemsetAsync(flags, 0, (size_t)s, st));
-    LayerSampleArgs la;
-    la.base = derive(derive(derive(ix->seed, HENN_TAG_SAMPLE), (uint64_t)layer), (uint64_t)a);
-    la.s = s;
-    la.t = t;
-    la.flags = flags;
-    launch_sample(la, st);
-    launch_compact(flags, s, prev_ids, tile_buf, d_total, pos, ids, st);
-    CKL("sample/compact");
+    // one attempt of Alg. 2 as one captured graph: draws, compaction and,
+    // when heavy rings exist, the r ring checks; then one read-back
+    const uint64_t base = derive(derive(derive(ix->seed, HENN_TAG_SAMPLE), (uint64_t)layer), (uint64_t)a);
+    const uint64_t bc = derive(derive(derive(ix->seed, HENN_TAG_RCENTRE), (uint64_t)layer), (uint64_t)a);
+    const uint64_t bs = derive(derive(derive(ix->seed, HENN_TAG_RSTART), (uint64_t)layer), (uint64_t)a);
+    run_captured(st, [&] {
+      CK(cudaMemsetAsync(flags, 0, (size_t)s, st));
+      LayerSampleArgs la;
+      la.base = base;
+      la.s = s;
+      la.t = t;
+      la.flags = flags;
+      launch_sample(la, st);
+      launch_compact(flags, s, prev_ids, tile_buf, d_total, pos, ids, st);
+      CKL("sample/compact");
+      if (w <= s) {
+        launch_ring_params(bc, bs, r, s, s - w + 1, centre, start, st);
+        launch_ring_dist(ix->x32, ix->dpad, prev_ids, s, centre, r, ix->metric, ix->inv_norm, D, st);
+        launch_ring_select_decide(D, s, start, w, r, pos, d_total, er, ea, lo, hi, status, st);
+        CKL("ring checks");
+      }
+    });
     int64_t count = 0;
     CK(cudaMemcpyAsync(&count, d_total, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     bool pass = true;
     if (w <= s) {
-      uint64_t bc = derive(derive(derive(ix->seed, HENN_TAG_RCENTRE), (uint64_t)layer), (uint64_t)a);
-      uint64_t bs = derive(derive(derive(ix->seed, HENN_TAG_RSTART), (uint64_t)layer), (uint64_t)a);
-      launch_ring_params(bc, bs, r, s, s - w + 1, centre, start, st);
-      launch_ring_dist(ix->x32, ix->dpad, prev_ids, s, centre, r, ix->metric, ix->inv_norm, D, st);
-      CKL("ring distances");
-      // the net positions are known on the device only after compaction;
-      // the decision kernel reads them there (count read below)
-      CK(cudaStreamSynchronize(st));
-      launch_ring_select_decide(D, s, start, w, r, pos, count, er, ea, lo, hi, status, st);
-      CKL("ring select/decide");
       CK(cudaMemcpyAsync(h_status.data(), status, sizeof(int32_t) * r, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
       for (int32_t q = 0; q < r; ++q)
@@ -323,38 +349,43 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     CKL("exact rows");
     ix->uncertified += nunc;
   }
-  // edge rule
+  // edge rule and traversal copy (layer order) as one captured graph;
+  // every buffer is allocated before the capture
   int32_t* cnt = sc.get<int32_t>(s);
   int32_t* fill = sc.get<int32_t>(s);
   int64_t* off = sc.get<int64_t>((size_t)s + 1);
   int64_t* tiles = sc.get<int64_t>((size_t)scan_tiles(s) + 1);
   uint64_t* rev = sc.get<uint64_t>((size_t)s * M);
-  CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * s, st));
-  CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * s, st));
-  launch_rev_count(Ly.fwd, s, M, cnt, st);
-  launch_offsets(cnt, s, tiles, off, st);
-  launch_rev_fill(Ly.fwd, Ly.fwd_d, s, M, off, fill, rev, st);
-  launch_select_adj(Ly.fwd, Ly.fwd_d, s, M, off, rev, ix->graph, Ly.adj, st);
-  CKL("edge rule");
-  // traversal copy of this layer, layer order
-  const float* src = ix->xw;
-  if (li > 0) {
-    float* g = (ix->storage == HENN_F32) ? ix->alloc<float>((size_t)s * dpad) : sc.get<float>((size_t)s * dpad);
-    launch_gather_rows32(ix->xw, Ly.ids, s, dpad, g, st);
-    src = g;
-    if (ix->storage == HENN_F32) Ly.vec = g;
-  } else if (ix->storage == HENN_F32) {
-    Ly.vec = ix->xw;
-  }
-  if (ix->storage == HENN_BF16) {
+  float* gathered = nullptr;
+  if (li > 0)
+    gathered = (ix->storage == HENN_F32) ? ix->alloc<float>((size_t)s * dpad) : sc.get<float>((size_t)s * dpad);
+  if (ix->storage == HENN_F32) {
+    Ly.vec = li > 0 ? (void*)gathered : (void*)ix->xw;
+  } else if (ix->storage == HENN_BF16) {
     Ly.vec = ix->alloc<uint16_t>((size_t)s * dpad);
-    launch_quantize(src, s, dpad, dpad, dpad, HENN_BF16, Ly.vec, nullptr, st);
-  } else if (ix->storage == HENN_FP8E4M3) {
+  } else {
     Ly.vec = ix->alloc<uint8_t>((size_t)s * dpad);
     Ly.vscale = ix->alloc<float>(s);
-    launch_quantize(src, s, dpad, dpad, dpad, HENN_FP8E4M3, Ly.vec, Ly.vscale, st);
   }
-  CKL("traversal copy");
+  run_captured(st, [&] {
+    CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * s, st));
+    CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * s, st));
+    launch_rev_count(Ly.fwd, s, M, cnt, st);
+    launch_offsets(cnt, s, tiles, off, st);
+    launch_rev_fill(Ly.fwd, Ly.fwd_d, s, M, off, fill, rev, st);
+    launch_select_adj(Ly.fwd, Ly.fwd_d, s, M, off, rev, ix->graph, Ly.adj, st);
+    CKL("edge rule");
+    const float* src = ix->xw;
+    if (li > 0) {
+      launch_gather_rows32(ix->xw, Ly.ids, s, dpad, gathered, st);
+      src = gathered;
+    }
+    if (ix->storage == HENN_BF16)
+      launch_quantize(src, s, dpad, dpad, dpad, HENN_BF16, Ly.vec, nullptr, st);
+    else if (ix->storage == HENN_FP8E4M3)
+      launch_quantize(src, s, dpad, dpad, dpad, HENN_FP8E4M3, Ly.vec, Ly.vscale, st);
+    CKL("traversal copy");
+  });
   CK(cudaStreamSynchronize(st));
 }
 
@@ -387,7 +418,22 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     require(p.max_attempts >= 1 && p.max_attempts <= 100000, "max_attempts");
     require(p.M >= 1 && p.M <= 32, "M must be in [1, 32]");
     require(p.Mmax == 32, "Mmax must be 32");
-    cudaStream_t st = (cudaStream_t)stream;
+    // The build runs on its own non-blocking stream (the legacy default
+    // stream cannot be captured into graphs), after the caller's stream
+    // has produced X; it synchronises before returning.
+    cudaStream_t ust = (cudaStream_t)stream;
+    CK(cudaStreamSynchronize(ust));
+    struct OwnStream {
+      cudaStream_t s = nullptr;
+      ~OwnStream() {
+        if (s) {
+          cudaStreamSynchronize(s);
+          cudaStreamDestroy(s);
+        }
+      }
+    } own;
+    CK(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+    cudaStream_t st = own.s;
 
     ix = new henn_index();
     CK(cudaGetDevice(&ix->device));

@@ -32,7 +32,7 @@ void launch_ring_dist(const float* x32, int32_t dpad, const int32_t* prev_ids, i
                       const int32_t* centre, int32_t r, int32_t metric, const float* inv_norm, float* D,
                       cudaStream_t st);
 void launch_ring_select_decide(const float* D, int64_t s, const int64_t* start, int64_t w, int32_t r,
-                               const int32_t* net_pos, int64_t nnet, double er, double ea, float* lo,
+                               const int32_t* net_pos, const int64_t* nnet_dev, double er, double ea, float* lo,
                                float* hi, int32_t* status, cudaStream_t st);
 void launch_ring_recheck(const float* x32, int32_t d, int32_t dpad, const int32_t* prev_ids, int64_t s,
                          int64_t centre_pos, int64_t a0, int64_t w, int32_t metric, const int32_t* net_pos,

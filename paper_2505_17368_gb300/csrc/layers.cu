@@ -310,9 +310,10 @@ __device__ __forceinline__ double finv(double y, double er, double ea) { return 
 __device__ __forceinline__ double ginv(double y, double er, double ea) { return (y + ea) / (1.0 - er); }
 
 __global__ void k_ring_decide(const float* __restrict__ D, int64_t s, const int32_t* __restrict__ net_pos,
-                              int64_t nnet, const float* __restrict__ lo, const float* __restrict__ hi,
-                              double er, double ea, int32_t* __restrict__ status) {
+                              const int64_t* __restrict__ nnet_ptr, const float* __restrict__ lo,
+                              const float* __restrict__ hi, double er, double ea, int32_t* __restrict__ status) {
   const int q = blockIdx.x;
+  const int64_t nnet = *nnet_ptr;  // written by the compaction on the device
   __shared__ int any_in, any_amb;
   if (threadIdx.x == 0) any_in = any_amb = 0;
   __syncthreads();
@@ -419,10 +420,10 @@ void launch_ring_dist(const float* x32, int32_t dpad, const int32_t* prev_ids, i
 }
 
 void launch_ring_select_decide(const float* D, int64_t s, const int64_t* start, int64_t w, int32_t r,
-                               const int32_t* net_pos, int64_t nnet, double er, double ea, float* lo,
+                               const int32_t* net_pos, const int64_t* nnet_dev, double er, double ea, float* lo,
                                float* hi, int32_t* status, cudaStream_t st) {
   k_ring_select32<<<r, 512, 0, st>>>(D, s, start, w, lo, hi);
-  k_ring_decide<<<r, 256, 0, st>>>(D, s, net_pos, nnet, lo, hi, er, ea, status);
+  k_ring_decide<<<r, 256, 0, st>>>(D, s, net_pos, nnet_dev, lo, hi, er, ea, status);
 }
 
 void launch_ring_recheck(const float* x32, int32_t d, int32_t dpad, const int32_t* prev_ids, int64_t s,
