@@ -160,7 +160,8 @@ def _recall(found, gt):
     return float(np.mean(hits)) / gt.shape[1]
 
 
-def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0):
+def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0, shape=None):
+    shape = shape or {}
     import torch
 
     H = sys.modules["paper_2505_17368_gb300"]
@@ -169,7 +170,7 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
     dd = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
     for _ in range(warmup):
         index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
-                     out=(ids, dd))
+                     out=(ids, dd), **shape)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
@@ -179,7 +180,7 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
-                     out=(ids, dd))
+                     out=(ids, dd), **shape)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -282,8 +283,12 @@ def run_ours(args):
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
     ef, efu, da, l1, _, rec = chosen
+    # ---- launch shape (warps per block, visited-table size) by the autotuner
+    from paper_2505_17368_gb300 import autotune
+
+    shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, use_cache=False)
     # ---- algorithmic bytes per launch from the kernel's own counters
-    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True)
+    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
     R = min(4 * K, ef)
@@ -294,7 +299,7 @@ def run_ours(args):
     torch.cuda.synchronize()
     with ClockSampler(_smi_id(dev, local)) as clk:
         times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da,
-                                   ef_l1=l1)
+                                   ef_l1=l1, shape=shape)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -323,7 +328,7 @@ def run_ours(args):
     e2e_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stream=stream)
+        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stream=stream, **shape)
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
@@ -337,7 +342,7 @@ def run_ours(args):
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
-            "descend_all": da, "ef_l1": l1,
+            "descend_all": da, "ef_l1": l1, "launch_shape": shape,
             "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
             "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,

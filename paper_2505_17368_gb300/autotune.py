@@ -1,0 +1,107 @@
+"""Launch-shape autotuner for henn_search.
+
+For an index, a batch size and a beam configuration, times henn_search over
+a small grid of launch shapes -- warps (queries in flight) per block and the
+size of the per-query visited table -- and keeps the fastest.  Results are
+cached in a JSON file keyed by (n, d, storage, batch bucket, k, ef,
+ef_upper, ef_l1, descend_all), so a process pays the sweep once per shape.
+Neither knob changes results: the visited table may forget entries without
+changing the answer, and queries are independent of the grid.
+
+    shape = autotune.tune(index, Q_device, k=10, ef=64, ef_upper=64)
+    ids, d, _ = index.search(Q_device, k=10, ef=64, ef_upper=64, **shape)
+"""
+from __future__ import annotations
+
+import json
+import math
+import os
+import threading
+
+_LOCK = threading.Lock()
+DEFAULT_CACHE = os.path.join(os.path.expanduser("~"), ".cache", "henn_gb300_autotune.json")
+
+
+def _beam_cap(k, ef, ef_upper, ef_l1):
+    need = max(k, ef, ef_upper, ef_l1)
+    cap = 32
+    while cap < need:
+        cap <<= 1
+    return cap
+
+
+def _default_hash_bits(cap):
+    hb = 10
+    while hb < 13 and (1 << hb) < cap * 16:
+        hb += 1
+    return hb
+
+
+def candidates(k, ef, ef_upper=1, ef_l1=0):
+    hb = _default_hash_bits(_beam_cap(k, ef, ef_upper, ef_l1))
+    out = []
+    for w in (4, 2):
+        for h in (hb - 1, hb, hb + 1):
+            if 8 <= h <= 15:
+                out.append({"warps_per_block": w, "hash_bits": h})
+    return out
+
+
+def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all):
+    bucket = 1 << max(0, int(math.ceil(math.log2(max(nq, 1)))))
+    return f"n={index.n},d={index.d},s={index.storage},b={bucket},k={k},ef={ef},eu={ef_upper},l1={ef_l1},da={descend_all}"
+
+
+def _load(path):
+    try:
+        with open(path) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats):
+    import torch
+
+    def run(shape):
+        index.search(Q, k=k, ef=ef, ef_upper=ef_upper, ef_l1=ef_l1, descend_all=descend_all, **shape)
+        torch.cuda.synchronize()
+        ts = []
+        for _ in range(repeats):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            index.search(Q, k=k, ef=ef, ef_upper=ef_upper, ef_l1=ef_l1, descend_all=descend_all, **shape)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1))
+        return min(ts)
+
+    return run
+
+
+def tune(index, Q, k=10, ef=64, ef_upper=1, ef_l1=0, descend_all=0, repeats=3, cache_path=DEFAULT_CACHE,
+         use_cache=True, timer=None):
+    """Fastest launch shape for this (index, batch, beam); Q is a CUDA
+    tensor.  `timer(shape) -> ms` replaces the CUDA-event timing (tests)."""
+    key = _key(index, Q.shape[0], k, ef, ef_upper, ef_l1, descend_all)
+    with _LOCK:
+        cache = _load(cache_path) if use_cache else {}
+        if key in cache:
+            return dict(cache[key]["shape"])
+    run = timer or _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats)
+    best, best_t, table = None, float("inf"), []
+    for shape in candidates(k, ef, ef_upper, ef_l1):
+        t = run(shape)
+        table.append((shape, t))
+        if t < best_t:
+            best, best_t = shape, t
+    if use_cache:
+        with _LOCK:
+            cache = _load(cache_path)
+            cache[key] = {"shape": best, "ms": best_t, "tried": [{"shape": s, "ms": t} for s, t in table]}
+            os.makedirs(os.path.dirname(cache_path), exist_ok=True)
+            tmp = cache_path + f".{os.getpid()}.tmp"
+            with open(tmp, "w") as f:
+                json.dump(cache, f, indent=1, sort_keys=True)
+            os.replace(tmp, cache_path)
+    return dict(best)

@@ -1,0 +1,43 @@
+"""Host logic of the launch-shape autotuner (no GPU: a fake timer)."""
+from __future__ import annotations
+
+import json
+
+import numpy as np
+
+from paper_2505_17368_gb300 import autotune
+
+
+class _FakeIndex:
+    n, d, storage = 1000, 32, 1
+
+
+def test_candidates_follow_the_beam():
+    c = autotune.candidates(10, 64)
+    assert {"warps_per_block": 4, "hash_bits": 10} in c
+    assert all(8 <= s["hash_bits"] <= 15 for s in c)
+    big = autotune.candidates(10, 512, ef_upper=64)
+    assert max(s["hash_bits"] for s in big) > max(s["hash_bits"] for s in c)
+
+
+def test_tune_picks_fastest_and_caches(tmp_path):
+    Q = np.zeros((3000, 32), np.float32)
+    calls = []
+
+    def timer(shape):
+        calls.append(shape)
+        return 1.0 + 0.1 * shape["hash_bits"] - (0.5 if shape["warps_per_block"] == 2 else 0.0)
+
+    path = str(tmp_path / "cache.json")
+    best = autotune.tune(_FakeIndex(), Q, k=10, ef=64, cache_path=path, timer=timer)
+    assert best["warps_per_block"] == 2
+    assert best["hash_bits"] == min(s["hash_bits"] for s in autotune.candidates(10, 64))
+    n_first = len(calls)
+    again = autotune.tune(_FakeIndex(), Q, k=10, ef=64, cache_path=path, timer=timer)
+    assert again == best and len(calls) == n_first  # served from the cache
+    data = json.load(open(path))
+    (entry,) = data.values()
+    assert entry["shape"] == best and len(entry["tried"]) == n_first
+    # another batch bucket is tuned separately
+    autotune.tune(_FakeIndex(), np.zeros((9000, 32), np.float32), k=10, ef=64, cache_path=path, timer=timer)
+    assert len(json.load(open(path))) == 2
