@@ -11,6 +11,8 @@
 #include <algorithm>
 #include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <deque>
 #include <exception>
@@ -64,6 +66,30 @@ struct Scratch {
   }
   ~Scratch() {
     for (void* p : ptrs) cudaFreeAsync(p, st);
+  }
+};
+
+// Build tracing: with HENN_TRACE=1 in the environment, henn_build prints the
+// wall time of each step to stderr, measured after synchronising the build
+// stream (so the steps no longer overlap while tracing), and the number of
+// rows that needed the exact recompute.
+struct BuildTrace {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::chrono::steady_clock::time_point t;
+  explicit BuildTrace(cudaStream_t s) : st(s), t(std::chrono::steady_clock::now()) {
+    const char* e = std::getenv("HENN_TRACE");
+    on = e && std::atoi(e) > 0;
+  }
+  void mark(const char* what, int32_t layer, int64_t count = -1) {
+    if (!on) return;
+    cudaStreamSynchronize(st);
+    auto n = std::chrono::steady_clock::now();
+    std::fprintf(stderr, "[henn build] layer %d %-22s %9.3f ms", layer, what,
+                 std::chrono::duration<double, std::milli>(n - t).count());
+    if (count >= 0) std::fprintf(stderr, "  (%lld)", (long long)count);
+    std::fprintf(stderr, "\n");
+    t = n;
   }
 };
 
@@ -277,7 +303,7 @@ int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32
   return -1;
 }
 
-void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, cudaStream_t st) {
+void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, cudaStream_t st, BuildTrace& tr) {
   LayerDev& Ly = ix->layers[li];
   const int64_t s = Ly.size;
   const int32_t dpad = ix->dpad, M = ix->M;
@@ -294,6 +320,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
   CKL("order/gather");
   float* nmax = sc.get<float>(1);
   launch_max_nonneg(norms, s, nmax, st);
+  tr.mark("mean/order/norms", li);
   // tiles + top-KP
   const int32_t KP = M <= 16 ? 32 : (M <= 48 ? 64 : 128);
   uint64_t* cand = sc.get<uint64_t>((size_t)s * KP);
@@ -336,6 +363,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
   const double pairs = mode == 0 ? 0.5 * (double)s * (double)(s - 1) : (double)s * (double)(s - 1);
   ix->tile_flops += pairs * 2.0 * ix->d;
   if (li == 0) ix->tile_engine = use_tc ? HENN_TILES_TCGEN05 : HENN_TILES_SIMT;
+  tr.mark("tiles + top-k", li);
   int32_t* unc = sc.get<int32_t>((size_t)s + 1);
   CK(cudaMemsetAsync(unc, 0, sizeof(int32_t), st));
   launch_rerank_fwd(ix->xw, Ly.ids, s, dpad, ix->metric, inv, cand, KP, M, norms, nmax, tile_u, Ly.fwd, Ly.fwd_d, unc,
@@ -349,6 +377,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     CKL("exact rows");
     ix->uncertified += nunc;
   }
+  tr.mark("rerank/certify", li, nunc);
   // edge rule and traversal copy (layer order) as one captured graph;
   // every buffer is allocated before the capture
   int32_t* cnt = sc.get<int32_t>(s);
@@ -387,6 +416,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     CKL("traversal copy");
   });
   CK(cudaStreamSynchronize(st));
+  tr.mark("edge rule + copy", li);
 }
 
 }  // namespace
@@ -434,6 +464,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     } own;
     CK(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
     cudaStream_t st = own.s;
+    BuildTrace tr(st);
 
     ix = new henn_index();
     CK(cudaGetDevice(&ix->device));
@@ -462,6 +493,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
       CKL("normalise");
     }
 
+    tr.mark("input copy", 0);
     // ---- layer membership (Alg. 1 + Alg. 2)
     ix->layers.push_back(LayerDev());
     ix->layers[0].size = n;
@@ -495,6 +527,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
         ix->layers.push_back(Ly);
         ix->attempts.push_back(a);
         ix->ambiguous.push_back(amb);
+        tr.mark("membership", layer);
       }
       CK(cudaStreamSynchronize(st));
     }
@@ -506,7 +539,8 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
       Ly.adj = ix->alloc<int32_t>((size_t)Ly.size * kMmax);
       Ly.fwd = ix->alloc<int32_t>((size_t)Ly.size * ix->M);
       Ly.fwd_d = ix->alloc<float>((size_t)Ly.size * ix->M);
-      build_layer_graph(ix, p, li, st);
+      build_layer_graph(ix, p, li, st, tr);
+      tr.mark("scratch release", li);
     }
 
     // ---- search-side layer table

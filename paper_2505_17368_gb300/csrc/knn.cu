@@ -247,12 +247,22 @@ __global__ void k_rerank_fwd(const float* __restrict__ xw, const int32_t* __rest
     uint64_t mkey = shfl64(list.v[(M - 1) >> 5], (M - 1) & 31);
     if (count == KP && uncertified) {
       double thr = (double)key_dist(thr_key);
-      double beta = tile_u * 4.0 * ((double)norms[r] + (double)*norm_max) + 1e-30;
       double dm = (mkey == kEmpty) ? 1e300 : (double)key_dist(mkey);
       // exact distances here are of raw vectors; tile distances of centred
       // ones: identical in exact arithmetic.  Angular: tile values are 2x.
       if (metric == HENN_ANGULAR) dm *= 2.0;
-      if (!(thr - beta > dm * (1.0 + 1e-6))) {
+      // relative error bound of the exact FP32 distances (dpad / 32 FMA
+      // steps per lane, five butterfly additions), doubled
+      const double slack = (dpad / 32 + 8) * 0x1p-23;
+      // Only columns whose true distance can reach dm matter, and those lie
+      // within sqrt(dm) of this row, so their centred norm is at most
+      // (|x_r| + sqrt(dm))^2 (widened for the centring rounding); the tile
+      // error bound needs the column norm only up to that cap.
+      const double nr = (double)norms[r];
+      const double rad = sqrt(nr) * (1.0 + 1e-3) + sqrt(dm * (1.0 + 2.0 * slack)) * (1.0 + 1e-3);
+      const double nc = fmin((double)*norm_max, rad * rad);
+      const double beta = tile_u * 4.0 * (nr + nc) + 1e-30;
+      if (!(thr - beta > dm * (1.0 + slack))) {
         if (lane == 0) {
           int at = atomicAdd(uncertified, 1);
           uncertified[1 + at] = (int32_t)r;
@@ -294,64 +304,180 @@ void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t d
   }
 }
 
-// Exact forward list of flagged rows: every valid column, exact FP32.
-template <int KM>
-__global__ void k_exact_rows(const float* __restrict__ xw, const int32_t* __restrict__ ids, int64_t s, int32_t dpad,
-                             int32_t metric, const int32_t* __restrict__ inv, int32_t mode,
-                             const int32_t* __restrict__ rows, int32_t nrows, int32_t M, int32_t* __restrict__ fwd,
-                             float* __restrict__ fwd_d) {
+// Exact forward lists of flagged rows, batched: a block takes RT flagged
+// rows (kept in shared memory) and streams every candidate column once for
+// all of them, so the columns are read once per RT rows instead of once per
+// row.  Each distance is formed exactly as warp_exact_dist forms it (lane
+// l sums the squared differences of elements l, l+32, ... in order with
+// FMA, then the xor butterfly over the 32 lanes), so a flagged row gets the
+// list the certified path would give it.  Column validity: mode 0 (causal,
+// NSW) columns before the row in insertion order, mode 1 (kNN) all other
+// columns.  KD = dpad / 32 when dpad <= 128 (the loads of CPG columns are
+// issued together), else 0 (any dpad, one column at a time).
+template <int KM, int RT, int KD>
+__global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__ xw, const int32_t* __restrict__ ids,
+                                                       int64_t s, int32_t dpad, int32_t metric,
+                                                       const int32_t* __restrict__ inv, int32_t mode,
+                                                       const int32_t* __restrict__ rows, int32_t nrows, int32_t M,
+                                                       int32_t* __restrict__ fwd, float* __restrict__ fwd_d) {
+  constexpr int CPG = KD > 0 ? 4 : 1;  // columns whose loads are in flight together
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  float* qrows = reinterpret_cast<float*>(smem_raw);                   // RT x dpad
+  uint64_t* merged = reinterpret_cast<uint64_t*>(qrows + RT * dpad);  // warps x RT x KM
+  __shared__ int64_t rank_of[RT];
   const int lane = threadIdx.x & 31;
+  const int w = threadIdx.x >> 5;
   const int warps = blockDim.x >> 5;
-  for (int i = blockIdx.x; i < nrows; i += gridDim.x) {
-    const int64_t r = rows[i];
-    const int64_t j = inv[r];
-    const float* xj = xw + (ids ? (int64_t)ids[j] : j) * dpad;
-    __shared__ uint64_t best[8][KM];
-    WarpList<KM> list;
-    list.clear();
-    const int w = threadIdx.x >> 5;
-    int64_t cend = mode == 0 ? r : s;
-    for (int64_t c = w; c < cend; c += warps) {
-      if (mode != 0 && c == r) continue;
-      int64_t qj = inv[c];
-      float dv = warp_exact_dist(xj, xw + (ids ? (int64_t)ids[qj] : qj) * dpad, dpad, metric);
-      uint64_t key = pack(dv, (uint32_t)qj);
-      if (key < list.worst()) list.insert(key);
+  const int64_t t0 = (int64_t)blockIdx.x * RT;
+  for (int i = 0; i < RT; ++i) {
+    const int64_t r = t0 + i < nrows ? (int64_t)rows[t0 + i] : -1;
+    if (threadIdx.x == 0) rank_of[i] = r;
+    if (r >= 0) {
+      const int64_t j = inv[r];
+      const float* src = xw + (ids ? (int64_t)ids[j] : j) * dpad;
+      for (int k = threadIdx.x; k < dpad; k += blockDim.x) qrows[i * dpad + k] = src[k];
     }
+  }
+  __syncthreads();
+  int64_t rr[RT];
+  int64_t cend = 0;
 #pragma unroll
-    for (int q = 0; q < KM / 32; ++q) best[w][q * 32 + lane] = list.v[q];
-    __syncthreads();
-    if (w == 0) {
-      WarpList<KM> all;
-      all.clear();
-      for (int o = 0; o < warps; ++o)
-        for (int c = 0; c < KM; ++c) {
-          uint64_t key = best[o][c];
-          if (key < all.worst()) all.insert(key);
+  for (int i = 0; i < RT; ++i) {
+    rr[i] = rank_of[i];
+    if (rr[i] >= 0) cend = max(cend, mode == 0 ? rr[i] : s);
+  }
+  WarpList<KM> lists[RT];
+#pragma unroll
+  for (int i = 0; i < RT; ++i) lists[i].clear();
+  const int kd = KD > 0 ? KD : dpad / 32;
+
+  for (int64_t c0 = (int64_t)w * 32; c0 < cend; c0 += (int64_t)warps * 32) {
+    // this chunk's 32 columns: lane cc owns column c0 + cc
+    const int64_t mycol = c0 + lane;
+    int32_t myq = -1;
+    const float* myrow = xw;
+    if (mycol < cend) {
+      myq = inv[mycol];
+      myrow = xw + (int64_t)(ids ? ids[myq] : myq) * dpad;
+    }
+    float dist[RT];
+#pragma unroll
+    for (int i = 0; i < RT; ++i) dist[i] = 0.f;
+    const int ncols = (int)min((int64_t)32, cend - c0);
+    for (int cc = 0; cc < ncols; cc += CPG) {
+      if constexpr (KD > 0) {
+        float v[CPG][KD];
+#pragma unroll
+        for (int g = 0; g < CPG; ++g) {
+          const float* p = reinterpret_cast<const float*>(
+              __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(myrow), (cc + g) & 31));
+          const bool ok = cc + g < ncols;
+#pragma unroll
+          for (int k = 0; k < KD; ++k) v[g][k] = ok ? __ldg(p + lane + 32 * k) : 0.f;
         }
 #pragma unroll
-      for (int q = 0; q < KM / 32; ++q) {
-        int g = q * 32 + lane;
-        if (g < M) {
-          uint64_t key = all.v[q];
-          fwd[j * M + g] = key == kEmpty ? -1 : (int32_t)key_index(key);
-          fwd_d[j * M + g] = key == kEmpty ? __int_as_float(0x7f800000) : key_dist(key);
+        for (int i = 0; i < RT; ++i) {
+          float q[KD];
+#pragma unroll
+          for (int k = 0; k < KD; ++k) q[k] = qrows[i * dpad + lane + 32 * k];
+#pragma unroll
+          for (int g = 0; g < CPG; ++g) {
+            float acc = 0.f;
+#pragma unroll
+            for (int k = 0; k < KD; ++k) {
+              const float t = q[k] - v[g][k];
+              acc = fmaf(t, t, acc);
+            }
+#pragma unroll
+            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (lane == cc + g) dist[i] = acc;
+          }
+        }
+      } else {
+        const float* p = reinterpret_cast<const float*>(
+            __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(myrow), cc & 31));
+#pragma unroll 1
+        for (int i = 0; i < RT; ++i) {
+          float acc = 0.f;
+          for (int k = 0; k < kd; ++k) {
+            const float t = qrows[i * dpad + lane + 32 * k] - __ldg(p + lane + 32 * k);
+            acc = fmaf(t, t, acc);
+          }
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+          if (lane == cc) dist[i] = acc;
         }
       }
     }
-    __syncthreads();
+    // lane cc holds column c0 + cc's distance to every row of the tile
+#pragma unroll
+    for (int i = 0; i < RT; ++i) {
+      const bool valid = mycol < cend && rr[i] >= 0 && (mode == 0 ? mycol < rr[i] : mycol != rr[i]);
+      const float dv = metric == HENN_ANGULAR ? 0.5f * dist[i] : dist[i];
+      const uint64_t key = valid ? pack(dv, (uint32_t)myq) : kEmpty;
+      unsigned m = __ballot_sync(0xffffffffu, key < lists[i].worst());
+      while (m) {
+        const int src = __ffs(m) - 1;
+        m &= m - 1;
+        const uint64_t k2 = shfl64(key, src);
+        if (k2 < lists[i].worst()) lists[i].insert(k2);
+      }
+    }
   }
+  // merge the warps' lists row by row
+#pragma unroll
+  for (int i = 0; i < RT; ++i)
+#pragma unroll
+    for (int q = 0; q < KM / 32; ++q) merged[((int64_t)w * RT + i) * KM + q * 32 + lane] = lists[i].v[q];
+  __syncthreads();
+  for (int i = w; i < RT; i += warps) {
+    if (rank_of[i] < 0) continue;
+    WarpList<KM> all;
+    all.clear();
+    for (int o = 0; o < warps; ++o)
+      for (int c = 0; c < KM; ++c) {
+        const uint64_t key = merged[((int64_t)o * RT + i) * KM + c];
+        if (key < all.worst()) all.insert(key);
+      }
+    const int64_t j = inv[rank_of[i]];
+#pragma unroll
+    for (int q = 0; q < KM / 32; ++q) {
+      const int g = q * 32 + lane;
+      if (g < M) {
+        const uint64_t key = all.v[q];
+        fwd[j * M + g] = key == kEmpty ? -1 : (int32_t)key_index(key);
+        fwd_d[j * M + g] = key == kEmpty ? __int_as_float(0x7f800000) : key_dist(key);
+      }
+    }
+  }
+}
+
+template <int KM, int KD>
+static void launch_exact_rows_t(const float* xw, const int32_t* ids, int64_t s, int32_t dpad, int32_t metric,
+                                const int32_t* inv, int32_t mode, const int32_t* rows, int32_t nrows, int32_t M,
+                                int32_t* fwd, float* fwd_d, cudaStream_t st) {
+  constexpr int RT = 8;
+  const int threads = 256;
+  const size_t smem = (size_t)RT * dpad * sizeof(float) + (size_t)(threads / 32) * RT * KM * sizeof(uint64_t);
+  auto kern = k_exact_rows<KM, RT, KD>;
+  cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  const int grid = (int)((nrows + RT - 1) / RT);
+  kern<<<grid, threads, smem, st>>>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d);
 }
 
 void launch_exact_rows(const float* xw, const int32_t* ids, int64_t s, int32_t dpad, int32_t metric, const int32_t* inv,
                        int32_t mode, const int32_t* rows, int32_t nrows, int32_t M, int32_t* fwd, float* fwd_d,
                        cudaStream_t st) {
   if (nrows <= 0) return;
-  int grid = nrows < 152 * 4 ? nrows : 152 * 4;
-  if (M <= 32)
-    k_exact_rows<32><<<grid, 256, 0, st>>>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d);
-  else
-    k_exact_rows<64><<<grid, 256, 0, st>>>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d);
+  const int kd = dpad / 32;
+  if (M <= 32) {
+    if (kd == 1) return launch_exact_rows_t<32, 1>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+    if (kd == 2) return launch_exact_rows_t<32, 2>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+    if (kd == 4) return launch_exact_rows_t<32, 4>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+    return launch_exact_rows_t<32, 0>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+  }
+  if (kd == 4) return launch_exact_rows_t<64, 4>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+  return launch_exact_rows_t<64, 0>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
 }
 
 // Query candidates -> exact k results (int64 ids, reported distances).

@@ -172,6 +172,38 @@ def test_graph_parity_tcgen05_tiles(case):
     _graph_parity(gidx, oidx, X)
 
 
+def _lattice(side, dim, pad_to=None):
+    g = np.stack(np.meshgrid(*[np.arange(side)] * dim, indexing="ij"), -1).reshape(-1, dim).astype(np.float32)
+    g = g[np.random.default_rng(3).permutation(len(g))]
+    if pad_to:
+        g = np.concatenate([g, np.zeros((len(g), pad_to - dim), np.float32)], axis=1)
+    return np.ascontiguousarray(g)
+
+
+@pytest.mark.parametrize("case", ["nsw_tc", "nsw_simt", "knn", "wide"])
+def test_graph_parity_uncertified_rows(case):
+    """Integer lattices put many points at exactly the M-th distance, so
+    the tile candidates of most rows cannot be certified and the rows go
+    through the batched exact recompute; forward lists and adjacency still
+    match the oracle (exact ties, broken by index on both sides)."""
+    if case == "wide":  # dpad = 160: the recompute's any-width path
+        X = _lattice(4, 5, pad_to=160)
+    else:
+        X = _lattice(8, 4)
+    kw, okw = dict(seed=2), dict(seed=2)
+    if case == "knn":
+        kw["graph"], okw["graph"] = H.GRAPH_KNN, O.GRAPH_KNN
+    if case == "nsw_tc":
+        kw["tiles"] = H.TILES_TCGEN05
+    elif case != "wide":
+        kw["tiles"] = H.TILES_SIMT
+    oidx = O.build_index(X, **okw)
+    gidx = _gpu_index(X, **kw)
+    assert gidx.info()["uncertified_rows"] > 0
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+
+
 def test_tcgen05_tiles_reject_wide_rows():
     with pytest.raises(H.HennError) as e:
         _gpu_index(synth.uniform_cube(500, 200, seed=1), tiles=H.TILES_TCGEN05)
