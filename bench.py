@@ -36,12 +36,12 @@ import synth  # noqa: E402
 
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
-EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512, 768, 1024]
+EF_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
 # (ef_upper, descend_all, ef_l1): beam width on the upper layers, whether
 # each layer is entered at all candidates of the layer above, and the beam
 # width on layer 1 (0 = ef_upper)
-UPPER_SWEEP = [(1, 0, 0), (32, 0, 0), (64, 0, 0), (64, 1, 0), (64, 0, 8), (64, 0, 16), (64, 0, 32), (128, 0, 8),
-               (128, 0, 16), (128, 0, 32), (128, 1, 16)]
+UPPER_SWEEP = [(1, 0, 0), (32, 0, 0), (48, 0, 0), (48, 1, 0), (56, 0, 0), (64, 0, 0), (64, 1, 0), (64, 0, 16),
+               (64, 0, 32), (80, 0, 16), (96, 0, 16), (128, 0, 16), (128, 1, 16)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -335,7 +335,7 @@ def run_ours(args):
     peaks, src = _peaks()
     avg = statistics.mean(times)
     achieved = alg_bytes / avg / 1e9
-    traffic = _profile_traffic()
+    traffic = _profile_traffic((ef, efu, da, l1))
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
@@ -395,9 +395,10 @@ def _build_roofline(info):
             "algorithmic_flops": info["tile_flops"], "peak_source": f"{src} bf16 sustained"}
 
 
-def _profile_traffic():
+def _profile_traffic(beam):
     """DRAM bytes per launch of the search kernel from the committed ncu
-    summary, if it was taken on the current kernel source; else None."""
+    summary, if it was taken on the current kernel source with the same
+    beam configuration (ef, ef_upper, descend_all, ef_l1); else None."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "search_bf16_mixture-1m-d128.md")
@@ -409,7 +410,8 @@ def _profile_traffic():
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
-        if kv.get("search.cu sha256[:16]") == sha:
+        want = "ef={} ef_upper={} descend_all={} ef_l1={}".format(*beam)
+        if kv.get("search.cu sha256[:16]") == sha and kv.get("beam") == want:
             return float(kv["dram bytes per launch"])
     except (OSError, KeyError, ValueError):
         pass

@@ -41,7 +41,7 @@ def candidates(k, ef, ef_upper=1, ef_l1=0):
     hb = _default_hash_bits(_beam_cap(k, ef, ef_upper, ef_l1))
     out = []
     for w in (4, 2):
-        for h in (hb - 1, hb, hb + 1):
+        for h in (hb - 2, hb - 1, hb, hb + 1):
             if 8 <= h <= 15:
                 out.append({"warps_per_block": w, "hash_bits": h})
     return out
