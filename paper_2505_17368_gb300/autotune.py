@@ -32,7 +32,7 @@ def _beam_cap(k, ef, ef_upper, ef_l1):
 
 def _default_hash_bits(cap):
     hb = 10
-    while hb < 13 and (1 << hb) < cap * 16:
+    while hb < 12 and (1 << hb) < cap * 8:
         hb += 1
     return hb
 

@@ -575,13 +575,12 @@ extern "C" void henn_free(henn_index* idx) { delete idx; }
 
 namespace {
 
-// Visited-table slots per query: about 16 per beam entry (a beam of ef
-// visits roughly 10 new nodes per expansion); the table may forget entries
-// without changing results, so it is sized for occupancy, not for
-// completeness.
+// Visited-table slots per query: at least 1024 and about 8 per beam entry;
+// the table may forget entries without changing results, so it is sized
+// for occupancy (shared memory per warp), not for completeness.
 int pick_hash_bits(int ef_cap) {
   int hb = 10;
-  while (hb < 13 && (1 << hb) < ef_cap * 16) ++hb;
+  while (hb < 12 && (1 << hb) < ef_cap * 8) ++hb;
   return hb;
 }
 
