@@ -22,7 +22,8 @@
 // of W is dropped, and a node that is not in W any more is farther than the
 // current worst entry (the worst entry only decreases), so it is rejected
 // exactly as a visited node would be.  Results therefore equal those of an
-// exact visited set.
+// exact visited set.  On layers of at most 32 << hash_bits points the same
+// shared memory holds an exact bitmap instead (one bit per point).
 #include <cuda_bf16.h>
 #include <cuda_fp16.h>
 #include <cuda_fp8.h>
@@ -186,6 +187,13 @@ __device__ __forceinline__ bool visit(int32_t* table, int HB, int32_t id, int& e
   return true;
 }
 
+// Layers of at most 32 << HB points: an exact visited bitmap in the
+// table's space (one atomic OR per node, nothing forgotten).
+__device__ __forceinline__ bool visit_bit(int32_t* table, int32_t id) {
+  const unsigned bit = 1u << (id & 31);
+  return (atomicOr(reinterpret_cast<unsigned*>(table) + (id >> 5), bit) & bit) == 0u;
+}
+
 // number of entries of sorted W[0..nw) (masked) strictly below key
 __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t key) {
   int lo = 0, hi = nw;
@@ -211,15 +219,18 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
   const unsigned below = (1u << lane) - 1u;  // lanes under this one
   int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
   const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
-  for (int s = lane; s < (1 << HB); s += 32) table[s] = -1;
+  const bool bitmap = Ly.size <= ((int64_t)32 << HB);
+  auto mark = [&](int32_t id) { return bitmap ? visit_bit(table, id) : visit(table, HB, id, evictions); };
+  const int words = bitmap ? (int)((Ly.size + 31) >> 5) : (1 << HB);
+  for (int s = lane; s < words; s += 32) table[s] = bitmap ? 0 : -1;
   __syncwarp();
   int nw;
   if (nseed > 0) {
     nw = min(nseed, ef);
     if (lane == 0)
-      for (int j = 0; j < nw; ++j) visit(table, HB, (int32_t)key_index(W[j] & kKeyMask), evictions);
+      for (int j = 0; j < nw; ++j) mark((int32_t)key_index(W[j] & kKeyMask));
   } else {
-    if (lane == 0) visit(table, HB, entry, evictions);
+    if (lane == 0) mark(entry);
     float d0 = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, entry, 1, qs, nchunk);
     d0 = __shfl_sync(0xffffffffu, d0, 0);
     ++evals;
@@ -257,7 +268,7 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
       asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
     }
     __syncwarp();
-    bool fresh = nb >= 0 && visit(table, HB, nb, evictions);
+    bool fresh = nb >= 0 && mark(nb);
     unsigned fm = __ballot_sync(0xffffffffu, fresh);
     int cnt = __popc(fm);
     if (cnt == 0) continue;
