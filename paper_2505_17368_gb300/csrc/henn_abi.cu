@@ -172,7 +172,12 @@ struct henn_index {
     bytes += (int64_t)b;
     return static_cast<T*>(p);
   }
+  // side streams for the concurrent per-class launches of one batch
+  // (created on first use)
+  mutable std::mutex side_mu;
+  mutable std::vector<cudaStream_t> side;
   ~henn_index() {
+    for (cudaStream_t t : side) cudaStreamDestroy(t);
     for (void* p : allocs) cudaFree(p);
   }
 };
@@ -658,10 +663,15 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     const int rerank = idx->storage != HENN_F32;
     require(sp.ef_upper >= 0 && sp.ef_upper <= 4096, "ef_upper must be in [0, 4096]");
     require(sp.ef_l1 >= 0 && sp.ef_l1 <= 4096, "ef_l1 must be in [0, 4096]");
-    int need = std::max(std::max(kmax, efmax), std::max((int)sp.ef_upper, (int)sp.ef_l1));
-    if (rerank) need = std::max(need, std::min(efmax, sp.rerank_mult * kmax));
-    int ef_cap = 32;
-    while (ef_cap < need) ef_cap <<= 1;
+    // beam capacity of a query: the power of two holding its widest list
+    auto cap_of = [&](int32_t kq, int32_t efq) {
+      int nd = std::max(std::max(kq, efq), std::max((int)sp.ef_upper, (int)sp.ef_l1));
+      if (rerank) nd = std::max(nd, std::min(efq, sp.rerank_mult * kq));
+      int c = 32;
+      while (c < nd) c <<= 1;
+      return c;
+    };
+    const int ef_cap = cap_of(kmax, efmax);
     int hb = sp.hash_bits > 0 ? sp.hash_bits : pick_hash_bits(ef_cap);
     require(hb >= 8 && hb <= 15, "hash_bits must be in [8, 15]");
     int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
@@ -698,8 +708,44 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
       dd = sc.get<float>((size_t)nq * out_stride);
       if (sp.stats) dstats = sc.get<int32_t>((size_t)nq * 4);
     }
-    unsigned long long* counter = sc.get<unsigned long long>(1);
-    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long), st));
+    // Per-query k / ef: queries are grouped by beam capacity and each group
+    // runs as its own persistent launch, sized (shared memory per warp,
+    // visited table, resident warps) for that capacity; the launches run
+    // concurrently on side streams.  Results do not depend on the grouping.
+    std::vector<int> caps;                  // distinct capacities, widest first
+    std::vector<int64_t> begin, count;      // their ranges in `order`
+    const int32_t* d_order = nullptr;
+    if ((sp.k || sp.ef) && sp.hash_bits <= 0) {
+      std::vector<int> qcap(nq);
+      for (int64_t q = 0; q < nq; ++q) qcap[q] = cap_of(sp.k ? hk[q] : kmax, sp.ef ? hef[q] : efmax);
+      for (int c = ef_cap; c >= 32; c >>= 1) {
+        int64_t n = 0;
+        for (int64_t q = 0; q < nq; ++q) n += qcap[q] == c;
+        if (n > 0) {
+          caps.push_back(c);
+          count.push_back(n);
+        }
+      }
+      if (caps.size() > 1) {
+        std::vector<int32_t> h_order;
+        h_order.reserve(nq);
+        for (size_t g = 0; g < caps.size(); ++g) {
+          begin.push_back((int64_t)h_order.size());
+          for (int64_t q = 0; q < nq; ++q)
+            if (qcap[q] == caps[g]) h_order.push_back((int32_t)q);
+        }
+        int32_t* o = sc.get<int32_t>(nq);
+        CK(cudaMemcpyAsync(o, h_order.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // h_order is a local vector
+        d_order = o;
+      } else {
+        caps.clear();
+        count.clear();
+      }
+    }
+    const int groups = caps.empty() ? 1 : (int)caps.size();
+    unsigned long long* counter = sc.get<unsigned long long>(groups);
+    CK(cudaMemsetAsync(counter, 0, sizeof(unsigned long long) * groups, st));
 
     SearchArgs a;
     fill_search_args(idx, a);
@@ -722,10 +768,42 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.stats = dstats;
     a.counter = counter;
 
-    size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
-    int64_t blocks_needed = (nq + warps - 1) / warps;
-    int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
-    CK(launch_search(a, warps, grid, st));
+    if (groups == 1) {
+      size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
+      int64_t blocks_needed = (nq + warps - 1) / warps;
+      int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
+      CK(launch_search(a, warps, grid, st));
+    } else {
+      std::lock_guard<std::mutex> lk(idx->side_mu);
+      while ((int)idx->side.size() < groups) {
+        cudaStream_t t;
+        CK(cudaStreamCreateWithFlags(&t, cudaStreamNonBlocking));
+        idx->side.push_back(t);
+      }
+      cudaEvent_t fork;
+      CK(cudaEventCreateWithFlags(&fork, cudaEventDisableTiming));
+      CK(cudaEventRecord(fork, st));
+      for (int g = 0; g < groups; ++g) {
+        cudaStream_t t = idx->side[g];
+        CK(cudaStreamWaitEvent(t, fork, 0));
+        SearchArgs ag = a;
+        ag.order = d_order + begin[g];
+        ag.nq = count[g];
+        ag.ef_cap = caps[g];
+        ag.hash_bits = pick_hash_bits(caps[g]);
+        ag.counter = counter + g;
+        size_t smem = search_warp_smem(ag.ef_cap, ag.hash_bits, idx->dpad) * warps;
+        int64_t blocks_needed = (count[g] + warps - 1) / warps;
+        int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
+        CK(launch_search(ag, warps, grid, t));
+        cudaEvent_t join;
+        CK(cudaEventCreateWithFlags(&join, cudaEventDisableTiming));
+        CK(cudaEventRecord(join, t));
+        CK(cudaStreamWaitEvent(st, join, 0));
+        cudaEventDestroy(join);
+      }
+      cudaEventDestroy(fork);
+    }
     if (!q_on_device) {
       CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(out_dists, dd, sizeof(float) * nq * out_stride, cudaMemcpyDeviceToHost, st));

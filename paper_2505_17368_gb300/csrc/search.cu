@@ -497,6 +497,7 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const Se
     if (lane == 0) qi = atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
     qi = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)qi, 0);
     if (qi >= a.nq) break;
+    if (a.order) qi = a.order[qi];
     const int k = a.kq ? a.kq[qi] : a.k_uniform;
     const int ef = a.efq ? a.efq[qi] : a.ef_uniform;
     const uint64_t key = a.keys ? a.keys[qi] : (uint64_t)qi;

@@ -40,6 +40,7 @@ struct SearchArgs {
   int32_t out_stride;
   int32_t* stats;
   unsigned long long* counter;  // work counter, zero at launch
+  const int32_t* order;         // nullptr, or the query of each work slot
   int32_t warp_smem;            // bytes of shared memory per warp
 };
 
