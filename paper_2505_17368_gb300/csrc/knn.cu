@@ -313,7 +313,7 @@ void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t d
 // list the certified path would give it.  Column validity: mode 0 (causal,
 // NSW) columns before the row in insertion order, mode 1 (kNN) all other
 // columns.  KD = dpad / 32 when dpad <= 128 (the loads of CPG columns are
-// issued together), else 0 (any dpad, one column at a time).
+// issued together), else 0 (any dpad, one column at a time, read once).
 template <int KM, int RT, int KD>
 __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__ xw, const int32_t* __restrict__ ids,
                                                        int64_t s, int32_t dpad, int32_t metric,
@@ -394,18 +394,32 @@ __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__
           }
         }
       } else {
+        // any width: the column is read once, 8 elements per lane at a time,
+        // into every row's running sum (same element order per row)
         const float* p = reinterpret_cast<const float*>(
             __shfl_sync(0xffffffffu, reinterpret_cast<unsigned long long>(myrow), cc & 31));
-#pragma unroll 1
-        for (int i = 0; i < RT; ++i) {
-          float acc = 0.f;
-          for (int k = 0; k < kd; ++k) {
-            const float t = qrows[i * dpad + lane + 32 * k] - __ldg(p + lane + 32 * k);
-            acc = fmaf(t, t, acc);
-          }
+        float acc[RT];
 #pragma unroll
-          for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-          if (lane == cc) dist[i] = acc;
+        for (int i = 0; i < RT; ++i) acc[i] = 0.f;
+        for (int k0 = 0; k0 < kd; k0 += 8) {
+          float v[8];
+#pragma unroll
+          for (int t = 0; t < 8; ++t) v[t] = k0 + t < kd ? __ldg(p + lane + 32 * (k0 + t)) : 0.f;
+#pragma unroll
+          for (int i = 0; i < RT; ++i)
+#pragma unroll
+            for (int t = 0; t < 8; ++t)
+              if (k0 + t < kd) {
+                const float u = qrows[i * dpad + lane + 32 * (k0 + t)] - v[t];
+                acc[i] = fmaf(u, u, acc[i]);
+              }
+        }
+#pragma unroll
+        for (int i = 0; i < RT; ++i) {
+          float r = acc[i];
+#pragma unroll
+          for (int o = 16; o > 0; o >>= 1) r += __shfl_xor_sync(0xffffffffu, r, o);
+          if (lane == cc) dist[i] = r;
         }
       }
     }
@@ -473,6 +487,7 @@ void launch_exact_rows(const float* xw, const int32_t* ids, int64_t s, int32_t d
   if (M <= 32) {
     if (kd == 1) return launch_exact_rows_t<32, 1>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
     if (kd == 2) return launch_exact_rows_t<32, 2>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
+    if (kd == 3) return launch_exact_rows_t<32, 3>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
     if (kd == 4) return launch_exact_rows_t<32, 4>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
     return launch_exact_rows_t<32, 0>(xw, ids, s, dpad, metric, inv, mode, rows, nrows, M, fwd, fwd_d, st);
   }

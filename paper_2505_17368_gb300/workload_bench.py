@@ -3,6 +3,8 @@ error of the returned results against FP64.
 
     python -m paper_2505_17368_gb300.workload_bench --workload shells-1m-d64 --storage f32
     python -m paper_2505_17368_gb300.workload_bench --workload mixture-1m-d960 --storage bf16,fp8
+    python -m paper_2505_17368_gb300.workload_bench --workload exponential-50k-d32-l4
+    python -m paper_2505_17368_gb300.workload_bench --workload exponential-1m-d16-l4 --scaling 16384,65536,262144,1048576
 
 For each storage form: one index build (timed), FP32 ground truth on the
 device (henn_exact_knn), a sweep of (ef_upper, ef) timed with CUDA events
@@ -10,8 +12,11 @@ device (henn_exact_knn), a sweep of (ef_upper, ef) timed with CUDA events
 recall@10 >= 0.95, and, on a sample of queries, FP64 ground truth computed
 here with numpy: recall@10 against it and the relative error of each
 returned distance against the FP64 distance of the same pair.  A workload
-with per-query beam widths (the nested shells) is also run as one launch
-with those widths.  Prints one JSON line per storage form.
+with per-query beam widths (the nested shells) is also run as one call
+with those widths.  The sweep table is the QPS-recall curve; per-query
+distance evaluations and hops (expansions, upper-layer moves included) at
+the chosen setting are reported as mean and maximum.  Prints one JSON line
+per storage form.
 """
 from __future__ import annotations
 
@@ -136,6 +141,13 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
         ef, efu = best["ef"], best["ef_upper"]
     else:
         ef, efu = EF_SWEEP[-1], UPPER_SWEEP[-1]
+    # per-query work at the chosen setting (the paper reports worst cases)
+    _, _, st = idx.search(Qd, k=K, ef=ef, ef_upper=efu, stats=True)
+    st = st.cpu().numpy().astype(np.int64)
+    hops = st[:, 1] + st[:, 2]
+    res["per_query"] = {"evals_mean": float(st[:, 0].mean()), "evals_max": int(st[:, 0].max()),
+                        "hops_mean": float(hops.mean()), "hops_max": int(hops.max()),
+                        "upper_layer_expansions_mean": float(st[:, 2].mean())}
     if "ef_per_query" in info:
         efq = torch.from_numpy(np.asarray(info["ef_per_query"], np.int32)).cuda()
         ids, _, _ = idx.search(Qd, k=K, ef=efq, ef_upper=efu)
@@ -164,6 +176,37 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
     return res
 
 
+def scaling(workload, ns, ef, ef_upper, storage="f32"):
+    """Work per query against n (the paper's hops and worst-case time against
+    n): for each prefix size n of the workload, build, search the queries at
+    a fixed beam, and report recall@10, batch QPS and the mean / maximum of
+    distance evaluations and hops per query."""
+    import torch
+
+    import paper_2505_17368_gb300 as H
+    import synth
+
+    form = {"f32": H.F32, "bf16": H.BF16, "fp8": H.FP8E4M3}[storage]
+    flush = torch.empty(64 << 20, dtype=torch.float32, device="cuda")
+    out = []
+    for n in ns:
+        X, Q, info = synth.workload(workload, n=n)
+        Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+        idx = H.Index(Xd, storage=form, seed=0)
+        gi, _ = H.exact_knn(Xd, Qd, K)
+        ids, _, st = idx.search(Qd, k=K, ef=ef, ef_upper=ef_upper, stats=True)
+        st = st.cpu().numpy().astype(np.int64)
+        hops = st[:, 1] + st[:, 2]
+        ms = _time(lambda: idx.search(Qd, k=K, ef=ef, ef_upper=ef_upper), flush)
+        out.append({"workload": workload, "n": n, "layers": idx.info()["sizes"], "ef": ef, "ef_upper": ef_upper,
+                    "recall_at_10": _recall(ids.cpu().numpy(), gi.cpu().numpy()), "qps": len(Q) / (ms * 1e-3),
+                    "evals_mean": float(st[:, 0].mean()), "evals_max": int(st[:, 0].max()),
+                    "hops_mean": float(hops.mean()), "hops_max": int(hops.max())})
+        del idx
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="shells-1m-d64")
@@ -171,7 +214,14 @@ def main():
     ap.add_argument("--n", type=int, default=None)
     ap.add_argument("--nq", type=int, default=None)
     ap.add_argument("--sample", type=int, default=100)
+    ap.add_argument("--scaling", default=None, help="comma-separated prefix sizes n: work per query against n")
+    ap.add_argument("--ef", type=int, default=10)
+    ap.add_argument("--ef-upper", type=int, default=1)
     a = ap.parse_args()
+    if a.scaling:
+        for r in scaling(a.workload, [int(float(v)) for v in a.scaling.split(",")], a.ef, a.ef_upper, a.storage):
+            print(json.dumps(r), flush=True)
+        return
     for st in a.storage.split(","):
         print(json.dumps(run(a.workload, st, n=a.n, nq=a.nq, sample=a.sample)), flush=True)
 

@@ -210,6 +210,12 @@ WORKLOADS = {
     "shells-1m-d64": dict(n=1_000_000, d=64, nq=10_000, k=10, metric="l2"),
     "mixture-1m-d960": dict(n=1_000_000, d=960, nq=10_000, k=10, metric="l2", clusters=500),
     "angular-10m-d96": dict(n=10_000_000, d=96, nq=10_000, k=10, metric="angular", clusters=10_000),
+    # the paper's own synthetic data (App. F): i.i.d. exponential coordinates
+    "exponential-50k-d32-l4": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=4.0),
+    "exponential-50k-d32-l32": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=32.0),
+    "exponential-50k-d32-l256": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=256.0),
+    "exponential-1m-d16-l4": dict(n=1 << 20, d=16, nq=10_000, k=10, metric="l2", lam=4.0),
+    "exponential-1m-d32-l4": dict(n=1 << 20, d=32, nq=10_000, k=10, metric="l2", lam=4.0),
 }
 
 
@@ -243,6 +249,9 @@ def workload(name: str, n: int | None = None, nq: int | None = None):
     elif name == "angular-10m-d96":
         X, _ = gaussian_mixture(n, d, spec["clusters"], seed=0, normalise=True)
         Q, _ = gaussian_mixture(nq, d, spec["clusters"], seed=1, normalise=True)
+    elif name.startswith("exponential-"):
+        X = exponential(n, d, spec["lam"], seed=0)
+        Q = exponential(nq, d, spec["lam"], seed=1)
     else:  # pragma: no cover
         raise KeyError(name)
     return X, Q, info

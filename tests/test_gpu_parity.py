@@ -180,7 +180,7 @@ def _lattice(side, dim, pad_to=None):
     return np.ascontiguousarray(g)
 
 
-@pytest.mark.parametrize("case", ["nsw_tc", "nsw_simt", "knn", "wide"])
+@pytest.mark.parametrize("case", ["nsw_tc", "nsw_simt", "knn", "wide", "d96"])
 def test_graph_parity_uncertified_rows(case):
     """Integer lattices put many points at exactly the M-th distance, so
     the tile candidates of most rows cannot be certified and the rows go
@@ -188,6 +188,8 @@ def test_graph_parity_uncertified_rows(case):
     match the oracle (exact ties, broken by index on both sides)."""
     if case == "wide":  # dpad = 160: the recompute's any-width path
         X = _lattice(4, 5, pad_to=160)
+    elif case == "d96":  # dpad = 96: three chunks of 32 per lane
+        X = _lattice(6, 4, pad_to=96)
     else:
         X = _lattice(8, 4)
     kw, okw = dict(seed=2), dict(seed=2)
