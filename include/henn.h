@@ -210,6 +210,28 @@ henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info);
 henn_status henn_index_get_layer(const henn_index* idx, int32_t layer, int32_t* ids, int32_t* down,
                                  int32_t* adj, int32_t* fwd, float* fwd_d);
 
+/*
+ * henn_greedy_probe -- GreedySearch of Alg. 4 on one layer of the index from
+ * given start nodes, one probe per (query, start).  The recall bound
+ * rho_delta of Def. 3 is the smallest k such that a probe from a random start
+ * ends among the query's k nearest points with probability >= delta; this
+ * call gives the end points to rank.
+ *   layer     0..L
+ *   Q         nq x d float32 query rows, DEVICE memory
+ *   starts    nq x S int32 start positions in the layer (0 .. |L_layer|-1),
+ *             DEVICE memory; a start outside that range yields -1
+ *   out_node  nq x S int32 DEVICE: the local minimum reached (layer position;
+ *             layer 0 positions are the global ids)
+ *   out_dist  nq x S float32 DEVICE: its distance to the query in the
+ *             traversal precision (squared l2, or 2 (1 - cos))
+ *   out_hops  nq x S int32 DEVICE, or NULL: moves made
+ * Ties go to the smaller index, and the walk moves only to a strictly closer
+ * node.  Asynchronous on `stream`.  Errors: HENN_ERR_INVALID_ARG for a bad
+ * layer, NULL pointers or S < 1.
+ */
+henn_status henn_greedy_probe(const henn_index* idx, int32_t layer, const float* Q, int64_t nq, const int32_t* starts,
+                              int32_t S, int32_t* out_node, float* out_dist, int32_t* out_hops, void* stream);
+
 /* ------------------------------------------------- standalone kernels */
 
 /*

@@ -46,6 +46,7 @@ EXPORTS = [
     "henn_index_get_info",
     "henn_index_get_layer",
     "henn_exact_knn",
+    "henn_greedy_probe",
     "henn_quantize_rows",
     "henn_last_error",
     "henn_serve_params_default",
@@ -169,6 +170,8 @@ def load(path: str | None = None):
         L.henn_index_get_layer.restype = i32
         L.henn_exact_knn.argtypes = [vp, i64, i32, vp, i64, i32, i32, vp, vp, vp]
         L.henn_exact_knn.restype = i32
+        L.henn_greedy_probe.argtypes = [vp, i32, vp, i64, vp, i32, vp, vp, vp, vp]
+        L.henn_greedy_probe.restype = i32
         L.henn_quantize_rows.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         L.henn_quantize_rows.restype = i32
         L.henn_serve_params_default.argtypes = [C.POINTER(ServeParams)]
@@ -293,6 +296,22 @@ class Index:
         P = lambda a: C.c_void_p(a.ctypes.data)  # noqa: E731
         _check(load().henn_index_get_layer(self._h, i, P(ids), P(down), P(adj), P(fwd), P(fwd_d)))
         return dict(ids=ids, down=down, adj=adj, fwd=fwd, fwd_d=fwd_d)
+
+    def greedy_probe(self, Q, starts, layer=0, stream=None):
+        """henn_greedy_probe: GreedySearch on one layer from each start.
+        Q [nq, d] and starts [nq, S] (int32 layer positions) are CUDA tensors.
+        Returns (node int32 [nq, S], dist float32 [nq, S], hops int32 [nq, S])."""
+        import torch
+
+        Q = Q.to(torch.float32).contiguous()
+        starts = starts.to(torch.int32).contiguous()
+        nq, S = starts.shape
+        node = torch.empty((nq, S), dtype=torch.int32, device=Q.device)
+        dist = torch.empty((nq, S), dtype=torch.float32, device=Q.device)
+        hops = torch.empty((nq, S), dtype=torch.int32, device=Q.device)
+        _check(load().henn_greedy_probe(self._h, int(layer), _ptr(Q)[0], nq, _ptr(starts)[0], S, _ptr(node)[0],
+                                        _ptr(dist)[0], _ptr(hops)[0], _stream(stream)))
+        return node, dist, hops
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
                warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None):

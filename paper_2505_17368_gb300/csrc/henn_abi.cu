@@ -820,6 +820,47 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
   }
 }
 
+// ------------------------------------------------------ greedy probes
+
+extern "C" henn_status henn_greedy_probe(const henn_index* idx, int32_t layer, const float* Q, int64_t nq,
+                                         const int32_t* starts, int32_t S, int32_t* out_node, float* out_dist,
+                                         int32_t* out_hops, void* stream) {
+  g_error.clear();
+  try {
+    require(idx != nullptr, "index is NULL");
+    require(layer >= 0 && layer <= idx->L, "layer out of range");
+    require(nq >= 0 && S >= 1, "nq must be >= 0 and S >= 1");
+    if (nq == 0) return HENN_OK;
+    require(Q && starts && out_node && out_dist, "Q / starts / out_node / out_dist must not be NULL");
+    const LayerDev& Ly = idx->layers[layer];
+    GreedyProbeArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.layer.adj = Ly.adj;
+    a.layer.vec = Ly.vec;
+    a.layer.scale = Ly.vscale;
+    a.layer.down = Ly.down;
+    a.layer.size = Ly.size;
+    a.dpad = idx->dpad;
+    a.d = idx->d;
+    a.metric = idx->metric;
+    a.Q = Q;
+    a.nq = nq;
+    a.starts = starts;
+    a.S = S;
+    a.out_node = out_node;
+    a.out_dist = out_dist;
+    a.out_hops = out_hops;
+    CK(launch_greedy_probe(a, idx->storage, (cudaStream_t)stream));
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  } catch (const std::exception& e) {
+    g_error = e.what();
+    return HENN_ERR_CUDA;
+  }
+}
+
 // ------------------------------------------------------ introspection
 
 extern "C" henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info) {

@@ -580,6 +580,98 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const Ser
   }
 }
 
+// ------------------------------------------------------ greedy probes
+
+// GreedySearch of Alg. 4 on one layer from a given start node, one warp
+// per (query, start): move to the closest neighbour (ties by index) while it
+// is strictly closer.  The local minimum it ends at is what the recall
+// bound rho_delta of Def. 3 ranks among the query's true neighbours.
+template <typename VT, int DMAX>
+__global__ void __launch_bounds__(128) k_greedy_probe(const GreedyProbeArgs a) {
+  constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int lane = lane_id();
+  float* qs = reinterpret_cast<float*>(smem) + (threadIdx.x >> 5) * a.dpad;
+  const int64_t stride = (int64_t)a.dpad * sizeof(VT);
+  const int nchunk = (int)(stride / 16);
+  const VT* vec = reinterpret_cast<const VT*>(a.layer.vec);
+  const int64_t total = a.nq * a.S;
+  const int64_t warps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t p = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; p < total; p += warps) {
+    const int64_t qi = p / a.S;
+    const float* qg = a.Q + qi * a.d;
+    float ss = 0.f;
+    __syncwarp();
+    for (int c = lane; c < a.dpad; c += 32) {
+      const float v = c < a.d ? qg[c] : 0.f;
+      qs[c] = v;
+      ss = fmaf(v, v, ss);
+    }
+    if (a.metric == HENN_ANGULAR) {
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      const float inv = ss > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(ss)) : 0.f;
+      __syncwarp();
+      for (int c = lane; c < a.dpad; c += 32) qs[c] *= inv;
+    }
+    __syncwarp();
+    int32_t cur = a.starts[p];
+    if (cur < 0 || cur >= a.layer.size) {
+      if (lane == 0) {
+        a.out_node[p] = -1;
+        a.out_dist[p] = __int_as_float(0x7f800000);
+        if (a.out_hops) a.out_hops[p] = 0;
+      }
+      continue;
+    }
+    float dc = rows_dist<VT, G, CPL>(vec, a.layer.scale, stride, cur, 1, qs, nchunk);
+    dc = __shfl_sync(0xffffffffu, dc, 0);
+    int32_t moves = 0;
+    for (;;) {
+      const int32_t nb = a.layer.adj[(int64_t)cur * kMmax + lane];
+      const int cnt = __popc(__ballot_sync(0xffffffffu, nb >= 0));
+      // neighbours are packed at the front of each row (-1 padding after)
+      const float dn = rows_dist<VT, G, CPL>(vec, a.layer.scale, stride, nb, cnt, qs, nchunk);
+      const uint64_t kk = lane < cnt ? pack(dn, (uint32_t)nb) : kEmpty;
+      const uint64_t best = warp_min64(kk);
+      if (best == kEmpty || !(key_dist(best) < dc)) break;
+      cur = (int32_t)key_index(best);
+      dc = key_dist(best);
+      ++moves;
+    }
+    if (lane == 0) {
+      a.out_node[p] = cur;
+      a.out_dist[p] = dc;
+      if (a.out_hops) a.out_hops[p] = moves;
+    }
+  }
+}
+
+template <typename VT, int DMAX>
+static cudaError_t launch_probe_t(const GreedyProbeArgs& a, cudaStream_t st) {
+  const int64_t warps_needed = a.nq * a.S;
+  int64_t blocks = (warps_needed + 3) / 4;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_greedy_probe<VT, DMAX><<<(int)blocks, 128, (size_t)4 * a.dpad * sizeof(float), st>>>(a);
+  return cudaGetLastError();
+}
+
+template <typename VT>
+static cudaError_t launch_probe_vt(const GreedyProbeArgs& a, cudaStream_t st) {
+  if (a.dpad <= 32) return launch_probe_t<VT, 32>(a, st);
+  if (a.dpad <= 64) return launch_probe_t<VT, 64>(a, st);
+  if (a.dpad <= 128) return launch_probe_t<VT, 128>(a, st);
+  if (a.dpad <= 512) return launch_probe_t<VT, 512>(a, st);
+  return launch_probe_t<VT, 1024>(a, st);
+}
+
+cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStream_t st) {
+  if (storage == HENN_BF16) return launch_probe_vt<__nv_bfloat16>(a, st);
+  if (storage == HENN_FP8E4M3) return launch_probe_vt<__nv_fp8_e4m3>(a, st);
+  return launch_probe_vt<float>(a, st);
+}
+
 // ------------------------------------------------------------ dispatch
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad) {

@@ -66,7 +66,21 @@ struct ServeArgs {
   long long idle_ns;             // the kernel leaves after this long without work
 };
 
+// GreedySearch probes on one layer (henn_greedy_probe).
+struct GreedyProbeArgs {
+  SearchLayer layer;
+  int32_t dpad, d, metric;
+  const float* Q;        // nq x d queries
+  int64_t nq;
+  const int32_t* starts;  // nq x S start positions in the layer
+  int32_t S;
+  int32_t* out_node;     // nq x S local minima (layer positions), -1 for a bad start
+  float* out_dist;       // their distances in traversal precision
+  int32_t* out_hops;     // moves per probe, or nullptr
+};
+
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStream_t st);
 cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st);
 

@@ -246,6 +246,41 @@ def test_search_upper_beam_parity(uniform10k, efu, l1, da):
     assert P.returned_distance_error(X, Q, ids.cpu().numpy(), dd.cpu().numpy()) <= P.DIST_RTOL
 
 
+@pytest.mark.parametrize("layer", [0, 1])
+def test_greedy_probe_matches_oracle(uniform10k, layer):
+    """henn_greedy_probe walks the same GreedySearch (Alg. 4) as the oracle's
+    on the same layer graph: from every start it stops at the same local
+    minimum, with the same number of moves (FP32 against FP64 distances:
+    a differing end point must be a near tie)."""
+    X, Q, oidx, gidx = uniform10k
+    lay = gidx.layer(layer)
+    size = len(lay["adj"])
+    nq, S = 40, 6
+    starts = (synth.uniform_stream(5, 7, nq * S) * size).astype(np.int64).reshape(nq, S)
+    starts[0, 0] = size + 3  # out of range -> -1
+    node, dist, hops = gidx.greedy_probe(torch.from_numpy(Q[:nq]).to(DEV), torch.from_numpy(starts).to(DEV),
+                                         layer=layer)
+    node, hops = node.cpu().numpy(), hops.cpu().numpy()
+    assert node[0, 0] == -1
+    ids = None if layer == 0 else lay["ids"].astype(np.int64)
+    same = total = 0
+    for q in range(nq):
+        for j in range(S):
+            if q == 0 and j == 0:
+                continue
+            o_node, o_hops, _ = O.greedy_layer(X, ids, lay["adj"], Q[q], int(starts[q, j]))
+            total += 1
+            if o_node == node[q, j]:
+                same += 1
+                assert o_hops == hops[q, j]
+            else:
+                pts = X if ids is None else X[ids]
+                da = float(((pts[o_node].astype(np.float64) - Q[q]) ** 2).sum())
+                db = float(((pts[node[q, j]].astype(np.float64) - Q[q]) ** 2).sum())
+                assert abs(da - db) <= 1e-5 * da, (q, j, da, db)
+    assert same >= 0.99 * total
+
+
 def test_search_host_buffers_equal_device(uniform10k):
     """The host-buffer form (copies inside the call) returns the same."""
     X, Q, oidx, gidx = uniform10k
