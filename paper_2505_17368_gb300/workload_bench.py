@@ -5,6 +5,7 @@ error of the returned results against FP64.
     python -m paper_2505_17368_gb300.workload_bench --workload mixture-1m-d960 --storage bf16,fp8
     python -m paper_2505_17368_gb300.workload_bench --workload exponential-50k-d32-l4
     python -m paper_2505_17368_gb300.workload_bench --workload exponential-1m-d16-l4 --scaling 16384,65536,262144,1048576
+    python -m paper_2505_17368_gb300.workload_bench --workload exponential-50k-d32-l4 --rho
 
 For each storage form: one index build (timed), FP32 ground truth on the
 device (henn_exact_knn), a sweep of (ef_upper, ef) timed with CUDA events
@@ -207,6 +208,51 @@ def scaling(workload, ns, ef, ef_upper, storage="f32"):
     return out
 
 
+def recall_bound(workload, n=None, nq=1000, starts=64, K=100, deltas=(0.5, 0.9), ef=64):
+    """The recall bound rho_delta of Def. 3 on layer 0, for the NSW and the
+    kNN navigation graph: GreedySearch from `starts` random nodes per query
+    (henn_greedy_probe); the rank of each end point among the query's exact
+    K nearest points (K when absent); rho_delta = the smallest k with at
+    least a delta fraction of probes ending among the k nearest.  Also the
+    recall@k of the full search against k (k up to K) at beam ef."""
+    import torch
+
+    import paper_2505_17368_gb300 as H
+    import synth
+
+    X, Q, info = synth.workload(workload, n=n, nq=nq)
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    gi, _ = H.exact_knn(Xd, Qd, K)
+    gi = gi.cpu().numpy()
+    u = synth.uniform_stream(9, 71, len(Q) * starts).reshape(len(Q), starts)
+    st = torch.from_numpy((u * len(X)).astype(np.int32)).cuda()
+    out = []
+    for graph, name in [(H.GRAPH_NSW, "nsw"), (H.GRAPH_KNN, "knn")]:
+        idx = H.Index(Xd, graph=graph, seed=0)
+        node, _, hops = idx.greedy_probe(Qd, st, layer=0)
+        node = node.cpu().numpy()
+        rank = np.full(node.shape, K)
+        for q in range(len(Q)):
+            pos = {int(v): r for r, v in enumerate(gi[q])}
+            rank[q] = [pos.get(int(v), K) for v in node[q]]
+        rho = {}
+        for dl in deltas:
+            frac = np.array([(rank < k).mean() for k in range(1, K + 1)])
+            hit = np.nonzero(frac >= dl)[0]
+            rho[str(dl)] = int(hit[0] + 1) if hit.size else None
+        ids, _, _ = idx.search(Qd, k=K, ef=max(ef, K))
+        ids = ids.cpu().numpy()
+        rk = {k: float(np.mean([len(set(ids[q, :k].tolist()) & set(gi[q, :k].tolist())) / k for q in range(len(Q))]))
+              for k in (1, 5, 10, 20, 50, 100) if k <= K}
+        out.append({"workload": workload, "n": len(X), "graph": name, "probes": int(node.size),
+                    "rho": rho, "greedy_hops_mean": float(hops.float().mean()),
+                    "end_in_top1": float((rank < 1).mean()), "end_in_top10": float((rank < 10).mean()),
+                    "search_recall_at_k": rk, "search_ef": max(ef, K)})
+        del idx
+        torch.cuda.empty_cache()
+    return out
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="shells-1m-d64")
@@ -217,7 +263,12 @@ def main():
     ap.add_argument("--scaling", default=None, help="comma-separated prefix sizes n: work per query against n")
     ap.add_argument("--ef", type=int, default=10)
     ap.add_argument("--ef-upper", type=int, default=1)
+    ap.add_argument("--rho", action="store_true", help="recall bound rho_delta and recall@k vs k, NSW and kNN graphs")
     a = ap.parse_args()
+    if a.rho:
+        for r in recall_bound(a.workload, n=a.n, nq=a.nq or 1000):
+            print(json.dumps(r), flush=True)
+        return
     if a.scaling:
         for r in scaling(a.workload, [int(float(v)) for v in a.scaling.split(",")], a.ef, a.ef_upper, a.storage):
             print(json.dumps(r), flush=True)
