@@ -49,6 +49,7 @@ struct Smem {
   uint8_t a[2 * MAX_KC][A_CHUNK];  // hi chunks then lo chunks
   uint8_t b[NS][B_CHUNK];
   uint64_t lists[BM][KP];          // running top-KP per row
+  alignas(16) float ncol[4][BN];   // column norms of the current tile, one copy per epilogue warp
   float s[4][32][S_LD];            // epilogue transposition, one slab per warp
   uint64_t full[NS], empty[NS], tfull[2], tempty[2], afull;
   uint32_t tmem_base;
@@ -298,27 +299,46 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       tc::fence_after();
+      // this tile's column norms, staged once (read back as broadcasts)
+      float* ncs = sm.ncol[ew];
+#pragma unroll
+      for (int q = 0; q < BN / 32; ++q) {
+        const int64_t c = (int64_t)t * BN + q * 32 + lane;
+        ncs[q * 32 + lane] = c < s ? __ldg(norms + c) : 0.f;
+      }
+      __syncwarp();
 #pragma unroll 1
       for (int q = 0; q < BN / 32; ++q) {
         const int64_t c0 = (int64_t)t * BN + q * 32;
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN + q * 32), v);
         if (c0 >= cend) continue;  // warp-uniform
-        const float ncol = (c0 + lane < s) ? __ldg(norms + c0 + lane) : 0.f;
-        // columns c0 + j valid for this row, as a bit mask
-        const int32_t rem = lim - (int32_t)c0;
-        unsigned vmask = rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-        const int32_t so = self - (int32_t)c0;
-        if (so >= 0 && so < 32) vmask &= ~(1u << so);
-        unsigned keep = 0;
+        // n_col - 2<a,b> for the 32 columns and their minimum: most chunks
+        // end here, with no column under the row's threshold
+        const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
+        float vmin = kInf;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) {
-          const float nc = __shfl_sync(0xffffffffu, ncol, j);
-          const float dv = fmaf(-2.f, v[j], nc);
-          v[j] = dv;
-          keep |= (dv <= thr_adj) ? (1u << j) : 0u;
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 nn = n4[j4];
+          v[4 * j4 + 0] = fmaf(-2.f, v[4 * j4 + 0], nn.x);
+          v[4 * j4 + 1] = fmaf(-2.f, v[4 * j4 + 1], nn.y);
+          v[4 * j4 + 2] = fmaf(-2.f, v[4 * j4 + 2], nn.z);
+          v[4 * j4 + 3] = fmaf(-2.f, v[4 * j4 + 3], nn.w);
+          vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
         }
-        keep &= vmask;
+        const bool maybe = vmin <= thr_adj;
+        if (!__any_sync(0xffffffffu, maybe)) continue;
+        unsigned keep = 0;
+        if (maybe) {
+          // columns c0 + j valid for this row, as a bit mask
+          const int32_t rem = lim - (int32_t)c0;
+          unsigned vmask = rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+          const int32_t so = self - (int32_t)c0;
+          if (so >= 0 && so < 32) vmask &= ~(1u << so);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) keep |= (v[j] <= thr_adj) ? (1u << j) : 0u;
+          keep &= vmask;
+        }
         unsigned m = __ballot_sync(0xffffffffu, keep != 0);
         if (!m) continue;
         if (keep) {
