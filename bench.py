@@ -353,6 +353,8 @@ def run_ours(args):
             "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
                           "recall_at_10": p_rec},
             "plain_f32_per_query_launch_qps": per_query_qps,
+            "step_ms_median": 1e3 * statistics.median(times), "step_ms_max": 1e3 * max(times),
+            "qps_of_slowest_step": args.nq / max(times),
             "parallelism": f"replicas{ws}",
         },
         "build_seconds": build_bf16,
