@@ -23,6 +23,7 @@ _lib = None
 
 L2, ANGULAR = 0, 1
 GRAPH_NSW, GRAPH_KNN = 0, 1
+SAMPLER_SAMPLING, SAMPLER_HALVING = 0, 1  # Alg. 2 (sampling + verification) or Alg. 3 V2 (halving)
 
 
 def build(force: bool = False) -> str:
@@ -72,6 +73,11 @@ def lib():
             L.ho_verify.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.POINTER(C.c_int64),
                                     C.c_int64, C.POINTER(C.c_int64), C.c_int64, C.c_uint64, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_uint8)]
+            L.ho_build_layers_halving.restype = C.c_int32
+            L.ho_build_layers_halving.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
+                                                  C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
+            L.ho_halving_positions.restype = C.c_int64
+            L.ho_halving_positions.argtypes = [C.c_uint64, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_int64)]
             L.ho_build_layers.restype = C.c_int32
             L.ho_build_layers.argtypes = [C.POINTER(C.c_float), C.c_int64, C.c_int32, C.c_int32,
                                           C.c_int32, C.c_int32, C.c_double, C.c_int32, C.c_int32,
@@ -173,18 +179,30 @@ def verify(X, prev, net_pos, seed, layer, attempt, r, w, metric=L2, exhaustive=F
     return bool(ok), ring_ok[:r].astype(bool)
 
 
+def halving_positions(s, m, seed, layer):
+    """Alg. 3 (BuildEpsNetDiscV2) on positions 0..s-1: the survivors."""
+    out = np.zeros(max(s, 1), dtype=np.int64)
+    c = lib().ho_halving_positions(seed, layer, s, m, _p(out, C.c_int64))
+    return out[:c].copy()
+
+
 def build_layers(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, metric=L2,
-                 exhaustive=False):
-    """Layer membership (Alg. 1 + Alg. 2).  Returns dict or raises RuntimeError."""
+                 exhaustive=False, sampler=SAMPLER_SAMPLING):
+    """Layer membership (Alg. 1 + Alg. 2, or Alg. 3 halving).  Returns dict
+    or raises RuntimeError."""
     X = _f32(X)
     n, d = X.shape
     sizes = np.zeros(64, dtype=np.int64)
     ids = np.zeros(max(n, 1), dtype=np.int64)
     down = np.zeros(max(n, 1), dtype=np.int64)
     attempts = np.zeros(64, dtype=np.int32)
-    L = lib().ho_build_layers(_p(X, C.c_float), n, d, metric, m, max_layers, c0, r, max_attempts,
-                              seed, int(exhaustive), _p(sizes, C.c_int64), _p(ids, C.c_int64),
-                              _p(down, C.c_int64), _p(attempts, C.c_int32))
+    if sampler == SAMPLER_HALVING:
+        L = lib().ho_build_layers_halving(n, m, max_layers, seed, _p(sizes, C.c_int64), _p(ids, C.c_int64),
+                                          _p(down, C.c_int64))
+    else:
+        L = lib().ho_build_layers(_p(X, C.c_float), n, d, metric, m, max_layers, c0, r, max_attempts,
+                                  seed, int(exhaustive), _p(sizes, C.c_int64), _p(ids, C.c_int64),
+                                  _p(down, C.c_int64), _p(attempts, C.c_int32))
     if L < 0:
         raise RuntimeError("no epsilon-net found within max_attempts")
     layer_ids, layer_down = [np.arange(n, dtype=np.int64)], [None]
@@ -230,9 +248,9 @@ def edge_rule(fwd, fwd_d, Mmax=32, graph=GRAPH_NSW):
 
 
 def build_index(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, M=16, Mmax=32,
-                graph=GRAPH_NSW, metric=L2, exhaustive=False):
+                graph=GRAPH_NSW, metric=L2, exhaustive=False, sampler=SAMPLER_SAMPLING):
     """Full HENN (Alg. 1): layers, per-layer forward lists and adjacency."""
-    idx = build_layers(X, m, max_layers, c0, r, max_attempts, seed, metric, exhaustive)
+    idx = build_layers(X, m, max_layers, c0, r, max_attempts, seed, metric, exhaustive, sampler)
     idx["fwd"], idx["fwd_d"], idx["adj"] = [], [], []
     for i, ids in enumerate(idx["ids"]):
         f, fd = forward_lists(X, ids, seed, i, M, graph, metric)

@@ -153,6 +153,58 @@ int64_t ho_sample_positions(uint64_t seed, int32_t layer, int32_t attempt, int64
   return cnt;
 }
 
+/* Alg. 3 (BuildEpsNetDiscV2): m halving steps, each over an arbitrary
+ * matching of the current set (here: consecutive pairs of the list) keeping
+ * one member of each pair at random. */
+int64_t ho_halving_positions(uint64_t seed, int32_t layer, int64_t s, int32_t m, int64_t* out_pos) {
+  int64_t* cur = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s > 0 ? s : 1));
+  for (int64_t p = 0; p < s; ++p) cur[p] = p;
+  int64_t c = s;
+  for (int32_t step = 0; step < m; ++step) {
+    uint64_t base = ho_derive(ho_derive(ho_derive(seed, HO_TAG_HALVE), (uint64_t)layer), (uint64_t)step);
+    int64_t next = 0;
+    for (int64_t j = 0; 2 * j < c; ++j) {
+      if (2 * j + 1 < c) {
+        uint64_t coin = ho_bounded(ho_derive(base, (uint64_t)j), 2);
+        cur[next++] = cur[2 * j + coin];
+      } else {
+        cur[next++] = cur[2 * j]; /* unmatched last element */
+      }
+    }
+    c = next;
+  }
+  for (int64_t j = 0; j < c; ++j) out_pos[j] = cur[j];
+  free(cur);
+  return c;
+}
+
+int32_t ho_build_layers_halving(int64_t n, int32_t m, int32_t max_layers, uint64_t seed, int64_t* sizes,
+                                int64_t* ids, int64_t* down) {
+  int64_t* prev = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
+  for (int64_t i = 0; i < n; ++i) prev[i] = i;
+  int64_t s = n, off = 0;
+  sizes[0] = n;
+  int32_t L = 0;
+  for (int32_t layer = 1; layer < 64; ++layer) {
+    if (max_layers > 0 && layer > max_layers) break;
+    if (s < (1LL << m)) break;
+    int64_t cnt = ho_halving_positions(seed, layer, s, m, pos);
+    for (int64_t j = 0; j < cnt; ++j) {
+      ids[off + j] = prev[pos[j]];
+      down[off + j] = pos[j];
+    }
+    for (int64_t j = 0; j < cnt; ++j) prev[j] = ids[off + j];
+    off += cnt;
+    s = cnt;
+    sizes[layer] = cnt;
+    L = layer;
+  }
+  free(prev);
+  free(pos);
+  return L;
+}
+
 /* ------------------------------------------------------- IsEpsNet check */
 
 /* One ring range (Def. 2) centred at a point of the previous layer: the

@@ -39,6 +39,7 @@ extern "C" {
 #define HO_TAG_RSTART 0x52535441ULL /* "RSTA": ring start rank */
 #define HO_TAG_ORDER 0x4F524452ULL  /* "ORDR": NSW insertion order */
 #define HO_TAG_ENTRY 0x454E5452ULL  /* "ENTR": random root node, Alg. 4 */
+#define HO_TAG_HALVE 0x48414C56ULL  /* "HALV": coin of each matched pair, Alg. 3 */
 
 #define HO_L2 0
 #define HO_ANGULAR 1
@@ -87,6 +88,20 @@ int32_t ho_build_layers(const float* X, int64_t n, int32_t d, int32_t metric, in
                         int32_t max_layers, double c0, int32_t r, int32_t max_attempts,
                         uint64_t seed, int32_t exhaustive, int64_t* sizes, int64_t* ids,
                         int64_t* down, int32_t* attempts);
+
+/* Alg. 3 BuildEpsNetDiscV2: m halving steps of the positions 0..s-1 of the
+ * previous layer.  Each step matches the current list in consecutive pairs
+ * (positions 2j, 2j+1 of the list: one arbitrary matching), keeps one
+ * member of each pair by a coin, bounded(derive(derive(derive(derive(seed,
+ * HALV), layer), step), j), 2), and keeps an unmatched last element.
+ * Writes the surviving positions in ascending order; returns their count. */
+int64_t ho_halving_positions(uint64_t seed, int32_t layer, int64_t s, int32_t m, int64_t* out_pos);
+
+/* Alg. 1 hierarchy with the halving sampler instead of Alg. 2: layers while
+ * |L_{i-1}| >= 2^m (and i <= max_layers when set).  Same outputs as
+ * ho_build_layers; no verification, so no attempts. */
+int32_t ho_build_layers_halving(int64_t n, int32_t m, int32_t max_layers, uint64_t seed, int64_t* sizes,
+                                int64_t* ids, int64_t* down);
 
 /* Forward lists of one layer: for each point p the M nearest by (dist,
  * index) among points of lower insertion rank (graph=NSW) or among all other

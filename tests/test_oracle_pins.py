@@ -532,3 +532,51 @@ def test_e4m3_rounding_matches_library():
     big = np.array([448.5, 449, 460, 480, 1e6, np.inf, -500], dtype=np.float32)
     codes = O.e4m3_bits(big)
     assert all(abs(O.e4m3_value(int(c))) == 448 for c in codes)
+
+
+# ------------------------------------------------ Alg. 3 halving sampler
+
+def test_halving_sizes_and_pairs():
+    """BuildEpsNetDiscV2 (Alg. 3): each halving step keeps exactly one point
+    of every matched pair (here consecutive list entries) and the unmatched
+    last one, so m steps leave ceil-halved m times; survivors are sorted."""
+    for s in [1, 2, 3, 17, 100, 1023, 4096]:
+        for m in [1, 2, 4]:
+            want = s
+            for _ in range(m):
+                want = (want + 1) // 2
+            p = O.halving_positions(s, m, seed=5, layer=1)
+            assert len(p) == want
+            assert np.all(np.diff(p) > 0)
+    p = O.halving_positions(101, 1, seed=9, layer=2)
+    assert [int(v) // 2 for v in p] == list(range(51))  # one of (2j, 2j+1), and 100 unmatched
+    assert p[-1] == 100
+
+
+def test_halving_survival_is_uniform():
+    """Every point survives m steps with probability 2^-m: over 4000 seeds,
+    each of 64 positions survives 2 steps about 1000 times (binomial, 6 sd)."""
+    counts = np.zeros(64)
+    for seed in range(4000):
+        counts[O.halving_positions(64, 2, seed=seed, layer=1)] += 1
+    assert counts.sum() == 4000 * 16
+    sd = math.sqrt(4000 * 0.25 * 0.75)
+    assert np.all(np.abs(counts - 1000) < 6 * sd)
+
+
+def test_halving_layers_ignore_values():
+    """The halving hierarchy depends on sizes and the seed only: two point
+    sets of the same size get the same layers, |L_i| halves m times per
+    layer, and down pointers index the layer below."""
+    X1 = synth.uniform_cube(5000, 8, seed=1)
+    X2 = synth.gaussian_mixture(5000, 8, 10, seed=2)[0]
+    a = O.build_layers(X1, m=3, seed=4, sampler=O.SAMPLER_HALVING)
+    b = O.build_layers(X2, m=3, seed=4, sampler=O.SAMPLER_HALVING)
+    assert a["L"] == b["L"] and all(np.array_equal(u, v) for u, v in zip(a["ids"], b["ids"]))
+    for i in range(1, a["L"] + 1):
+        prev = a["ids"][i - 1]
+        assert np.array_equal(prev[a["down"][i]], a["ids"][i])
+        want = len(prev)
+        for _ in range(3):
+            want = (want + 1) // 2
+        assert len(a["ids"][i]) == want
