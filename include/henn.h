@@ -55,6 +55,7 @@ extern "C" {
 #define HENN_TAG_RSTART 0x52535441ULL  /* "RSTA" first rank of a sampled ring range    */
 #define HENN_TAG_ORDER 0x4F524452ULL   /* "ORDR" NSW insertion order of a layer        */
 #define HENN_TAG_ENTRY 0x454E5452ULL   /* "ENTR" random top-layer node of a query      */
+#define HENN_TAG_HALVE 0x48414C56ULL   /* "HALV" coin of a matched pair, Alg. 3 halving */
 
 typedef enum {
   HENN_OK = 0,
@@ -76,6 +77,12 @@ typedef enum { HENN_F32 = 0, HENN_BF16 = 1, HENN_FP8E4M3 = 2 } henn_storage;
 /* Navigable graph of each layer (App. C; App. F "Navigation Graphs"). */
 typedef enum { HENN_GRAPH_NSW = 0, HENN_GRAPH_KNN = 1 } henn_graph;
 
+/* Layer sampler: SAMPLING = Alg. 2 (draws with replacement, ring-range
+ * verification, Las-Vegas retries); HALVING = Alg. 3 BuildEpsNetDiscV2 (m
+ * halving steps over a matching of consecutive list entries, one member of
+ * each pair kept by a coin, no verification). */
+typedef enum { HENN_SAMPLER_SAMPLING = 0, HENN_SAMPLER_HALVING = 1 } henn_sampler;
+
 /* Engine for the construction distance tiles: AUTO = tcgen05 where it
  * applies (d <= 128, M <= 16), else SIMT FP32. */
 typedef enum { HENN_TILES_AUTO = 0, HENN_TILES_SIMT = 1, HENN_TILES_TCGEN05 = 2 } henn_tiles;
@@ -96,6 +103,7 @@ typedef struct {
   int32_t Mmax;          /* adjacency row width; 32 (only 32 is supported)      */
   int32_t tiles;         /* henn_tiles                                          */
   uint64_t seed;         /* index seed                                          */
+  int32_t sampler;       /* henn_sampler; default SAMPLING                      */
 } henn_build_params;
 
 /* Fills *p with the defaults above (struct_size included). */
@@ -111,7 +119,9 @@ typedef struct henn_index henn_index; /* opaque, owned by the library */
  * L_{i-1} with replacement (Alg. 2, Cor. 2), keep the distinct ones, accept
  * them when every one of num_ranges random ring ranges (Def. 2) holding
  * floor(eps*s)+1 points, eps from Eq. 1, contains one of them (IsEpsNet,
- * App. C practical implementation), else draw again.  Every layer then gets
+ * App. C practical implementation), else draw again; with
+ * sampler = HENN_SAMPLER_HALVING the layer is instead m halving steps of
+ * L_{i-1} (Alg. 3, BuildEpsNetDiscV2).  Every layer then gets
  * its navigable graph: each point links to the M nearest points inserted
  * before it (NSW, App. C; or its M nearest overall for HENN_GRAPH_KNN) and
  * each row keeps its nearest predecessor plus the nearest Mmax-1 of its

@@ -5,7 +5,8 @@ run in CUDA kernels for sm_103a behind the C ABI of include/henn.h; this
 package is the Python binding.  `build()` compiles the library in tree.
 """
 from .binding import (  # noqa: F401
-    ANGULAR, BF16, F32, FP8E4M3, GRAPH_KNN, GRAPH_NSW, L2, TILES_AUTO, TILES_SIMT, TILES_TCGEN05,
+    ANGULAR, BF16, F32, FP8E4M3, GRAPH_KNN, GRAPH_NSW, L2, SAMPLER_HALVING, SAMPLER_SAMPLING, TILES_AUTO, TILES_SIMT,
+    TILES_TCGEN05,
     HennError, Index, Server, exact_knn, load, quantize_rows,
 )
 

@@ -23,6 +23,7 @@ L2, ANGULAR = 0, 1
 F32, BF16, FP8E4M3 = 0, 1, 2
 GRAPH_NSW, GRAPH_KNN = 0, 1
 TILES_AUTO, TILES_SIMT, TILES_TCGEN05 = 0, 1, 2
+SAMPLER_SAMPLING, SAMPLER_HALVING = 0, 1
 MAX_LAYERS = 32
 
 STATUS = {
@@ -79,6 +80,7 @@ class BuildParams(C.Structure):
         ("Mmax", C.c_int32),
         ("tiles", C.c_int32),
         ("seed", C.c_uint64),
+        ("sampler", C.c_int32),
     ]
 
 
@@ -234,7 +236,8 @@ class Index:
     """A HENN index resident in device memory (henn_build / henn_free)."""
 
     def __init__(self, X, metric=L2, storage=F32, graph=GRAPH_NSW, m=4, max_layers=0, eps_c0=1.0,
-                 num_ranges=100, max_attempts=64, M=16, Mmax=32, tiles=TILES_AUTO, seed=0, stream=None):
+                 num_ranges=100, max_attempts=64, M=16, Mmax=32, tiles=TILES_AUTO, seed=0, stream=None,
+                 sampler=SAMPLER_SAMPLING):
         L = load()
         p = BuildParams()
         L.henn_build_params_default(C.byref(p))
@@ -242,6 +245,7 @@ class Index:
         p.m, p.max_layers, p.eps_c0 = m, max_layers, float(eps_c0)
         p.num_ranges, p.max_attempts, p.M, p.Mmax, p.tiles = num_ranges, max_attempts, M, Mmax, tiles
         p.seed = seed & 0xFFFFFFFFFFFFFFFF
+        p.sampler = int(sampler)
         if _is_torch(X):
             import torch
 

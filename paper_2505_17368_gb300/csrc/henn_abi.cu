@@ -200,6 +200,7 @@ extern "C" void henn_build_params_default(henn_build_params* p) {
   p->Mmax = 32;
   p->tiles = HENN_TILES_AUTO;
   p->seed = 0;
+  p->sampler = HENN_SAMPLER_SAMPLING;
 }
 
 extern "C" void henn_search_params_default(henn_search_params* sp) {
@@ -447,6 +448,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     require(p.storage >= HENN_F32 && p.storage <= HENN_FP8E4M3, "storage");
     require(p.graph == HENN_GRAPH_NSW || p.graph == HENN_GRAPH_KNN, "graph");
     require(p.m >= 1 && p.m <= 8, "m must be in [1, 8]");
+    require(p.sampler == HENN_SAMPLER_SAMPLING || p.sampler == HENN_SAMPLER_HALVING, "sampler");
     require(p.max_layers >= 0 && p.max_layers < HENN_MAX_LAYERS, "max_layers");
     require(p.eps_c0 > 0.0 && std::isfinite(p.eps_c0), "eps_c0 must be > 0");
     require(p.num_ranges >= 1 && p.num_ranges <= 4096, "num_ranges must be in [1, 4096]");
@@ -518,8 +520,16 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
         if (s < decay) break;
         int64_t count = 0;
         int32_t amb = 0;
-        int32_t a = build_layer_membership(ix, p, layer, s, ix->layers[layer - 1].ids, sc, flags, tile_buf, d_total,
-                                           pos, ids, &count, &amb, st);
+        int32_t a = 0;
+        if (p.sampler == HENN_SAMPLER_HALVING) {
+          // Alg. 3 (BuildEpsNetDiscV2): m halving steps, no verification;
+          // `ids` doubles as the ping-pong buffer until the ids are written
+          count = launch_halving(ix->seed, layer, s, p.m, ix->layers[layer - 1].ids, ids, pos, ids, st);
+          CKL("halving");
+        } else {
+          a = build_layer_membership(ix, p, layer, s, ix->layers[layer - 1].ids, sc, flags, tile_buf, d_total, pos,
+                                     ids, &count, &amb, st);
+        }
         if (a < 0)
           throw Failure(HENN_ERR_EPSNET_NOT_FOUND,
                         "no eps-net for layer " + std::to_string(layer) + " within max_attempts");

@@ -31,6 +31,11 @@ void launch_ring_params(uint64_t bc, uint64_t bs, int32_t r, int64_t s, int64_t 
 void launch_ring_dist(const float* x32, int32_t dpad, const int32_t* prev_ids, int64_t s,
                       const int32_t* centre, int32_t r, int32_t metric, const float* inv_norm, float* D,
                       cudaStream_t st);
+// Alg. 3 halving: m steps over positions 0..s-1; the survivors (ascending)
+// land in pos and their global ids in ids; returns their count.  tmp holds
+// ceil(s/2) entries.
+int64_t launch_halving(uint64_t seed, int32_t layer, int64_t s, int32_t m, const int32_t* prev_ids, int32_t* tmp,
+                       int32_t* pos, int32_t* ids, cudaStream_t st);
 void launch_ring_select_decide(const float* D, int64_t s, const int64_t* start, int64_t w, int32_t r,
                                const int32_t* net_pos, const int64_t* nnet_dev, double er, double ea, float* lo,
                                float* hi, int32_t* status, cudaStream_t st);

@@ -172,6 +172,49 @@ void launch_offsets(const int32_t* counts, int64_t s, int64_t* tile_buf, int64_t
   k_write_offsets<<<tiles, kScanThreads, 0, st>>>(counts, s, tile_buf, out_offsets);
 }
 
+// ------------------------------------------------------ halving (Alg. 3)
+
+// One halving step of BuildEpsNetDiscV2: the current list (in, c entries;
+// nullptr = positions 0..c-1) is matched in consecutive pairs, pair j keeps
+// in[2j + coin], coin = bounded(derive(base, j), 2); an unmatched last entry
+// is kept.  out[j] for j < ceil(c / 2).
+__global__ void k_halve_step(const int32_t* __restrict__ in, int64_t c, uint64_t base, int32_t* __restrict__ out) {
+  const int64_t half = (c + 1) / 2;
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < half; j += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t pick = 2 * j + 1 < c ? 2 * j + (int64_t)bounded(derive(base, (uint64_t)j), 2) : 2 * j;
+    out[j] = in ? in[pick] : (int32_t)pick;
+  }
+}
+
+__global__ void k_positions_to_ids(const int32_t* __restrict__ pos, int64_t cnt, const int32_t* __restrict__ prev_ids,
+                                   int32_t* __restrict__ ids) {
+  for (int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; j < cnt; j += (int64_t)gridDim.x * blockDim.x)
+    ids[j] = prev_ids ? prev_ids[pos[j]] : pos[j];
+}
+
+int64_t launch_halving(uint64_t seed, int32_t layer, int64_t s, int32_t m, const int32_t* prev_ids, int32_t* tmp,
+                       int32_t* pos, int32_t* ids, cudaStream_t st) {
+  // ping-pong so that the last step lands in pos
+  int64_t c = s;
+  const int32_t* in = nullptr;
+  for (int32_t step = 0; step < m; ++step) {
+    int32_t* out = ((m - 1 - step) & 1) ? tmp : pos;
+    const uint64_t base = derive(derive(derive(seed, HENN_TAG_HALVE), (uint64_t)layer), (uint64_t)step);
+    const int64_t half = (c + 1) / 2;
+    int grid = (int)((half + 255) / 256);
+    if (grid > 152 * 16) grid = 152 * 16;
+    if (grid < 1) grid = 1;
+    k_halve_step<<<grid, 256, 0, st>>>(in, c, base, out);
+    in = out;
+    c = half;
+  }
+  int grid = (int)((c + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (grid < 1) grid = 1;
+  k_positions_to_ids<<<grid, 256, 0, st>>>(pos, c, prev_ids, ids);
+  return c;
+}
+
 // ---------------------------------------------------------- ring ranges
 
 __global__ void k_ring_params(uint64_t bc, uint64_t bs, int32_t r, uint64_t s, uint64_t span,

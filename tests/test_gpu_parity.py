@@ -206,6 +206,20 @@ def test_graph_parity_uncertified_rows(case):
     _graph_parity(gidx, oidx, X)
 
 
+@pytest.mark.parametrize("graph", ["nsw", "knn"])
+def test_halving_sampler_parity(graph):
+    """Layers from the halving sampler of Alg. 3 (BuildEpsNetDiscV2) are
+    bit-exact against the oracle's, and the graphs built on them match."""
+    X = synth.uniform_cube(6001, 24, seed=11)
+    kw, okw = dict(seed=3, sampler=H.SAMPLER_HALVING), dict(seed=3, sampler=O.SAMPLER_HALVING)
+    if graph == "knn":
+        kw["graph"], okw["graph"] = H.GRAPH_KNN, O.GRAPH_KNN
+    oidx = O.build_index(X, **okw)
+    gidx = _gpu_index(X, **kw)
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+
+
 def test_tcgen05_tiles_reject_wide_rows():
     with pytest.raises(H.HennError) as e:
         _gpu_index(synth.uniform_cube(500, 200, seed=1), tiles=H.TILES_TCGEN05)
