@@ -102,7 +102,7 @@ def lib():
                                     C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_int32), C.c_int32, C.POINTER(C.c_float), C.c_int64,
                                     C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_int32, C.c_int32, C.c_int32,
-                                    C.c_uint64,
+                                    C.c_int64, C.c_uint64,
                                     C.POINTER(C.c_uint64), C.POINTER(C.c_int64),
                                     C.POINTER(C.c_double), C.c_int32, C.POINTER(C.c_int64)]
             L.ho_greedy_layer.restype = C.c_int64
@@ -262,7 +262,7 @@ def build_index(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, M=
 
 
 def search(idx, X, Q, k=10, ef=64, keys=None, out_stride=None, seed=None, ef_upper=1, ef_l1=0,
-           descend_all=0):
+           descend_all=0, exact_upper=0):
     """Alg. 4 descent + layer-0 beam.  Returns (ids int64, dists f64, stats)."""
     X, Q = _f32(X), _f32(Q)
     n, d = X.shape
@@ -286,7 +286,7 @@ def search(idx, X, Q, k=10, ef=64, keys=None, out_stride=None, seed=None, ef_upp
     lib().ho_search(_p(X, C.c_float), n, d, idx["metric"], L + 1, _p(sizes, C.c_int64),
                     _p(ids, C.c_int64), _p(down, C.c_int64), _p(adj, C.c_int32), Mmax,
                     _p(Q, C.c_float), nq, _p(kq, C.c_int32), _p(efq, C.c_int32), int(ef_upper), int(ef_l1),
-                    int(descend_all),
+                    int(descend_all), int(exact_upper),
                     idx["seed"] if seed is None else seed,
                     None if keys_a is None else _p(keys_a, C.c_uint64),
                     _p(out_ids, C.c_int64), _p(out_d, C.c_double), stride, _p(stats, C.c_int64))

@@ -565,11 +565,26 @@ static void beam_layer(const float* X, int32_t d, int32_t metric, const int64_t*
  * candidates at each step) whose best node is taken down; the width is
  * ef_upper, or ef_l1 on layer 1 when ef_l1 > 0.  Layer 0 runs the beam of width
  * max(ef, k) and returns its first k entries. */
+/* The exact candidate set of one layer: the `width` points of the layer
+ * nearest to q in (distance, index) order, written to W; returns their
+ * number.  Used for upper layers of at most exact_upper points. */
+static int64_t exact_layer(const float* X, int32_t d, int32_t metric, const int64_t* ids, int64_t s,
+                           const float* q, int32_t width, pair_t* C, pair_t* W) {
+  for (int64_t j = 0; j < s; ++j) {
+    C[j].d = ho_dist(q, layer_point(X, d, ids, j), d, metric);
+    C[j].i = j;
+  }
+  qsort(C, (size_t)s, sizeof(pair_t), pair_cmp);
+  int64_t nw = width < s ? width : s;
+  for (int64_t j = 0; j < nw; ++j) W[j] = C[j];
+  return nw;
+}
+
 void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nlayers,
                const int64_t* sizes, const int64_t* ids, const int64_t* down, const int32_t* adj,
                int32_t Mmax, const float* Q, int64_t nq, const int32_t* k, const int32_t* ef,
-               int32_t ef_upper, int32_t ef_l1, int32_t descend_all, uint64_t seed, const uint64_t* keys,
-               int64_t* out_ids, double* out_d, int32_t out_stride, int64_t* stats) {
+               int32_t ef_upper, int32_t ef_l1, int32_t descend_all, int64_t exact_upper, uint64_t seed,
+               const uint64_t* keys, int64_t* out_ids, double* out_d, int32_t out_stride, int64_t* stats) {
   int32_t L = nlayers - 1;
   /* offsets of each layer inside the concatenated arrays */
   int64_t id_off[66], adj_off[66];
@@ -607,7 +622,18 @@ void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nla
     for (int32_t i = L; i >= 1; --i) {
       int64_t c;
       const int32_t width = (i == 1 && ef_l1 > 0) ? ef_l1 : ef_upper;
-      if (width <= 1) {
+      if (sizes[i] <= exact_upper) {
+        /* a small layer: its exact candidate set instead of the walk */
+        nw = exact_layer(X, d, metric, ids + id_off[i], sizes[i], q, width > 1 ? width : 1, C, W);
+        evals += sizes[i];
+        if (descend_all && width > 1) {
+          for (int64_t t = 0; t < nw; ++t) seeds[t] = down[id_off[i] + W[t].i];
+          nseeds = nw;
+        } else {
+          seeds[0] = down[id_off[i] + W[0].i];
+          nseeds = 1;
+        }
+      } else if (width <= 1) {
         int64_t h = 0, ev = 0;
         c = ho_greedy_layer(X, d, metric, ids + id_off[i], adj + adj_off[i], Mmax, q, seeds[0], &h, &ev);
         hops_upper += h;

@@ -124,7 +124,9 @@ void ho_edge_rule(const int32_t* fwd, const double* fwd_d, int64_t s, int32_t M,
 
 /* Query (Alg. 4 + candidate-set beam on layer 0; ef_upper > 1 runs a beam
  * of that width on layers >= 1 too, ef_l1 > 0 overrides it on layer 1,
- * descend_all enters each layer at all candidates of the beam above).
+ * descend_all enters each layer at all candidates of the beam above;
+ * upper layers of at most exact_upper points give their exact candidate set
+ * of that width instead of a walk, 0 = never).
  * nlayers = L + 1; sizes[0] = n.  ids/down: concatenated for layers 1..L;
  * adj: concatenated per layer 0..L, Mmax per row.  k[q], ef[q] per query.
  * out_ids (int64) / out_d (double) have stride out_stride; distances are
@@ -134,8 +136,8 @@ void ho_edge_rule(const int32_t* fwd, const double* fwd_d, int64_t s, int32_t M,
 void ho_search(const float* X, int64_t n, int32_t d, int32_t metric, int32_t nlayers,
                const int64_t* sizes, const int64_t* ids, const int64_t* down, const int32_t* adj,
                int32_t Mmax, const float* Q, int64_t nq, const int32_t* k, const int32_t* ef,
-               int32_t ef_upper, int32_t ef_l1, int32_t descend_all, uint64_t seed, const uint64_t* keys,
-               int64_t* out_ids, double* out_d, int32_t out_stride, int64_t* stats);
+               int32_t ef_upper, int32_t ef_l1, int32_t descend_all, int64_t exact_upper, uint64_t seed,
+               const uint64_t* keys, int64_t* out_ids, double* out_d, int32_t out_stride, int64_t* stats);
 
 /* Greedy search on one layer (Alg. 4 GreedySearch); returns the local index
  * reached and writes the number of moves to *hops. */

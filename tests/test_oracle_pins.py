@@ -580,3 +580,21 @@ def test_halving_layers_ignore_values():
         for _ in range(3):
             want = (want + 1) // 2
         assert len(a["ids"][i]) == want
+
+
+def test_exact_upper_layers_pick_true_nearest():
+    """With exact_upper covering the upper layers, layer 1 hands layer 0 the
+    copy of the query's true nearest layer-1 point (scipy brute force), and
+    a width-1 search on layer 0 is GreedySearch from there (Alg. 4)."""
+    X = synth.uniform_cube(3000, 8, seed=21)
+    Q = synth.uniform_cube(60, 8, seed=22)
+    idx = O.build_index(X, seed=5)
+    ids1 = idx["ids"][1]
+    near1 = np.argmin(cdist(Q.astype(np.float64), X[ids1].astype(np.float64), "sqeuclidean"), axis=1)
+    start0 = idx["down"][1][near1]
+    got, _, st = O.search(idx, X, Q, k=1, ef=1, ef_upper=1, exact_upper=10**9)
+    for q in range(len(Q)):
+        want, _, _ = O.greedy_layer(X, None, idx["adj"][0], Q[q], int(start0[q]))
+        assert got[q, 0] == want
+    # every upper-layer point is evaluated once per query
+    assert np.all(st[:, 0] >= sum(len(a) for a in idx["ids"][1:]))
