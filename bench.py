@@ -37,11 +37,13 @@ import synth  # noqa: E402
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
 EF_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
-# (ef_upper, descend_all, ef_l1): beam width on the upper layers, whether
+# (ef_upper, descend_all, ef_l1, exact_upper): beam width on the upper layers, whether
 # each layer is entered at all candidates of the layer above, and the beam
 # width on layer 1 (0 = ef_upper)
-UPPER_SWEEP = [(1, 0, 0), (32, 0, 0), (48, 0, 0), (48, 1, 0), (56, 0, 0), (64, 0, 0), (64, 1, 0), (64, 0, 16),
-               (64, 0, 32), (80, 0, 16), (96, 0, 16), (128, 0, 16), (128, 1, 16)]
+UPPER_SWEEP = [(1, 0, 0, 0), (32, 0, 0, 0), (48, 0, 0, 0), (48, 1, 0, 0), (56, 0, 0, 0), (64, 0, 0, 0),
+               (64, 1, 0, 0), (64, 0, 16, 0), (64, 0, 32, 0), (80, 0, 16, 0), (96, 0, 16, 0), (128, 0, 16, 0),
+               (128, 1, 16, 0),
+               (32, 0, 0, 256), (48, 1, 0, 256), (64, 0, 0, 256), (64, 1, 0, 256), (64, 0, 16, 256)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -187,7 +189,8 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
     return times, ids
 
 
-def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1, l1: int = 0, da: int = 0):
+def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1, l1: int = 0, da: int = 0,
+                    xu: int = 0):
     """The FP64 oracle (as it stands) on the host cores: its own index on
     the first n_sample points of the workload stream (built with all
     cores), then the same beam configuration answering nq_sample queries
@@ -203,12 +206,12 @@ def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int
     secs = []
     for _ in range(steps):
         t0 = time.perf_counter()
-        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da)
+        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
         secs.append(time.perf_counter() - t0)
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
     t0 = time.perf_counter()
-    oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da)
+    oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
     all_cores = (nq_sample / (time.perf_counter() - t0), ncores)
     return nq_sample / statistics.median(secs), 1, secs, all_cores
 
@@ -271,15 +274,16 @@ def run_ours(args):
     # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
     def sweep(index, tag):
         best = None
-        for efu, da, l1 in UPPER_SWEEP:
+        for efu, da, l1, xu in UPPER_SWEEP:
             for ef in EF_SWEEP:
-                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream, descend_all=da, ef_l1=l1)
+                t, ids = _timed_search(index, Qd, ef, efu, 2, 1, None, stream, descend_all=da, ef_l1=l1,
+                                       shape={"exact_upper": xu})
                 r = _recall(ids.cpu().numpy(), gt)
-                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} ef={ef} recall@10={r:.4f} "
-                      f"ms={1e3 * min(t):.3f}", file=sys.stderr, flush=True)
+                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} exact_upper={xu} ef={ef} "
+                      f"recall@10={r:.4f} ms={1e3 * min(t):.3f}", file=sys.stderr, flush=True)
                 if r >= RECALL_TARGET:
-                    if best is None or min(t) < best[4]:
-                        best = (ef, efu, da, l1, min(t), r)
+                    if best is None or min(t) < best[5]:
+                        best = (ef, efu, da, l1, xu, min(t), r)
                     break
         return best
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
@@ -287,11 +291,13 @@ def run_ours(args):
     plain = sweep(idx_f32, "f32")
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, da, l1, _, rec = chosen
+    ef, efu, da, l1, xu, _, rec = chosen
     # ---- launch shape (warps per block, visited-table size) by the autotuner
     from paper_2505_17368_gb300 import autotune
 
-    shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, use_cache=False)
+    shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
+                          use_cache=False)
+    shape = dict(shape, exact_upper=xu)
     # ---- algorithmic bytes per launch from the kernel's own counters
     _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)
     st = st.cpu().numpy().astype(np.int64)
@@ -313,9 +319,9 @@ def run_ours(args):
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
     # plain FP32 comparator, same procedure
-    p_ef, p_efu, p_da, p_l1, _, p_rec = plain
+    p_ef, p_efu, p_da, p_l1, p_xu, _, p_rec = plain
     p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da,
-                               ef_l1=p_l1)
+                               ef_l1=p_l1, shape={"exact_upper": p_xu})
     plain_qps = args.nq / statistics.median(p_times)
     # one launch per query, FP32 (latency form), on a sample
     ns = min(200, args.nq)
@@ -323,7 +329,8 @@ def run_ours(args):
     for q in range(ns):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, ef_l1=p_l1, stream=stream)
+        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, ef_l1=p_l1, exact_upper=p_xu,
+                       stream=stream)
         e1.record(stream)
         e1.synchronize()
         t_one.append(e0.elapsed_time(e1) / 1e3)
@@ -340,17 +347,18 @@ def run_ours(args):
     peaks, src = _peaks()
     avg = statistics.mean(times)
     achieved = alg_bytes / avg / 1e9
-    traffic = _profile_traffic((ef, efu, da, l1))
+    traffic = _profile_traffic((ef, efu, da, l1, xu))
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
-            "descend_all": da, "ef_l1": l1, "launch_shape": shape,
+            "descend_all": da, "ef_l1": l1, "exact_upper": xu, "launch_shape": shape,
             "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
             "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
+                          "exact_upper": p_xu,
                           "recall_at_10": p_rec},
             "plain_f32_per_query_launch_qps": per_query_qps,
             "step_ms_median": 1e3 * statistics.median(times), "step_ms_max": 1e3 * max(times),
@@ -369,9 +377,10 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        qps, cores, secs, (qps_all, ncores) = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq, l1=l1, da=da)
+        qps, cores, secs, (qps_all, ncores) = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq, l1=l1, da=da,
+                                                                xu=xu)
         sample = (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
-                  f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, ef_l1={l1}, descend_all={da}")
+                  f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, ef_l1={l1}, descend_all={da}, exact_upper={xu}")
         line["cpu_baseline"] = {
             "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
             "sample": sample + f", answered sequentially on one core (the paper's protocol), {sum(secs):.1f} s of search",
@@ -421,7 +430,7 @@ def _profile_traffic(beam):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 kv[k.strip()] = v.strip().strip("`")
-        want = "ef={} ef_upper={} descend_all={} ef_l1={}".format(*beam)
+        want = "ef={} ef_upper={} descend_all={} ef_l1={} exact_upper={}".format(*beam)
         if kv.get("search.cu sha256[:16]") == sha and kv.get("beam") == want:
             return float(kv["dram bytes per launch"])
     except (OSError, KeyError, ValueError):

@@ -159,6 +159,11 @@ typedef struct {
                                  all candidates of the layer above instead of the
                                  best one only (default 0)                          */
   int32_t ef_l1;              /* beam width on layer 1 only; 0 = ef_upper          */
+  int32_t exact_upper;        /* upper layers of at most this many points give
+                                 their exact candidate set (the layer's nearest
+                                 max(width, 1) points, every point evaluated)
+                                 instead of a walk; 0 = never (default); at most
+                                 2^(hash_bits - 1)                                  */
 } henn_search_params;
 
 void henn_search_params_default(henn_search_params* sp);

@@ -99,6 +99,7 @@ class SearchParams(C.Structure):
         ("ef_upper", C.c_int32),
         ("descend_all", C.c_int32),
         ("ef_l1", C.c_int32),
+        ("exact_upper", C.c_int32),
     ]
 
 
@@ -318,7 +319,8 @@ class Index:
         return node, dist, hops
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
-               warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None):
+               warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None,
+               exact_upper=0):
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
@@ -355,6 +357,7 @@ class Index:
         sp.ef_upper = int(ef_upper)
         sp.descend_all = int(descend_all)
         sp.ef_l1 = int(ef_l1)
+        sp.exact_upper = int(exact_upper)
         if keys is not None:
             p, _, kk = _ptr(keys)
             sp.query_keys = p

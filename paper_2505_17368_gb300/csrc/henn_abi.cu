@@ -673,6 +673,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     const int rerank = idx->storage != HENN_F32;
     require(sp.ef_upper >= 0 && sp.ef_upper <= 4096, "ef_upper must be in [0, 4096]");
     require(sp.ef_l1 >= 0 && sp.ef_l1 <= 4096, "ef_l1 must be in [0, 4096]");
+    require(sp.exact_upper >= 0, "exact_upper must be >= 0");
     // beam capacity of a query: the power of two holding its widest list
     auto cap_of = [&](int32_t kq, int32_t efq) {
       int nd = std::max(std::max(kq, efq), std::max((int)sp.ef_upper, (int)sp.ef_l1));
@@ -684,6 +685,10 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     const int ef_cap = cap_of(kmax, efmax);
     int hb = sp.hash_bits > 0 ? sp.hash_bits : pick_hash_bits(ef_cap);
     require(hb >= 8 && hb <= 15, "hash_bits must be in [8, 15]");
+    // the exact layers' keys sit in the visited table; capacity-group launches
+    // (default table sizes) use at least 2^10 slots
+    const int hb_min = sp.hash_bits > 0 ? hb : 10;
+    require(sp.exact_upper <= (1 << (hb_min - 1)), "exact_upper must be <= 2^(hash_bits - 1) (512 by default)");
     int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
     require(warps >= 1 && warps <= kSearchWarps, "warps_per_block must be in [1, 4]");
 
@@ -769,6 +774,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.ef_upper = sp.ef_upper;
     a.descend_all = sp.descend_all;
     a.ef_l1 = sp.ef_l1;
+    a.exact_upper = sp.exact_upper;
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.keys = dkeys;

@@ -432,7 +432,50 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
   for (int li = a.L; li >= 1; --li) {
     const SearchLayer Ly = a.layers[li];
     const int width = (li == 1 && a.ef_l1 > 0) ? a.ef_l1 : a.ef_upper;
-    if (width > 1) {
+    if (Ly.size <= a.exact_upper) {
+      // a small layer: its exact candidate set, the nearest max(width, 1)
+      // points by (distance, index), every point evaluated; the keys sit in
+      // the visited table's space (the next walk clears it)
+      const int s = (int)Ly.size;
+      uint64_t* keys = reinterpret_cast<uint64_t*>(table);
+      const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
+      for (int c0 = 0; c0 < s; c0 += 32) {
+        const int cnt = min(32, s - c0);
+        const float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, c0 + lane, cnt, qs, nchunk);
+        if (lane < cnt) keys[c0 + lane] = pack(dn, (uint32_t)(c0 + lane));
+      }
+      evals += s;
+      int P = 1;
+      while (P < s) P <<= 1;
+      for (int i = s + lane; i < P; i += 32) keys[i] = kEmpty;
+      __syncwarp();
+      for (int size = 2; size <= P; size <<= 1)
+        for (int half = size >> 1; half > 0; half >>= 1) {
+          for (int i = lane; i < P; i += 32) {
+            const int j = i ^ half;
+            if (j > i) {
+              const uint64_t x = keys[i], y = keys[j];
+              if ((x > y) == ((i & size) == 0)) {
+                keys[i] = y;
+                keys[j] = x;
+              }
+            }
+          }
+          __syncwarp();
+        }
+      const int nw = min(min(max(width, 1), EFCAP), s);
+      for (int j = lane; j < nw; j += 32) W[j] = keys[j];
+      __syncwarp();
+      cur = (int32_t)key_index(W[0]);
+      if (a.descend_all && width > 1) {
+        for (int j = lane; j < nw; j += 32) {
+          const uint64_t e = W[j];
+          W[j] = (e & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(e)];
+        }
+        nseed = nw;
+      }
+      __syncwarp();
+    } else if (width > 1) {
       int ex = 0;
       int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(width, EFCAP), W, table, HB, stage, qs, evals, ex,
                                 evictions, nseed);

@@ -32,6 +32,7 @@ struct SearchArgs {
   int32_t ef_upper;           // beam width on layers >= 1 (<= 1: greedy)
   int32_t descend_all;        // enter each layer at all candidates of the layer above
   int32_t ef_l1;              // beam width on layer 1 (0: ef_upper)
+  int32_t exact_upper;        // upper layers of at most this many points: exact candidate set
   int32_t ef_cap, hash_bits;  // beam capacity and log2 visited slots per warp
   const uint64_t* keys;
   uint64_t entry_key;  // derive(seed, ENTR)

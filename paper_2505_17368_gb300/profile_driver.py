@@ -1,7 +1,7 @@
 """Small, fixed workloads for profiling the kernels under ncu.
 
     python -m paper_2505_17368_gb300.profile_driver search [--n 1000000] [--nq 10000] [--ef 64] [--ef-upper 64]
-                                                          [--descend-all 0] [--ef-l1 0]
+                                                          [--descend-all 0] [--ef-l1 0] [--exact-upper 0]
     python -m paper_2505_17368_gb300.profile_driver tiles  [--n 200000]
 
 `search` builds a BF16 index of the n-point prefix of the 1M x 128 mixture
@@ -34,6 +34,7 @@ def main():
     ap.add_argument("--ef-upper", type=int, default=64)
     ap.add_argument("--descend-all", type=int, default=0)
     ap.add_argument("--ef-l1", type=int, default=0)
+    ap.add_argument("--exact-upper", type=int, default=0)
     a = ap.parse_args()
     n = a.n or (1_000_000 if a.what == "search" else 200_000)
     X, Q, _ = synth.workload("mixture-1m-d128", n=n, nq=a.nq)
@@ -47,7 +48,8 @@ def main():
     Qd = torch.from_numpy(Q).cuda()
     idx = H.Index(Xd, storage=H.BF16, seed=0)
     for _ in range(3):
-        ids, _, _ = idx.search(Qd, k=10, ef=a.ef, ef_upper=a.ef_upper, descend_all=a.descend_all, ef_l1=a.ef_l1)
+        ids, _, _ = idx.search(Qd, k=10, ef=a.ef, ef_upper=a.ef_upper, descend_all=a.descend_all, ef_l1=a.ef_l1,
+                               exact_upper=a.exact_upper)
     torch.cuda.synchronize()
     print("search ok", idx.info()["sizes"], ids[0, :3].tolist())
 

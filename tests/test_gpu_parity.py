@@ -260,6 +260,23 @@ def test_search_upper_beam_parity(uniform10k, efu, l1, da):
     assert P.returned_distance_error(X, Q, ids.cpu().numpy(), dd.cpu().numpy()) <= P.DIST_RTOL
 
 
+@pytest.mark.parametrize("efu,da", [(1, 0), (16, 0), (16, 1)])
+def test_search_exact_upper_parity(uniform10k, efu, da):
+    """Upper layers of at most exact_upper points give their exact candidate
+    sets instead of a walk: same answers as the oracle's."""
+    X, Q, oidx, gidx = uniform10k
+    gi, gd = O.bruteforce(X, Q, 10)
+    ids, dd, st = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=32, ef_upper=efu, descend_all=da,
+                              exact_upper=64, stats=True)
+    oi, od, ost = O.search(oidx, X, Q, k=10, ef=32, ef_upper=efu, descend_all=da, exact_upper=64)
+    ids = ids.cpu().numpy()
+    assert abs(_recall(ids, gi, gd) - _recall(oi, gi, gd)) <= P.RECALL_TOL + 1e-12
+    assert P.returned_distance_error(X, Q, ids, dd.cpu().numpy()) <= P.DIST_RTOL
+    assert np.mean(np.all(ids == oi, axis=1)) >= 0.98
+    small = sum(int(s) for s in oidx["sizes"][1:] if s <= 64)
+    assert small > 0 and np.all(st.cpu().numpy()[:, 0] >= small)
+
+
 @pytest.mark.parametrize("layer", [0, 1])
 def test_greedy_probe_matches_oracle(uniform10k, layer):
     """henn_greedy_probe walks the same GreedySearch (Alg. 4) as the oracle's
