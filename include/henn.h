@@ -4,11 +4,11 @@
  * for approximate nearest neighbour search (arXiv 2505.17368).
  *
  * The problem (Sec. 2, "Data Model" and "Problem setting"): n points x_i in
- * R^d with a distance (l2, or angular 1 - cos per App. F); for a query q
+ * R^d with a distance (l2, or angular 1 - cos per App. G); for a query q
  * return k points of X with the smallest distance, approximately, with high
  * Recall@k.  The index (Def. 1) is a stack of layers L_0 = X, L_1, ..., L_L,
  * each an eps-net of the one below it for ring ranges (Def. 2, Eq. 1,
- * Alg. 1, Alg. 2), each with its own navigable graph (App. C), linked
+ * Alg. 1, Alg. 2), each with its own navigable graph (App. B), linked
  * between layers by the copies of the same point.  A query descends from a
  * random node of the top layer by greedy search (Alg. 4) and runs a beam of
  * width ef on the bottom layer (Sec. 2.2, last paragraph).
@@ -74,7 +74,7 @@ typedef enum { HENN_L2 = 0, HENN_ANGULAR = 1 } henn_metric;
  * copy as well, used for the exact rerank of the final candidates. */
 typedef enum { HENN_F32 = 0, HENN_BF16 = 1, HENN_FP8E4M3 = 2 } henn_storage;
 
-/* Navigable graph of each layer (App. C; App. F "Navigation Graphs"). */
+/* Navigable graph of each layer (App. B; App. G "Navigation Graphs"). */
 typedef enum { HENN_GRAPH_NSW = 0, HENN_GRAPH_KNN = 1 } henn_graph;
 
 /* Layer sampler: SAMPLING = Alg. 2 (draws with replacement, ring-range
@@ -97,7 +97,7 @@ typedef struct {
   int32_t m;             /* layer decay 2^m (Alg. 1, Lemma 1); 1..8, default 4  */
   int32_t max_layers;    /* L of Alg. 1; 0 = while |L_{i-1}| >= 2^m (Cor. 3)    */
   double eps_c0;         /* c0 of Eq. 1; default 1.0                            */
-  int32_t num_ranges;    /* r, the "range size" of App. F; default 100          */
+  int32_t num_ranges;    /* r, the "range size" of App. G; default 100          */
   int32_t max_attempts;  /* Las-Vegas repeats of Alg. 2 per layer; default 64   */
   int32_t M;             /* forward links per inserted point; default 16        */
   int32_t Mmax;          /* adjacency row width; 32 (only 32 is supported)      */
@@ -119,11 +119,11 @@ typedef struct henn_index henn_index; /* opaque, owned by the library */
  * L_{i-1} with replacement (Alg. 2, Cor. 2), keep the distinct ones, accept
  * them when every one of num_ranges random ring ranges (Def. 2) holding
  * floor(eps*s)+1 points, eps from Eq. 1, contains one of them (IsEpsNet,
- * App. C practical implementation), else draw again; with
+ * App. B practical implementation), else draw again; with
  * sampler = HENN_SAMPLER_HALVING the layer is instead m halving steps of
  * L_{i-1} (Alg. 3, BuildEpsNetDiscV2).  Every layer then gets
  * its navigable graph: each point links to the M nearest points inserted
- * before it (NSW, App. C; or its M nearest overall for HENN_GRAPH_KNN) and
+ * before it (NSW, App. B; or its M nearest overall for HENN_GRAPH_KNN) and
  * each row keeps its nearest predecessor plus the nearest Mmax-1 of its
  * forward and reverse links.
  * On success *out owns device memory for the vectors, layers and graphs.

@@ -8,6 +8,7 @@ This module compiles the C source with gcc and wraps it with ctypes/numpy.
 from __future__ import annotations
 
 import ctypes as C
+import math
 import os
 import subprocess
 import threading
@@ -258,6 +259,65 @@ def build_index(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, M=
         idx["fwd_d"].append(fd)
         idx["adj"].append(edge_rule(f, fd, Mmax, graph))
     idx.update(M=M, Mmax=Mmax, seed=seed, metric=metric, graph=graph)
+    return idx
+
+
+TAG_INSERT = 0x494E5352  # "INSR": layer promotion coin of an inserted point (App. C, Insert)
+
+
+def insert_layers(seed, p, m, L):
+    """Layers an inserted point joins (App. C, Insert): layer 0, then layer i
+    while the point is in layer i-1 and its coin bounded(derive(derive(
+    derive(seed, INSR), p), i), 2^m) is 0 (each layer keeps about a 2^-m
+    fraction of the one below, the rate of the built layers); at most L."""
+    out = [0]
+    for i in range(1, L + 1):
+        if bounded(derive(derive(derive(seed, TAG_INSERT), p), i), 1 << m) != 0:
+            break
+        out.append(i)
+    return out
+
+
+def _dist64(X, p, members, metric):
+    x = X[p].astype(np.float64)
+    Y = X[members].astype(np.float64)
+    if metric == ANGULAR:
+        nx = math.sqrt(float(x @ x))
+        ny = np.sqrt((Y * Y).sum(1))
+        return 1.0 - (Y @ x) / (np.maximum(ny, 1e-300) * max(nx, 1e-300))
+    return ((Y - x) ** 2).sum(1)
+
+
+def insert(idx, X, new_ids, m=4):
+    """Dynamic Insert (App. C) of the points `new_ids` (ascending, every id
+    larger than the indexed ones; X holds all points), one after another.
+    For each layer the point joins: it is appended to the layer (ids stay
+    ascending), its down pointer is its position in the layer below, its
+    forward list is the M nearest current members by (distance, position)
+    (it is the last point in the layer's insertion order, so every member
+    is earlier), and the layer's adjacency is the edge rule over the updated
+    forward lists.  NSW graphs only.  Modifies and returns idx."""
+    if idx["graph"] != GRAPH_NSW:
+        raise ValueError("insert supports NSW graphs")
+    X = _f32(X)
+    M, Mmax, metric, L = idx["M"], idx["Mmax"], idx["metric"], idx["L"]
+    for p in [int(v) for v in new_ids]:
+        for i in insert_layers(idx["seed"], p, m, L):
+            members = idx["ids"][i]
+            s = len(members)
+            d = _dist64(X, p, members, metric)
+            order = np.lexsort((np.arange(s), d))[:M]
+            row = np.full(M, -1, np.int32)
+            row_d = np.full(M, np.inf)
+            row[:len(order)] = order
+            row_d[:len(order)] = d[order]
+            idx["ids"][i] = np.append(members, p).astype(np.int64)
+            if i >= 1:
+                idx["down"][i] = np.append(idx["down"][i], len(idx["ids"][i - 1]) - 1).astype(np.int64)
+            idx["fwd"][i] = np.vstack([idx["fwd"][i], row[None, :]])
+            idx["fwd_d"][i] = np.vstack([idx["fwd_d"][i], row_d[None, :]])
+            idx["adj"][i] = edge_rule(idx["fwd"][i], idx["fwd_d"][i], Mmax, idx["graph"])
+        idx["sizes"] = np.array([len(a) for a in idx["ids"]], dtype=np.int64)
     return idx
 
 

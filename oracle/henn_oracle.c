@@ -54,7 +54,7 @@ uint64_t ho_bounded(uint64_t u, uint64_t s) {
 /* ---------------------------------------------------- insertion order */
 
 /* The NSW graph inserts the points of a layer one at a time in random order
- * (App. C, Navigable Graphs; App. F, Methods).  The order is a keyed
+ * (App. B, Navigable Graphs; App. G, Methods).  The order is a keyed
  * pseudo-random permutation of 0..s-1: a balanced 4-round Feistel network
  * (Luby & Rackoff 1988) on 2h bits whose round function is SplitMix64,
  * restricted to [0, s) by cycle walking (Black & Rogaway 2002). */
@@ -85,7 +85,7 @@ int64_t ho_order_rank(uint64_t seed, int32_t layer, int64_t s, int64_t x) {
 /* ------------------------------------------------------------- metric */
 
 /* Sec. 2 "Data Model": l_p distance with p = 2 (squared; the square root is
- * monotone so every order and ring test is unchanged).  App. F: angular
+ * monotone so every order and ring test is unchanged).  App. G: angular
  * distance 1 - cos. */
 double ho_dist(const float* a, const float* b, int32_t d, int32_t metric) {
   if (metric == HO_ANGULAR) {
@@ -124,7 +124,7 @@ static int pair_cmp(const void* pa, const void* pb) {
 /* ---------------------------------------------------------- Eq. 1 window */
 
 /* eps(s) = c0 * d * log(s) / s * 2^m (Eq. 1, natural log).  A ring is heavy
- * when it holds MORE than eps*s points (definition of an eps-net, App. C),
+ * when it holds MORE than eps*s points (definition of an eps-net, App. B),
  * so the smallest heavy ring has floor(eps*s) + 1 points.  eps*s is
  * evaluated as ((c0 * d) * log(s)) * 2^m. */
 int64_t ho_ring_window(double c0, int32_t d, int64_t s, int32_t m) {
@@ -137,8 +137,8 @@ int64_t ho_ring_window(double c0, int32_t d, int64_t s, int32_t m) {
 
 /* ---------------------------------------------------------- Alg. 2 draw */
 
-/* One Monte-Carlo draw of Alg. 2: t samples with replacement (App. F,
- * Implementation Details; App. E parallel sampling), the layer being the
+/* One Monte-Carlo draw of Alg. 2: t samples with replacement (App. G,
+ * Implementation Details; App. D parallel sampling), the layer being the
  * distinct set.  Draw j of attempt a for layer i picks position
  * bounded(derive(derive(derive(derive(seed, SAMP), i), a), j), s). */
 int64_t ho_sample_positions(uint64_t seed, int32_t layer, int32_t attempt, int64_t s, int64_t t,
@@ -232,7 +232,7 @@ static void centre_order(const float* X, int32_t d, int32_t metric, const int64_
   qsort(sorted, (size_t)s, sizeof(pair_t), pair_cmp);
 }
 
-/* App. C "Practical Implementation" / App. F: instead of every range, r
+/* App. B "Practical Implementation" / App. G: instead of every range, r
  * ranges are drawn uniformly at random and the candidate must hit each.
  * Ring rho of attempt a at layer i: centre position
  * bounded(derive(derive(derive(derive(seed, RCEN), i), a), rho), s), start
@@ -351,11 +351,11 @@ static void keep_best(pair_t* best, int32_t* cnt, int32_t cap, double dv, int64_
   best[j] = e;
 }
 
-/* NSW (App. C, Navigable Graphs; App. F): each point, when inserted, is
+/* NSW (App. B, Navigable Graphs; App. G): each point, when inserted, is
  * linked to its nearest already-inserted points.  Written here as the exact
  * definition that incremental greedy insertion approximates: the M nearest
  * by (dist, index) among points of lower insertion rank.  graph=KNN: the M
- * nearest among all other points (App. F, knn graph). */
+ * nearest among all other points (App. G, knn graph). */
 void ho_forward_lists(const float* X, int32_t d, int32_t metric, const int64_t* ids, int64_t s,
                       uint64_t seed, int32_t layer, int32_t M, int32_t graph, int32_t* fwd,
                       double* fwd_d) {
@@ -404,7 +404,7 @@ void ho_forward_row(const float* X, int32_t d, int32_t metric, const int64_t* id
   free(best);
 }
 
-/* Edge rule (reading of App. C NSW): links are undirected at insertion, so
+/* Edge rule (reading of App. B NSW): links are undirected at insertion, so
  * a node sees its forward list and every later node that linked to it; the
  * list is capped at Mmax, always keeping the nearest predecessor pred(j) =
  * fwd(j)[0] so that the graph stays connected. */

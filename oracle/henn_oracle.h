@@ -12,7 +12,7 @@
  *  - Points are float32 row-major (n x d), promoted to double on use.
  *  - Squared L2 distances are sum_k (x_k - y_k)^2 summed in index order, one
  *    rounding per operation (compile with -ffp-contract=off).
- *  - Angular distance is 1 - <x,y> / (|x| |y|)  (App. F, angular metric).
+ *  - Angular distance is 1 - <x,y> / (|x| |y|)  (App. G, angular metric).
  *  - Every argmin / sort is over (distance, index) pairs, a total order.
  *  - Layer 0 is all points 0..n-1; layer i >= 1 is a sorted subset of layer
  *    i-1.  Graph rows hold layer-local indices (positions inside the layer).
@@ -35,7 +35,7 @@ extern "C" {
 
 /* stream tags (ASCII words) */
 #define HO_TAG_SAMPLE 0x53414D50ULL /* "SAMP": with-replacement draws, Alg. 2 */
-#define HO_TAG_RCENTRE 0x5243454EULL /* "RCEN": ring centre, App. C practical impl. */
+#define HO_TAG_RCENTRE 0x5243454EULL /* "RCEN": ring centre, App. B practical impl. */
 #define HO_TAG_RSTART 0x52535441ULL /* "RSTA": ring start rank */
 #define HO_TAG_ORDER 0x4F524452ULL  /* "ORDR": NSW insertion order */
 #define HO_TAG_ENTRY 0x454E5452ULL  /* "ENTR": random root node, Alg. 4 */
@@ -68,7 +68,7 @@ double ho_dist(const float* a, const float* b, int32_t d, int32_t metric);
 int64_t ho_sample_positions(uint64_t seed, int32_t layer, int32_t attempt, int64_t s, int64_t t,
                             int64_t* out_pos);
 
-/* IsEpsNet with r sampled ring ranges (App. C practical implementation).
+/* IsEpsNet with r sampled ring ranges (App. B practical implementation).
  * prev: global ids of layer i-1 (s of them).  net_pos: sorted positions in
  * prev of the candidate layer (nnet of them).  Returns 1 if every sampled
  * ring of >= w points holds a candidate, else 0.  exhaustive=1 checks every

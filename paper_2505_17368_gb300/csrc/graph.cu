@@ -1,6 +1,6 @@
 // graph.cu -- the edge rule that turns forward lists into adjacency rows.
 //
-// NSW links are undirected at insertion (App. C): a point sees its own
+// NSW links are undirected at insertion (App. B): a point sees its own
 // forward links and the later points that linked to it (reverse links).
 // Each row of width Mmax = 32 keeps the nearest predecessor pred(j) =
 // fwd(j)[0] first (so every point keeps a path towards the first inserted

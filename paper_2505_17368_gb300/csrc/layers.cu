@@ -1,10 +1,10 @@
 // layers.cu -- eps-net layer construction (Alg. 1 membership, Alg. 2).
 //
 //  * draws: ceil(s/2^m) samples with replacement of the previous layer's
-//    positions (Alg. 2; App. E parallel sampling: one thread per draw)
+//    positions (Alg. 2; App. D parallel sampling: one thread per draw)
 //  * compaction: the distinct positions in ascending order (= the new
 //    layer, and its down pointers into the previous layer)
-//  * IsEpsNet with r sampled ring ranges (App. C practical implementation):
+//  * IsEpsNet with r sampled ring ranges (App. B practical implementation):
 //    FP32 distances from each ring centre to every point of the previous
 //    layer, radix selection of the ring's two boundary order statistics,
 //    and a certified decision per ring; a ring whose FP32 decision is not

@@ -2,7 +2,7 @@
 //
 //  * padded FP32 master copy (rows of dpad = roundup(d, 32) floats, zero
 //    tail, so every row is a whole number of 128-byte lines)
-//  * inverse norms and unit-length copies for the angular metric (App. F:
+//  * inverse norms and unit-length copies for the angular metric (App. G:
 //    cosine similarity works on vectors normalised to the unit sphere)
 //  * insertion order of a layer (keyed Feistel permutation) and the layer's
 //    centred vectors in that order, the operand of the distance tiles

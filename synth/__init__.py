@@ -12,14 +12,14 @@ Uniforms take the top 53 bits; normals use the Box-Muller transform in FP64;
 every dataset is cast to float32 at the end.
 
 Workloads (the paper evaluates on SIFT/GloVe/MNIST and on exponential
-synthetic data, Sec. 4 and App. F; none of those files are used here, these
+synthetic data, Sec. 4 and App. G; none of those files are used here, these
 generators stand in for them):
   * uniform_cube      : i.i.d. U[0,1)^d
   * gaussian_mixture  : isotropic clusters, centres N(0,I), per-cluster sigma
                         U[0.1,0.5]; optional affine rescale to [0,255]
                         (SIFT-like range) or unit-length normalisation
   * nested_shells     : points uniform on spheres of radius 2^-i
-  * exponential       : i.i.d. Exp(lambda) coordinates (App. F, "Methods and
+  * exponential       : i.i.d. Exp(lambda) coordinates (App. G, "Methods and
                         Datasets")
 """
 from __future__ import annotations
@@ -210,7 +210,7 @@ WORKLOADS = {
     "shells-1m-d64": dict(n=1_000_000, d=64, nq=10_000, k=10, metric="l2"),
     "mixture-1m-d960": dict(n=1_000_000, d=960, nq=10_000, k=10, metric="l2", clusters=500),
     "angular-10m-d96": dict(n=10_000_000, d=96, nq=10_000, k=10, metric="angular", clusters=10_000),
-    # the paper's own synthetic data (App. F): i.i.d. exponential coordinates
+    # the paper's own synthetic data (App. G): i.i.d. exponential coordinates
     "exponential-50k-d32-l4": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=4.0),
     "exponential-50k-d32-l32": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=32.0),
     "exponential-50k-d32-l256": dict(n=50_000, d=32, nq=10_000, k=10, metric="l2", lam=256.0),

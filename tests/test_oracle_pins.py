@@ -205,7 +205,7 @@ def _plane_enumeration(P, net_pos, w, centres):
 
 
 def test_epsnet_exhaustive_matches_enumeration():
-    """Def. 2 ring ranges / App. C eps-net definition on tiny planar sets:
+    """Def. 2 ring ranges / App. B eps-net definition on tiny planar sets:
     (a) the oracle's exhaustive IsEpsNet over data centres equals an
     independent enumeration of every (centre, window);  (b) a set that is an
     eps-net for rings around every centre of the plane passes the oracle's
@@ -239,7 +239,7 @@ def test_epsnet_exhaustive_matches_enumeration():
 
 
 def test_sampled_rings_are_heavy_windows():
-    """Each sampled ring (App. F: r random ranges) holds exactly w points,
+    """Each sampled ring (App. G: r random ranges) holds exactly w points,
     i.e. more than eps*s: its verdict equals a direct check of that window."""
     rng = np.random.default_rng(2)
     s, d, w, r = 300, 4, 17, 12
@@ -296,7 +296,7 @@ def test_las_vegas_retries_are_counted():
 # ------------------------------------------------------- navigable graphs
 
 def test_knn_graph_equals_bruteforce():
-    """App. F knn graph: each point's list is its exact M nearest (scipy)."""
+    """App. G knn graph: each point's list is its exact M nearest (scipy)."""
     X = synth.uniform_cube(500, 6, seed=6)
     ids = np.arange(500)
     fwd, fwd_d = O.forward_lists(X, ids, 0, 0, M=8, graph=O.GRAPH_KNN)
@@ -308,7 +308,7 @@ def test_knn_graph_equals_bruteforce():
 
 
 def test_nsw_forward_lists_are_nearest_predecessors():
-    """App. C NSW: the point inserted at rank r links to its M nearest among
+    """App. B NSW: the point inserted at rank r links to its M nearest among
     the points inserted before it (brute force over predecessors)."""
     X = synth.uniform_cube(400, 5, seed=7)
     ids = np.arange(400)
@@ -370,7 +370,7 @@ def test_edge_rule_properties():
 # ------------------------------------------------------------- queries
 
 def test_complete_graph_greedy_is_exact():
-    """App. C: the complete graph is navigable; GreedySearch (Alg. 4) on it
+    """App. B: the complete graph is navigable; GreedySearch (Alg. 4) on it
     returns the exact nearest neighbour from any start."""
     X = synth.uniform_cube(30, 4, seed=9)
     Q = synth.uniform_cube(50, 4, seed=10)
@@ -435,7 +435,7 @@ def test_greedy_hop_bound():
 
 def test_query_evaluations_grow_polylog():
     """Thm. 1: query time O(d d* rho log^2 n).  Distance evaluations per
-    query, for n = 2^10 .. 2^14 (exponential coordinates, App. F), must fit
+    query, for n = 2^10 .. 2^14 (exponential coordinates, App. G), must fit
     a log^2 n law better than a linear one.  The constant is not pinned (the
     paper gives none)."""
     ns = [2**10, 2**11, 2**12, 2**13, 2**14]
@@ -479,7 +479,7 @@ def test_search_exact_on_tiny_index():
 
 
 def test_angular_distance_definition():
-    """App. F: angular distance 1 - cos, equal to |x/|x| - y/|y||^2 / 2."""
+    """App. G: angular distance 1 - cos, equal to |x/|x| - y/|y||^2 / 2."""
     rng = np.random.default_rng(4)
     a, b = rng.normal(size=8).astype(np.float32), rng.normal(size=8).astype(np.float32)
     v = O.dist(a, b, O.ANGULAR)
