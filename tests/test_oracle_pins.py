@@ -598,3 +598,40 @@ def test_exact_upper_layers_pick_true_nearest():
         assert got[q, 0] == want
     # every upper-layer point is evaluated once per query
     assert np.all(st[:, 0] >= sum(len(a) for a in idx["ids"][1:]))
+
+
+# ------------------------------------------------ dynamic insert (App. C)
+
+def test_insert_forward_rows_and_structure():
+    """Insert (App. C): an inserted point's forward list in each layer it
+    joins is its exact M nearest current members (scipy brute force, ties by
+    position); layers stay ascending with consistent down pointers; a
+    search for an inserted point finds it at distance 0."""
+    X = synth.uniform_cube(2600, 6, seed=31)
+    idx = O.build_index(X[:2000], seed=7)
+    M = idx["M"]
+    new = np.arange(2000, 2600)
+    before = [a.copy() for a in idx["ids"]]
+    O.insert(idx, X, new)
+    for i in range(idx["L"] + 1):
+        ids = idx["ids"][i]
+        assert np.all(np.diff(ids) > 0)
+        if i >= 1:
+            assert np.array_equal(idx["ids"][i - 1][idx["down"][i]], ids)
+        for pos in range(len(before[i]), len(ids)):
+            p = ids[pos]
+            d = cdist(X[p:p + 1].astype(np.float64), X[ids[:pos]].astype(np.float64), "sqeuclidean")[0]
+            want = np.lexsort((np.arange(pos), d))[:M]
+            assert np.array_equal(idx["fwd"][i][pos][:len(want)], want)
+    got, dist, _ = O.search(idx, X, X[new[::50]], k=1, ef=64)
+    assert np.array_equal(got[:, 0], new[::50]) and np.all(dist[:, 0] == 0)
+
+
+def test_insert_promotion_rate():
+    """An inserted point joins layer i with probability 2^-m given layer
+    i-1 (the built layers' rate): about 1/16 of 20000 ids reach layer 1."""
+    hits = sum(1 for p in range(20000) if len(O.insert_layers(3, p, 4, 5)) > 1)
+    sd = math.sqrt(20000 / 16 * 15 / 16)
+    assert abs(hits - 20000 / 16) < 6 * sd
+    deep = [O.insert_layers(3, p, 2, 6) for p in range(4000)]
+    assert all(v == list(range(len(v))) for v in deep)
