@@ -56,6 +56,7 @@ extern "C" {
 #define HENN_TAG_ORDER 0x4F524452ULL   /* "ORDR" NSW insertion order of a layer        */
 #define HENN_TAG_ENTRY 0x454E5452ULL   /* "ENTR" random top-layer node of a query      */
 #define HENN_TAG_HALVE 0x48414C56ULL   /* "HALV" coin of a matched pair, Alg. 3 halving */
+#define HENN_TAG_INSERT 0x494E5352ULL  /* "INSR" layer promotion coin of an inserted point */
 
 typedef enum {
   HENN_OK = 0,
@@ -132,6 +133,26 @@ typedef struct henn_index henn_index; /* opaque, owned by the library */
  */
 henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t x_on_device,
                        const henn_build_params* p, void* stream, henn_index** out);
+
+/*
+ * henn_insert -- Insert (App. C, dynamic setting) of n_new points, appended
+ * after the indexed ones: the j-th gets global id n + j.  X: n_new x d
+ * float32 (device if x_on_device, else host).  Each point joins layer 0 and
+ * then layer i while it is in layer i-1 and its coin
+ * bounded(derive(derive(derive(seed, INSR), id), i), 2^m) is 0 (the rate at
+ * which the built layers thin out; no layer above L is created).  In every
+ * layer it joins it is appended last in the insertion order, so its
+ * forward list is its M nearest current members (exact FP32, ties by
+ * position), points of one call being inserted one after another; the
+ * layer's adjacency is then the edge rule over the updated forward lists
+ * (the rows of its forward neighbours gain it as a reverse link).  Device
+ * arrays grow by doubling.  NSW graphs only (HENN_ERR_UNSUPPORTED for kNN
+ * graphs, where earlier points' own lists would change).  Synchronises
+ * `stream` before returning.  Not safe concurrently with searches on idx;
+ * servers made from idx before the call still point at the old arrays and
+ * must be destroyed first.
+ */
+henn_status henn_insert(henn_index* idx, const float* X, int64_t n_new, int32_t x_on_device, void* stream);
 
 /* Releases the index and its device memory.  NULL is a no-op. */
 void henn_free(henn_index* idx);

@@ -48,6 +48,7 @@ EXPORTS = [
     "henn_index_get_layer",
     "henn_exact_knn",
     "henn_greedy_probe",
+    "henn_insert",
     "henn_quantize_rows",
     "henn_last_error",
     "henn_serve_params_default",
@@ -175,6 +176,8 @@ def load(path: str | None = None):
         L.henn_exact_knn.restype = i32
         L.henn_greedy_probe.argtypes = [vp, i32, vp, i64, vp, i32, vp, vp, vp, vp]
         L.henn_greedy_probe.restype = i32
+        L.henn_insert.argtypes = [vp, vp, i64, i32, vp]
+        L.henn_insert.restype = i32
         L.henn_quantize_rows.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         L.henn_quantize_rows.restype = i32
         L.henn_serve_params_default.argtypes = [C.POINTER(ServeParams)]
@@ -261,6 +264,22 @@ class Index:
         self.n, self.d, self.M, self.Mmax = n, d, M, Mmax
         self.metric, self.storage = metric, storage
         del keep
+
+    def insert(self, X, stream=None):
+        """henn_insert: append the rows of X (n_new x d, host or CUDA) to the
+        index; they get ids n, n + 1, ...  Returns the first new id."""
+        if _is_torch(X):
+            import torch
+
+            X = X.to(torch.float32).contiguous()
+        else:
+            X = np.ascontiguousarray(X, dtype=np.float32)
+        xp, on_dev, keep = _ptr(X)
+        first = self.n
+        _check(load().henn_insert(self._h, xp, X.shape[0], int(on_dev), _stream(stream)))
+        self.n += X.shape[0]
+        del keep
+        return first
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

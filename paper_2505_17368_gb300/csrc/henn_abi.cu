@@ -134,6 +134,7 @@ int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
 
 struct LayerDev {
   int64_t size = 0;
+  int64_t cap = 0;          // rows the arrays below hold (insertions grow it)
   int32_t* ids = nullptr;   // global ids (layers >= 1)
   int32_t* down = nullptr;  // positions in the layer below (layers >= 1)
   int32_t* adj = nullptr;   // size x 32
@@ -145,6 +146,8 @@ struct LayerDev {
 
 struct henn_index {
   int64_t n = 0;
+  int64_t cap_n = 0;  // rows x32 / xw / inv_norm hold
+  int32_t m = 4;      // layer decay 2^m of the build
   int32_t d = 0, dpad = 0, metric = 0, storage = 0, graph = 0, M = 16, Mmax = 32;
   uint64_t seed = 0;
   int32_t L = 0;
@@ -171,6 +174,16 @@ struct henn_index {
     allocs.push_back(p);
     bytes += (int64_t)b;
     return static_cast<T*>(p);
+  }
+  // frees one allocation made by alloc() (device idle for it)
+  void release(void* p) {
+    if (!p) return;
+    for (size_t i = 0; i < allocs.size(); ++i)
+      if (allocs[i] == p) {
+        cudaFree(p);
+        allocs.erase(allocs.begin() + (long)i);
+        return;
+      }
   }
   // side streams for the concurrent per-class launches of one batch
   // (created on first use)
@@ -484,10 +497,12 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     ix->M = p.M;
     ix->Mmax = p.Mmax;
     ix->seed = p.seed;
+    ix->m = p.m;
     const int32_t dpad = ix->dpad;
 
     // FP32 master copy with zero padding
     ix->x32 = ix->alloc<float>((size_t)n * dpad);
+    ix->cap_n = n;
     CK(cudaMemsetAsync(ix->x32, 0, sizeof(float) * (size_t)n * dpad, st));
     CK(cudaMemcpy2DAsync(ix->x32, sizeof(float) * dpad, X, sizeof(float) * d, sizeof(float) * d, (size_t)n,
                          x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
@@ -551,6 +566,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     // ---- navigable graph + traversal copy per layer
     for (int32_t li = 0; li <= ix->L; ++li) {
       LayerDev& Ly = ix->layers[li];
+      Ly.cap = Ly.size;
       Ly.adj = ix->alloc<int32_t>((size_t)Ly.size * kMmax);
       Ly.fwd = ix->alloc<int32_t>((size_t)Ly.size * ix->M);
       Ly.fwd_d = ix->alloc<float>((size_t)Ly.size * ix->M);
@@ -585,6 +601,183 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
 }
 
 extern "C" void henn_free(henn_index* idx) { delete idx; }
+
+// ------------------------------------------------------------- insertion
+
+namespace {
+
+// Reallocates a tracked device array to `cap` elements keeping the first
+// `used` (the stream is synchronised before the old one is freed).
+template <typename T>
+T* regrow(henn_index* ix, T* old, size_t used, size_t cap, cudaStream_t st) {
+  T* p = ix->alloc<T>(cap);
+  if (old && used) CK(cudaMemcpyAsync(p, old, sizeof(T) * used, cudaMemcpyDeviceToDevice, st));
+  if (old) {
+    CK(cudaStreamSynchronize(st));
+    ix->release(old);
+  }
+  return p;
+}
+
+}  // namespace
+
+extern "C" henn_status henn_insert(henn_index* ix, const float* X, int64_t n_new, int32_t x_on_device, void* stream) {
+  g_error.clear();
+  try {
+    require(ix != nullptr, "index is NULL");
+    require(n_new >= 0, "n_new must be >= 0");
+    if (n_new == 0) return HENN_OK;
+    require(X != nullptr, "X is NULL");
+    if (ix->graph != HENN_GRAPH_NSW) throw Failure(HENN_ERR_UNSUPPORTED, "insertion supports NSW graphs only");
+    require(ix->n + n_new < (int64_t)INT32_MAX, "too many points");
+    CK(cudaStreamSynchronize((cudaStream_t)stream));
+    struct OwnStream {
+      cudaStream_t s = nullptr;
+      ~OwnStream() {
+        if (s) {
+          cudaStreamSynchronize(s);
+          cudaStreamDestroy(s);
+        }
+      }
+    } own;
+    CK(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+    cudaStream_t st = own.s;
+    const int64_t n0 = ix->n, n1 = n0 + n_new;
+    const int32_t dpad = ix->dpad, d = ix->d, M = ix->M;
+    const bool angular = ix->metric == HENN_ANGULAR;
+
+    // ---- vectors (FP32 master copy, unit rows for angular)
+    if (n1 > ix->cap_n) {
+      const int64_t cap = std::max(n1, 2 * ix->cap_n);
+      const bool aliased = ix->xw == ix->x32;
+      ix->x32 = regrow(ix, ix->x32, (size_t)n0 * dpad, (size_t)cap * dpad, st);
+      if (angular) {
+        ix->xw = regrow(ix, ix->xw, (size_t)n0 * dpad, (size_t)cap * dpad, st);
+        ix->inv_norm = regrow(ix, ix->inv_norm, (size_t)n0, (size_t)cap, st);
+      } else if (aliased) {
+        ix->xw = ix->x32;
+      }
+      ix->cap_n = cap;
+    }
+    float* xrow = ix->x32 + (size_t)n0 * dpad;
+    CK(cudaMemsetAsync(xrow, 0, sizeof(float) * (size_t)n_new * dpad, st));
+    CK(cudaMemcpy2DAsync(xrow, sizeof(float) * dpad, X, sizeof(float) * d, sizeof(float) * d, (size_t)n_new,
+                         x_on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    if (angular) {
+      launch_inv_norms(xrow, n_new, dpad, ix->inv_norm + n0, st);
+      launch_normalise(xrow, ix->inv_norm + n0, n_new, dpad, ix->xw + (size_t)n0 * dpad, st);
+      CKL("normalise");
+    }
+
+    // ---- layers each new point joins (App. C, Insert)
+    std::vector<std::vector<int32_t>> add(ix->L + 1);
+    for (int64_t j = 0; j < n_new; ++j) {
+      const uint64_t pid = (uint64_t)(n0 + j);
+      add[0].push_back((int32_t)pid);
+      for (int32_t i = 1; i <= ix->L; ++i) {
+        if (bounded(derive(derive(derive(ix->seed, HENN_TAG_INSERT), pid), (uint64_t)i), 1ull << ix->m) != 0) break;
+        add[i].push_back((int32_t)pid);
+      }
+    }
+
+    // ---- per layer: append members, their traversal rows, forward lists, edge rule
+    for (int32_t li = 0; li <= ix->L; ++li) {
+      LayerDev& Ly = ix->layers[li];
+      const int64_t s0 = Ly.size, c = (int64_t)add[li].size(), s1 = s0 + c;
+      if (c == 0) continue;
+      const size_t elem = ix->storage == HENN_BF16 ? 2 : (ix->storage == HENN_FP8E4M3 ? 1 : 4);
+      const bool vec_aliased = li == 0 && ix->storage == HENN_F32;
+      if (s1 > Ly.cap) {
+        const int64_t cap = std::max(s1, 2 * Ly.cap);
+        if (li >= 1) {
+          Ly.ids = regrow(ix, Ly.ids, (size_t)s0, (size_t)cap, st);
+          Ly.down = regrow(ix, Ly.down, (size_t)s0, (size_t)cap, st);
+        }
+        Ly.adj = regrow(ix, Ly.adj, (size_t)s0 * kMmax, (size_t)cap * kMmax, st);
+        Ly.fwd = regrow(ix, Ly.fwd, (size_t)s0 * M, (size_t)cap * M, st);
+        Ly.fwd_d = regrow(ix, Ly.fwd_d, (size_t)s0 * M, (size_t)cap * M, st);
+        if (!vec_aliased)
+          Ly.vec = regrow(ix, static_cast<uint8_t*>(Ly.vec), (size_t)s0 * dpad * elem, (size_t)cap * dpad * elem, st);
+        if (ix->storage == HENN_FP8E4M3) Ly.vscale = regrow(ix, Ly.vscale, (size_t)s0, (size_t)cap, st);
+        Ly.cap = cap;
+      }
+      if (vec_aliased) Ly.vec = ix->xw;
+      Scratch sc(st);
+      if (li >= 1) {
+        // global ids, and positions in the layer below (appended there in this call)
+        std::vector<int32_t> dn(c);
+        const LayerDev& Lb = ix->layers[li - 1];
+        const int64_t below_first = Lb.size - (int64_t)add[li - 1].size();
+        size_t at = 0;
+        for (int64_t j = 0; j < c; ++j) {
+          while (add[li - 1][at] != add[li][j]) ++at;
+          dn[j] = (int32_t)(below_first + (int64_t)at);
+        }
+        CK(cudaMemcpyAsync(Ly.ids + s0, add[li].data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, st));
+        CK(cudaMemcpyAsync(Ly.down + s0, dn.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, st));
+        CK(cudaStreamSynchronize(st));  // host vectors go out of scope
+      }
+      // traversal rows of the new members
+      const float* src = ix->xw + (size_t)n0 * dpad;  // layer 0: the appended rows in order
+      if (li >= 1) {
+        float* g = ix->storage == HENN_F32 ? static_cast<float*>(Ly.vec) + (size_t)s0 * dpad
+                                           : sc.get<float>((size_t)c * dpad);
+        launch_gather_rows32(ix->xw, Ly.ids + s0, c, dpad, g, st);
+        src = g;
+      }
+      if (ix->storage == HENN_BF16)
+        launch_quantize(src, c, dpad, dpad, dpad, HENN_BF16, static_cast<uint16_t*>(Ly.vec) + (size_t)s0 * dpad,
+                        nullptr, st);
+      else if (ix->storage == HENN_FP8E4M3)
+        launch_quantize(src, c, dpad, dpad, dpad, HENN_FP8E4M3, static_cast<uint8_t*>(Ly.vec) + (size_t)s0 * dpad,
+                        Ly.vscale + s0, st);
+      CKL("traversal rows");
+      // forward lists: the new rows, inserted last in this order
+      std::vector<int32_t> rows(c);
+      for (int64_t j = 0; j < c; ++j) rows[j] = (int32_t)(s0 + j);
+      int32_t* drows = sc.get<int32_t>(c);
+      CK(cudaMemcpyAsync(drows, rows.data(), sizeof(int32_t) * c, cudaMemcpyHostToDevice, st));
+      launch_exact_rows(ix->xw, li >= 1 ? Ly.ids : nullptr, s1, dpad, ix->metric, nullptr, 0, drows, (int32_t)c, M,
+                        Ly.fwd, Ly.fwd_d, st);
+      CKL("forward lists");
+      // edge rule over the layer's updated forward lists
+      int32_t* cnt = sc.get<int32_t>(s1);
+      int32_t* fill = sc.get<int32_t>(s1);
+      int64_t* off = sc.get<int64_t>((size_t)s1 + 1);
+      int64_t* tiles = sc.get<int64_t>((size_t)scan_tiles(s1) + 1);
+      uint64_t* rev = sc.get<uint64_t>((size_t)s1 * M);
+      CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * s1, st));
+      CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * s1, st));
+      launch_rev_count(Ly.fwd, s1, M, cnt, st);
+      launch_offsets(cnt, s1, tiles, off, st);
+      launch_rev_fill(Ly.fwd, Ly.fwd_d, s1, M, off, fill, rev, st);
+      launch_select_adj(Ly.fwd, Ly.fwd_d, s1, M, off, rev, ix->graph, Ly.adj, st);
+      CKL("edge rule");
+      CK(cudaStreamSynchronize(st));  // rows vector goes out of scope
+      Ly.size = s1;
+    }
+    ix->n = n1;
+
+    // ---- search-side layer table
+    std::vector<SearchLayer> h(ix->L + 1);
+    for (int32_t li = 0; li <= ix->L; ++li) {
+      h[li].adj = ix->layers[li].adj;
+      h[li].vec = ix->layers[li].vec;
+      h[li].scale = ix->layers[li].vscale;
+      h[li].down = ix->layers[li].down;
+      h[li].size = ix->layers[li].size;
+    }
+    CK(cudaMemcpyAsync(ix->d_layers, h.data(), sizeof(SearchLayer) * h.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  } catch (const std::exception& e) {
+    g_error = e.what();
+    return HENN_ERR_CUDA;
+  }
+}
 
 // -------------------------------------------------------------- search
 

@@ -312,7 +312,8 @@ void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t d
 // FMA, then the xor butterfly over the 32 lanes), so a flagged row gets the
 // list the certified path would give it.  Column validity: mode 0 (causal,
 // NSW) columns before the row in insertion order, mode 1 (kNN) all other
-// columns.  KD = dpad / 32 when dpad <= 128 (the loads of CPG columns are
+// columns.  inv maps insertion ranks to layer positions (nullptr: the
+// identity, as for points appended by an insertion).  KD = dpad / 32 when dpad <= 128 (the loads of CPG columns are
 // issued together), else 0 (any dpad, one column at a time, read once).
 template <int KM, int RT, int KD>
 __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__ xw, const int32_t* __restrict__ ids,
@@ -333,7 +334,7 @@ __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__
     const int64_t r = t0 + i < nrows ? (int64_t)rows[t0 + i] : -1;
     if (threadIdx.x == 0) rank_of[i] = r;
     if (r >= 0) {
-      const int64_t j = inv[r];
+      const int64_t j = inv ? (int64_t)inv[r] : r;
       const float* src = xw + (ids ? (int64_t)ids[j] : j) * dpad;
       for (int k = threadIdx.x; k < dpad; k += blockDim.x) qrows[i * dpad + k] = src[k];
     }
@@ -357,7 +358,7 @@ __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__
     int32_t myq = -1;
     const float* myrow = xw;
     if (mycol < cend) {
-      myq = inv[mycol];
+      myq = inv ? inv[mycol] : (int32_t)mycol;
       myrow = xw + (int64_t)(ids ? ids[myq] : myq) * dpad;
     }
     float dist[RT];
@@ -453,7 +454,7 @@ __global__ void __launch_bounds__(256, 2) k_exact_rows(const float* __restrict__
         const uint64_t key = merged[((int64_t)o * RT + i) * KM + c];
         if (key < all.worst()) all.insert(key);
       }
-    const int64_t j = inv[rank_of[i]];
+    const int64_t j = inv ? (int64_t)inv[rank_of[i]] : rank_of[i];
 #pragma unroll
     for (int q = 0; q < KM / 32; ++q) {
       const int g = q * 32 + lane;

@@ -1,0 +1,44 @@
+"""Dynamic Insert (App. C) on the GPU against the oracle's Insert."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+import oracle as O  # noqa: E402
+import paper_2505_17368_gb300 as H  # noqa: E402
+import synth  # noqa: E402
+
+from test_gpu_parity import DEV, _gpu_index, _graph_parity, _layers_equal  # noqa: E402
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_insert_parity(storage):
+    """Points appended by henn_insert (in two calls, so the arrays grow)
+    land in the same layers as the oracle's Insert, with the same forward
+    lists and adjacency (up to near-ties), and a search for an inserted
+    point returns it first."""
+    X = synth.uniform_cube(5200, 16, seed=41)
+    oidx = O.build_index(X[:4000], seed=6)
+    st = H.F32 if storage == "f32" else H.BF16
+    gidx = _gpu_index(X[:4000], seed=6, storage=st)
+    O.insert(oidx, X, np.arange(4000, 5200))
+    assert gidx.insert(X[4000:4600]) == 4000
+    assert gidx.insert(torch.from_numpy(X[4600:]).to(DEV)) == 4600
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+    q = np.arange(4000, 5200, 37)
+    ids, dd, _ = gidx.search(torch.from_numpy(X[q]).to(DEV), k=1, ef=64)
+    assert np.array_equal(ids.cpu().numpy()[:, 0], q)
+    assert np.all(dd.cpu().numpy()[:, 0] == 0)
+
+
+def test_insert_rejects_knn_graphs():
+    X = synth.uniform_cube(1000, 8, seed=2)
+    gidx = _gpu_index(X, graph=H.GRAPH_KNN, seed=1)
+    with pytest.raises(H.HennError) as e:
+        gidx.insert(X[:10])
+    assert e.value.status == 6
