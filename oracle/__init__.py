@@ -322,8 +322,25 @@ def insert(idx, X, new_ids, m=4):
 
 
 def search(idx, X, Q, k=10, ef=64, keys=None, out_stride=None, seed=None, ef_upper=1, ef_l1=0,
-           descend_all=0, exact_upper=0):
-    """Alg. 4 descent + layer-0 beam.  Returns (ids int64, dists f64, stats)."""
+           descend_all=0, exact_upper=0, deleted=None):
+    """Alg. 4 descent + layer-0 beam.  Returns (ids int64, dists f64, stats).
+    deleted: optional boolean mask over global ids (Delete of App. C as
+    tombstones): deleted points still carry the walk but the result is the
+    first k live entries of the final candidate list."""
+    if deleted is not None:
+        kq = np.broadcast_to(np.asarray(k, dtype=np.int32), (Q.shape[0],)).copy()
+        efq = np.broadcast_to(np.asarray(ef, dtype=np.int32), (Q.shape[0],)).copy()
+        full = np.maximum(kq, efq)
+        wi, wd, st = search(idx, X, Q, k=full, ef=efq, keys=keys, out_stride=int(full.max()), seed=seed,
+                            ef_upper=ef_upper, ef_l1=ef_l1, descend_all=descend_all, exact_upper=exact_upper)
+        stride = int(out_stride or max(int(kq.max()), 1))
+        oi = np.full((len(Q), stride), -1, np.int64)
+        od = np.full((len(Q), stride), np.inf)
+        for q in range(len(Q)):
+            live = [(i, v) for i, v in zip(wi[q], wd[q]) if i >= 0 and not deleted[i]][:kq[q]]
+            for j, (i, v) in enumerate(live):
+                oi[q, j], od[q, j] = i, v
+        return oi, od, st
     X, Q = _f32(X), _f32(Q)
     n, d = X.shape
     nq = Q.shape[0]

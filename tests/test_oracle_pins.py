@@ -635,3 +635,19 @@ def test_insert_promotion_rate():
     assert abs(hits - 20000 / 16) < 6 * sd
     deep = [O.insert_layers(3, p, 2, 6) for p in range(4000)]
     assert all(v == list(range(len(v))) for v in deep)
+
+
+def test_delete_tombstones_give_live_nearest():
+    """Delete (App. C) as tombstones: with a beam covering the whole base
+    layer the result is the exact k nearest live points (scipy)."""
+    X = synth.uniform_cube(400, 5, seed=51)
+    Q = synth.uniform_cube(30, 5, seed=52)
+    idx = O.build_index(X, seed=8)
+    dead = np.zeros(len(X), bool)
+    dead[::3] = True
+    got, gd, _ = O.search(idx, X, Q, k=10, ef=400, deleted=dead)
+    D = cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    D[:, dead] = np.inf
+    want = np.argsort(D, axis=1, kind="stable")[:, :10]
+    assert np.array_equal(got, want)
+    assert not dead[got].any()
