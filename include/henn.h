@@ -154,6 +154,18 @@ henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t x_on_device
  */
 henn_status henn_insert(henn_index* idx, const float* X, int64_t n_new, int32_t x_on_device, void* stream);
 
+/*
+ * henn_delete -- Delete (App. C) as tombstones: the points with these
+ * global ids (HOST array of n int64, each in [0, number of points)) no
+ * longer appear in search results; they stay in their layers and graphs as
+ * waypoints, and a result is the first k live entries of the final
+ * candidate list.  The paper's resampling of a layer that shrinks below its
+ * threshold is not done here: rebuild with henn_build when many points are
+ * gone.  Servers made from idx before the first delete do not see it.
+ * Synchronises `stream`.  Errors: HENN_ERR_INVALID_ARG for an id out of range.
+ */
+henn_status henn_delete(henn_index* idx, const int64_t* ids, int64_t n, void* stream);
+
 /* Releases the index and its device memory.  NULL is a no-op. */
 void henn_free(henn_index* idx);
 

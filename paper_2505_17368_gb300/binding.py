@@ -49,6 +49,7 @@ EXPORTS = [
     "henn_exact_knn",
     "henn_greedy_probe",
     "henn_insert",
+    "henn_delete",
     "henn_quantize_rows",
     "henn_last_error",
     "henn_serve_params_default",
@@ -178,6 +179,8 @@ def load(path: str | None = None):
         L.henn_greedy_probe.restype = i32
         L.henn_insert.argtypes = [vp, vp, i64, i32, vp]
         L.henn_insert.restype = i32
+        L.henn_delete.argtypes = [vp, vp, i64, vp]
+        L.henn_delete.restype = i32
         L.henn_quantize_rows.argtypes = [vp, i64, i32, i32, vp, vp, vp]
         L.henn_quantize_rows.restype = i32
         L.henn_serve_params_default.argtypes = [C.POINTER(ServeParams)]
@@ -280,6 +283,11 @@ class Index:
         self.n += X.shape[0]
         del keep
         return first
+
+    def delete(self, ids, stream=None):
+        """henn_delete: tombstone the points with these global ids."""
+        ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64).reshape(-1))
+        _check(load().henn_delete(self._h, C.c_void_p(ids.ctypes.data), ids.size, _stream(stream)))
 
     def close(self):
         if getattr(self, "_h", None) is not None and self._h.value:

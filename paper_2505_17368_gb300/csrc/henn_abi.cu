@@ -156,6 +156,8 @@ struct henn_index {
   float* x32 = nullptr;  // raw vectors, rows of dpad
   float* xw = nullptr;   // working vectors: x32 (l2) or unit rows (angular)
   float* inv_norm = nullptr;
+  uint8_t* dead = nullptr;  // 1 per deleted point (allocated at the first delete)
+  int64_t n_dead = 0;
   SearchLayer* d_layers = nullptr;
   std::vector<void*> allocs;
   int64_t bytes = 0;
@@ -602,6 +604,46 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
 
 extern "C" void henn_free(henn_index* idx) { delete idx; }
 
+// ---------------------------------------------------------------- delete
+
+namespace {
+__global__ void k_mark_dead(const int64_t* __restrict__ ids, int64_t n, uint8_t* __restrict__ dead) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dead[ids[i]] = 1;
+}
+}  // namespace
+
+extern "C" henn_status henn_delete(henn_index* ix, const int64_t* ids, int64_t n, void* stream) {
+  g_error.clear();
+  try {
+    require(ix != nullptr, "index is NULL");
+    require(n >= 0, "n must be >= 0");
+    if (n == 0) return HENN_OK;
+    require(ids != nullptr, "ids is NULL");
+    for (int64_t i = 0; i < n; ++i) require(ids[i] >= 0 && ids[i] < ix->n, "id out of range");
+    cudaStream_t st = (cudaStream_t)stream;
+    if (!ix->dead) {
+      ix->dead = ix->alloc<uint8_t>((size_t)ix->cap_n);
+      CK(cudaMemsetAsync(ix->dead, 0, (size_t)ix->cap_n, st));
+    }
+    Scratch sc(st);
+    int64_t* d_ids = sc.get<int64_t>((size_t)n);
+    CK(cudaMemcpyAsync(d_ids, ids, sizeof(int64_t) * n, cudaMemcpyHostToDevice, st));
+    int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 8);
+    k_mark_dead<<<grid, 256, 0, st>>>(d_ids, n, ix->dead);
+    CKL("delete");
+    CK(cudaStreamSynchronize(st));
+    ix->n_dead += n;  // an upper bound: a point deleted twice counts twice
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
+  } catch (const std::exception& e) {
+    g_error = e.what();
+    return HENN_ERR_CUDA;
+  }
+}
+
 // ------------------------------------------------------------- insertion
 
 namespace {
@@ -657,8 +699,10 @@ extern "C" henn_status henn_insert(henn_index* ix, const float* X, int64_t n_new
       } else if (aliased) {
         ix->xw = ix->x32;
       }
+      if (ix->dead) ix->dead = regrow(ix, ix->dead, (size_t)n0, (size_t)cap, st);
       ix->cap_n = cap;
     }
+    if (ix->dead) CK(cudaMemsetAsync(ix->dead + n0, 0, (size_t)n_new, st));
     float* xrow = ix->x32 + (size_t)n0 * dpad;
     CK(cudaMemsetAsync(xrow, 0, sizeof(float) * (size_t)n_new * dpad, st));
     CK(cudaMemcpy2DAsync(xrow, sizeof(float) * dpad, X, sizeof(float) * d, sizeof(float) * d, (size_t)n_new,
@@ -806,6 +850,7 @@ void fill_search_args(const henn_index* idx, SearchArgs& a) {
   a.storage = idx->storage;
   a.rerank = idx->storage != HENN_F32;
   a.x32 = idx->xw;
+  a.dead = idx->dead;
   a.entry_key = derive(idx->seed, HENN_TAG_ENTRY);
 }
 

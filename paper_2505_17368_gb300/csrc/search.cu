@@ -341,6 +341,21 @@ __device__ __noinline__ void finish_query(const SearchArgs& a, uint64_t* W, int 
   const int lane = lane_id();
   const int dpad = a.dpad;
   const int out_k = min(k, a.out_stride);
+  if (a.dead) {
+    // deleted points carried the walk but leave the list (order kept)
+    int live = 0;
+    for (int base = 0; base < nw; base += 32) {
+      const int i = base + lane;
+      const uint64_t e = i < nw ? W[i] : kEmpty;
+      const bool keep = i < nw && !a.dead[key_index(e & kKeyMask)];
+      const unsigned m = __ballot_sync(0xffffffffu, keep);
+      __syncwarp();
+      if (keep) W[live + __popc(m & ((1u << lane) - 1u))] = e;
+      __syncwarp();
+      live += __popc(m);
+    }
+    nw = live;
+  }
   if (a.rerank && nw > 0) {
     int R = min(nw, max(k, a.rerank_mult * k));
     // exact FP32 distances for W[0..R), then sort in place

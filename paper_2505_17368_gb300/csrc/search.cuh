@@ -24,6 +24,7 @@ struct SearchArgs {
   int32_t metric, storage;
   int32_t rerank, rerank_mult;
   const float* x32;  // FP32 layer-0 rows (unit length for angular), for the rerank
+  const uint8_t* dead;  // nullptr, or 1 per deleted point (global id): kept out of results
   const float* Q;    // nq x d queries
   int64_t nq;
   const int32_t* kq;

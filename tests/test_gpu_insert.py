@@ -42,3 +42,30 @@ def test_insert_rejects_knn_graphs():
     with pytest.raises(H.HennError) as e:
         gidx.insert(X[:10])
     assert e.value.status == 6
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_delete_parity(storage):
+    """Delete as tombstones: deleted points never come back, and recall
+    against the live points' exact neighbours tracks the oracle's."""
+    X = synth.uniform_cube(6000, 16, seed=43)
+    Q = synth.uniform_cube(300, 16, seed=44)
+    st = H.F32 if storage == "f32" else H.BF16
+    oidx = O.build_index(X, seed=9)
+    gidx = _gpu_index(X, seed=9, storage=st)
+    dead = np.zeros(len(X), bool)
+    dead[::4] = True
+    gi_all, _ = O.bruteforce(X, Q, 1)
+    dead[gi_all[:100, 0]] = True  # some queries lose their nearest point
+    gidx.delete(np.nonzero(dead)[0][: len(np.nonzero(dead)[0]) // 2])
+    gidx.delete(np.nonzero(dead)[0][len(np.nonzero(dead)[0]) // 2:])
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64)
+    ids = ids.cpu().numpy()
+    oi, od, _ = O.search(oidx, X, Q, k=10, ef=64, deleted=dead)
+    assert np.all(ids >= 0) and not dead[ids].any()
+    live = np.nonzero(~dead)[0]
+    li, ld = O.bruteforce(X[live], Q, 10)
+    gt = live[li]
+    rec = lambda found: np.mean([len(set(found[q]) & set(gt[q])) / 10 for q in range(len(Q))])  # noqa: E731
+    assert abs(rec(ids) - rec(oi)) <= 0.02, (rec(ids), rec(oi))
+    assert np.all(np.diff(dd.cpu().numpy(), axis=1) >= 0)
