@@ -6,6 +6,7 @@ error of the returned results against FP64.
     python -m paper_2505_17368_gb300.workload_bench --workload exponential-50k-d32-l4
     python -m paper_2505_17368_gb300.workload_bench --workload exponential-1m-d16-l4 --scaling 16384,65536,262144,1048576
     python -m paper_2505_17368_gb300.workload_bench --workload exponential-50k-d32-l4 --rho
+    python -m paper_2505_17368_gb300.workload_bench --workload mixture-1m-d128 --storage bf16 --insert 100000 --ef 64 --ef-upper 64
 
 For each storage form: one index build (timed), FP32 ground truth on the
 device (henn_exact_knn), a sweep of (ef_upper, ef) timed with CUDA events
@@ -253,6 +254,46 @@ def recall_bound(workload, n=None, nq=1000, starts=64, K=100, deltas=(0.5, 0.9),
     return out
 
 
+def synth_n(workload):
+    import synth
+
+    return synth.WORKLOADS[workload]["n"]
+
+
+def dynamic(workload, n, n_insert, batch, ef, ef_upper, storage="bf16"):
+    """Insert (App. C) throughput and its effect on recall: build on the
+    first n - n_insert points, insert the rest in batches, then compare
+    recall@10 with a fresh build of all n points at the same beam."""
+    import torch
+
+    import paper_2505_17368_gb300 as H
+    import synth
+
+    X, Q, info = synth.workload(workload, n=n)
+    form = {"f32": H.F32, "bf16": H.BF16, "fp8": H.FP8E4M3}[storage]
+    Xd, Qd = torch.from_numpy(X).cuda(), torch.from_numpy(Q).cuda()
+    gi, _ = H.exact_knn(Xd, Qd, K)
+    gt = gi.cpu().numpy()
+    base = n - n_insert
+    idx = H.Index(Xd[:base], storage=form, seed=0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for s in range(base, n, batch):
+        idx.insert(Xd[s:min(n, s + batch)])
+    torch.cuda.synchronize()
+    secs = time.perf_counter() - t0
+    ids, _, _ = idx.search(Qd, k=K, ef=ef, ef_upper=ef_upper)
+    r_ins = _recall(ids.cpu().numpy(), gt)
+    sizes_ins = idx.info()["sizes"]
+    del idx
+    fresh = H.Index(Xd, storage=form, seed=0)
+    ids, _, _ = fresh.search(Qd, k=K, ef=ef, ef_upper=ef_upper)
+    return {"workload": workload, "n": n, "inserted": n_insert, "batch": batch, "insert_seconds": secs,
+            "inserts_per_second": n_insert / secs, "recall_at_10_after_insert": r_ins,
+            "recall_at_10_fresh_build": _recall(ids.cpu().numpy(), gt), "ef": ef, "ef_upper": ef_upper,
+            "layers_after_insert": sizes_ins, "layers_fresh": fresh.info()["sizes"]}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="shells-1m-d64")
@@ -264,7 +305,13 @@ def main():
     ap.add_argument("--ef", type=int, default=10)
     ap.add_argument("--ef-upper", type=int, default=1)
     ap.add_argument("--rho", action="store_true", help="recall bound rho_delta and recall@k vs k, NSW and kNN graphs")
+    ap.add_argument("--insert", type=int, default=0, help="points to insert after building on the rest")
+    ap.add_argument("--batch", type=int, default=10000)
     a = ap.parse_args()
+    if a.insert:
+        print(json.dumps(dynamic(a.workload, a.n or synth_n(a.workload), a.insert, a.batch, a.ef, a.ef_upper,
+                                 a.storage)), flush=True)
+        return
     if a.rho:
         for r in recall_bound(a.workload, n=a.n, nq=a.nq or 1000):
             print(json.dumps(r), flush=True)
