@@ -419,7 +419,8 @@ def _build_roofline(info):
 def _profile_traffic(beam):
     """DRAM bytes per launch of the search kernel from the committed ncu
     summary, if it was taken on the current kernel source with the same
-    beam configuration (ef, ef_upper, descend_all, ef_l1); else None."""
+    beam configuration (ef, ef_upper, descend_all, ef_l1, exact_upper);
+    else None."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "search_bf16_mixture-1m-d128.md")
@@ -429,7 +430,7 @@ def _profile_traffic(beam):
         kv = {}
         for line in open(path):
             if ":" in line and line.startswith("- "):
-                k, v = line[2:].split(":", 1)
+                k, v = line[2:].rsplit(":", 1)  # keys may hold a colon ("sha256[:16]")
                 kv[k.strip()] = v.strip().strip("`")
         want = "ef={} ef_upper={} descend_all={} ef_l1={} exact_upper={}".format(*beam)
         if kv.get("search.cu sha256[:16]") == sha:
