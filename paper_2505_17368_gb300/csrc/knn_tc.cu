@@ -355,13 +355,33 @@ __global__ void __launch_bounds__(192, 1)
           const uint64_t key = isinf(dv) ? kEmpty : pack(dv, (uint32_t)(c0 + lane));
           uint64_t worst = lst[31];
           unsigned bm = __ballot_sync(0xffffffffu, key < worst);
-          while (bm) {
-            const int src = __ffs(bm) - 1;
-            bm &= bm - 1;
-            const uint64_t x = shfl64(key, src);
-            if (x < worst) {
-              tc::list_insert_smem(lst, x);
-              worst = lst[31];
+          if (__popc(bm) >= 6) {
+            // many candidates (a row's early tiles): sort them across the
+            // warp and merge with the sorted list; the element-wise minimum
+            // of the list and the reversed candidates holds the 32 smallest
+            // as a bitonic sequence, which five half-cleaners sort
+            uint64_t r = warp_sort_asc(key < worst ? key : kEmpty);
+            r = shfl64(r, 31 - lane);
+            const uint64_t l = lst[lane];
+            r = l < r ? l : r;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+              const uint64_t o = shfl_xor64(r, j);
+              r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+            }
+            __syncwarp();
+            lst[lane] = r;
+            __syncwarp();
+            worst = shfl64(r, 31);
+          } else {
+            while (bm) {
+              const int src = __ffs(bm) - 1;
+              bm &= bm - 1;
+              const uint64_t x = shfl64(key, src);
+              if (x < worst) {
+                tc::list_insert_smem(lst, x);
+                worst = lst[31];
+              }
             }
           }
           const float nthr = worst == kEmpty ? kInf : key_dist(worst);
