@@ -194,10 +194,29 @@ typedef struct {
   int32_t ef_l1;              /* beam width on layer 1 only; 0 = ef_upper          */
   int32_t exact_upper;        /* upper layers of at most this many points give
                                  their exact candidate set (the layer's nearest
-                                 max(width, 1) points, every point evaluated)
-                                 instead of a walk; 0 = never (default); at most
-                                 2^(hash_bits - 1)                                  */
+                                 max(width, 1) points, by the traversal distance)
+                                 instead of a walk; 0 = never (default).  Only the
+                                 lowest such layer is computed: its result
+                                 replaces those of the layers above it           */
+  int32_t exact_method;       /* how that layer's set is found (henn_exact_method):
+                                 SORT: per query, every point evaluated and sorted
+                                 in the visited table (layer of at most
+                                 2^(hash_bits - 1) points; default);
+                                 TILES: one batched distance-tile launch (tcgen05
+                                 for dpad <= 128, else SIMT) gives each query 32
+                                 candidates, rescored in traversal precision and
+                                 kept when a tile-error certificate proves them
+                                 to hold the set, else a scan of the layer;
+                                 SCAN: every point evaluated, running top 32.
+                                 TILES and SCAN: any layer size; with descend_all
+                                 the layer's width must be <= 32.  All three give
+                                 the same set                                     */
+  int32_t time_kernel;        /* 1: record device events around this call's
+                                 search launches (henn_last_search_ms)           */
 } henn_search_params;
+
+/* exact_method values */
+typedef enum { HENN_EXACT_SORT = 0, HENN_EXACT_TILES = 1, HENN_EXACT_SCAN = 2 } henn_exact_method;
 
 void henn_search_params_default(henn_search_params* sp);
 
@@ -220,6 +239,17 @@ void henn_search_params_default(henn_search_params* sp);
 henn_status henn_search(const henn_index* idx, const float* Q, int64_t nq, int32_t q_on_device,
                         const henn_search_params* sp, int64_t* out_ids, float* out_dists,
                         int32_t out_stride, void* stream);
+
+/*
+ * henn_last_search_ms -- device time of the search-kernel launches of the
+ * last henn_search on this index made with time_kernel = 1 (events recorded
+ * on its stream, around the launches only: query preparation and the tile
+ * launch of exact_method TILES are outside), and the number of kernel
+ * launches that call made.  Waits for the end event.  Either output may be
+ * NULL.  Errors: HENN_ERR_INVALID_ARG if no timed search ran on the index.
+ * One timed search at a time per index.
+ */
+henn_status henn_last_search_ms(const henn_index* idx, float* ms, int32_t* launches);
 
 /* ------------------------------------------------------ introspection */
 

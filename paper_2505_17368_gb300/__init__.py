@@ -6,7 +6,7 @@ package is the Python binding.  `build()` compiles the library in tree.
 """
 from .binding import (  # noqa: F401
     ANGULAR, BF16, F32, FP8E4M3, GRAPH_KNN, GRAPH_NSW, L2, SAMPLER_HALVING, SAMPLER_SAMPLING, TILES_AUTO, TILES_SIMT,
-    TILES_TCGEN05,
+    TILES_TCGEN05, EXACT_SORT, EXACT_TILES, EXACT_SCAN,
     HennError, Index, Server, exact_knn, load, quantize_rows,
 )
 

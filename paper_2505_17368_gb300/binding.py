@@ -24,6 +24,7 @@ F32, BF16, FP8E4M3 = 0, 1, 2
 GRAPH_NSW, GRAPH_KNN = 0, 1
 TILES_AUTO, TILES_SIMT, TILES_TCGEN05 = 0, 1, 2
 SAMPLER_SAMPLING, SAMPLER_HALVING = 0, 1
+EXACT_SORT, EXACT_TILES, EXACT_SCAN = 0, 1, 2
 MAX_LAYERS = 32
 
 STATUS = {
@@ -58,6 +59,7 @@ EXPORTS = [
     "henn_serve_poll",
     "henn_serve_destroy",
     "henn_search_host_noalloc",
+    "henn_last_search_ms",
 ]
 
 
@@ -102,6 +104,8 @@ class SearchParams(C.Structure):
         ("descend_all", C.c_int32),
         ("ef_l1", C.c_int32),
         ("exact_upper", C.c_int32),
+        ("exact_method", C.c_int32),
+        ("time_kernel", C.c_int32),
     ]
 
 
@@ -195,6 +199,8 @@ def load(path: str | None = None):
         L.henn_serve_destroy.restype = None
         L.henn_search_host_noalloc.argtypes = [vp, vp, i64, i32, i32, i32, vp, vp, i32, vp]
         L.henn_search_host_noalloc.restype = i32
+        L.henn_last_search_ms.argtypes = [vp, C.POINTER(C.c_float), C.POINTER(i32)]
+        L.henn_last_search_ms.restype = i32
         L.henn_last_error.argtypes = []
         L.henn_last_error.restype = C.c_char_p
         _lib = L
@@ -347,7 +353,7 @@ class Index:
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
                warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None,
-               exact_upper=0):
+               exact_upper=0, exact_method=EXACT_SORT, time_kernel=False):
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
@@ -385,6 +391,8 @@ class Index:
         sp.descend_all = int(descend_all)
         sp.ef_l1 = int(ef_l1)
         sp.exact_upper = int(exact_upper)
+        sp.exact_method = int(exact_method)
+        sp.time_kernel = int(bool(time_kernel))
         if keys is not None:
             p, _, kk = _ptr(keys)
             sp.query_keys = p
@@ -410,6 +418,14 @@ class Index:
                              _stream(stream)))
         del keep, kq
         return ids, dists, st
+
+    def last_search_ms(self):
+        """(device ms of the search launches, kernel launches) of the last
+        search made with time_kernel=True (henn_last_search_ms)."""
+        ms = C.c_float()
+        n = C.c_int32()
+        _check(load().henn_last_search_ms(self._h, C.byref(ms), C.byref(n)))
+        return float(ms.value), int(n.value)
 
 
 def search_host_noalloc(index: "Index", Q, k=10, ef=64, ef_upper=1, out_stride=None, stream=None):

@@ -53,14 +53,18 @@ void require(bool ok, const std::string& msg) {
 // scope (also on failure).
 struct Scratch {
   cudaStream_t st;
+  cudaMemPool_t pool;
   std::vector<void*> ptrs;
-  explicit Scratch(cudaStream_t s) : st(s) {}
+  explicit Scratch(cudaStream_t s, cudaMemPool_t p = nullptr) : st(s), pool(p) {}
   template <typename T>
   T* get(size_t count) {
     void* p = nullptr;
     size_t bytes = count * sizeof(T);
     if (bytes == 0) bytes = 16;
-    CK(cudaMallocAsync(&p, bytes, st));
+    if (pool)
+      CK(cudaMallocFromPoolAsync(&p, bytes, pool, st));
+    else
+      CK(cudaMallocAsync(&p, bytes, st));
     ptrs.push_back(p);
     return static_cast<T*>(p);
   }
@@ -191,7 +195,61 @@ struct henn_index {
   // (created on first use)
   mutable std::mutex side_mu;
   mutable std::vector<cudaStream_t> side;
+  // Tile operands of an exact upper layer (exact_method TILES), made at its
+  // first use: the layer's traversal rows as FP32 minus their mean, split
+  // into BF16 planes (tcgen05) or kept as FP32 rows (SIMT), their squared
+  // norms and the largest of them.
+  struct EntryOps {
+    int64_t size = 0;    // 0: not made
+    int32_t engine = 0;  // HENN_TILES_TCGEN05 or HENN_TILES_SIMT
+    void* hi = nullptr;
+    void* lo = nullptr;
+    alignas(64) unsigned char maps[256];  // tensor maps of hi / lo (tcgen05)
+    float* xo = nullptr;
+    float* mean = nullptr;
+    float* norms = nullptr;
+    float* nmax = nullptr;
+    std::vector<void*> mem;
+  };
+  mutable std::mutex entry_mu;
+  mutable std::vector<EntryOps> entry;
+  void drop_entry_ops() const {
+    std::lock_guard<std::mutex> lk(entry_mu);
+    for (EntryOps& e : entry)
+      for (void* p : e.mem) cudaFree(p);
+    entry.clear();
+  }
+  // search scratch comes from this pool, which keeps its memory between
+  // calls (created on first use)
+  mutable std::mutex pool_mu;
+  mutable cudaMemPool_t pool = nullptr;
+  cudaMemPool_t search_pool() const {
+    std::lock_guard<std::mutex> lk(pool_mu);
+    if (!pool) {
+      cudaMemPoolProps props;
+      std::memset(&props, 0, sizeof(props));
+      props.allocType = cudaMemAllocationTypePinned;
+      props.location.type = cudaMemLocationTypeDevice;
+      props.location.id = device;
+      CK(cudaMemPoolCreate(&pool, &props));
+      uint64_t keep = UINT64_MAX;
+      CK(cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep));
+    }
+    return pool;
+  }
+  // events of the last search with time_kernel = 1
+  mutable std::mutex time_mu;
+  mutable cudaEvent_t tev[2] = {nullptr, nullptr};
+  mutable int32_t t_launches = 0;
+  mutable bool t_valid = false;
   ~henn_index() {
+    drop_entry_ops();
+    if (pool) {
+      cudaDeviceSynchronize();
+      cudaMemPoolDestroy(pool);
+    }
+    for (cudaEvent_t e : tev)
+      if (e) cudaEventDestroy(e);
     for (cudaStream_t t : side) cudaStreamDestroy(t);
     for (void* p : allocs) cudaFree(p);
   }
@@ -673,6 +731,7 @@ extern "C" henn_status henn_insert(henn_index* ix, const float* X, int64_t n_new
     if (ix->graph != HENN_GRAPH_NSW) throw Failure(HENN_ERR_UNSUPPORTED, "insertion supports NSW graphs only");
     require(ix->n + n_new < (int64_t)INT32_MAX, "too many points");
     CK(cudaStreamSynchronize((cudaStream_t)stream));
+    ix->drop_entry_ops();  // upper layers may grow
     struct OwnStream {
       cudaStream_t s = nullptr;
       ~OwnStream() {
@@ -852,7 +911,62 @@ void fill_search_args(const henn_index* idx, SearchArgs& a) {
   a.x32 = idx->xw;
   a.dead = idx->dead;
   a.entry_key = derive(idx->seed, HENN_TAG_ENTRY);
+  a.top_exact = idx->L;
+  a.exact_method = HENN_EXACT_SORT;
 }
+
+// The tile operands of upper layer li (exact_method TILES), made on first
+// use on stream st and waited for, so that any stream may use them after.
+const henn_index::EntryOps& entry_ops(const henn_index* idx, int32_t li, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(idx->entry_mu);
+  if ((int)idx->entry.size() <= li) idx->entry.resize(li + 1);
+  henn_index::EntryOps& e = idx->entry[li];
+  const LayerDev& Ly = idx->layers[li];
+  if (e.size == Ly.size) return e;
+  for (void* p : e.mem) cudaFree(p);
+  e = henn_index::EntryOps();
+  const int64_t s = Ly.size;
+  const int32_t dpad = idx->dpad;
+  auto get = [&](size_t bytes) {
+    void* p = nullptr;
+    CK(cudaMalloc(&p, bytes > 0 ? bytes : 16));
+    e.mem.push_back(p);
+    return p;
+  };
+  Scratch sc(st);
+  float* rows = sc.get<float>((size_t)s * dpad);
+  CK(launch_layer_rows_f32(Ly.vec, Ly.vscale, s, idx->storage, dpad, rows, st));
+  e.mean = static_cast<float*>(get(sizeof(float) * dpad));
+  float* partial = sc.get<float>((size_t)((s + 4095) / 4096) * dpad);
+  launch_layer_mean(rows, nullptr, s, dpad, partial, e.mean, st);
+  int32_t* inv = sc.get<int32_t>(s);
+  float* xo = sc.get<float>((size_t)s * dpad);
+  e.norms = static_cast<float*>(get(sizeof(float) * s));
+  launch_order_gather(rows, nullptr, s, dpad, 0, 0, HENN_GRAPH_KNN, e.mean, inv, xo, e.norms, st);
+  e.nmax = static_cast<float*>(get(sizeof(float)));
+  launch_max_nonneg(e.norms, s, e.nmax, st);
+  if (tc_tiles_supported(dpad, 32)) {
+    const int32_t dk = round_up(dpad, 64);
+    e.hi = get((size_t)s * dk * 2);
+    e.lo = get((size_t)s * dk * 2);
+    launch_split_bf16(xo, s, dpad, dk, e.hi, e.lo, st);
+    require(make_column_maps(e.hi, e.lo, s, dk, e.maps), "tensor maps of the exact layer");
+    e.engine = HENN_TILES_TCGEN05;
+  } else {
+    e.xo = static_cast<float*>(get(sizeof(float) * s * dpad));
+    CK(cudaMemcpyAsync(e.xo, xo, sizeof(float) * s * dpad, cudaMemcpyDeviceToDevice, st));
+    e.engine = HENN_TILES_SIMT;
+  }
+  CKL("exact-layer operands");
+  CK(cudaStreamSynchronize(st));
+  e.size = s;
+  return e;
+}
+
+// exact_method TILES: layers up to this size (and matrices up to this many
+// bytes) go through the distance matrix instead of in-epilogue lists
+constexpr int64_t kDenseExactMax = 16384;
+constexpr double kDenseExactBytes = 1.0 * (1 << 30);
 
 int persistent_grid(int device, int warps, size_t smem) {
   int sms = 0;
@@ -912,6 +1026,21 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     require(sp.ef_upper >= 0 && sp.ef_upper <= 4096, "ef_upper must be in [0, 4096]");
     require(sp.ef_l1 >= 0 && sp.ef_l1 <= 4096, "ef_l1 must be in [0, 4096]");
     require(sp.exact_upper >= 0, "exact_upper must be >= 0");
+    require(sp.exact_method >= HENN_EXACT_SORT && sp.exact_method <= HENN_EXACT_SCAN, "exact_method must be 0, 1 or 2");
+    // the lowest upper layer with at most exact_upper points (sizes shrink
+    // upwards); the layers above it are skipped
+    int32_t top_exact = idx->L;
+    bool has_exact = false;
+    for (int32_t li = 1; sp.exact_upper > 0 && li <= idx->L; ++li)
+      if (idx->layers[li].size <= sp.exact_upper) {
+        top_exact = li;
+        has_exact = true;
+        break;
+      }
+    const int32_t exact_width = (top_exact == 1 && sp.ef_l1 > 0) ? sp.ef_l1 : sp.ef_upper;
+    if (has_exact && sp.exact_method != HENN_EXACT_SORT)
+      require(!(sp.descend_all && exact_width > 32),
+              "exact_method TILES / SCAN with descend_all needs the exact layer's width (ef_upper, or ef_l1 on layer 1) <= 32");
     // beam capacity of a query: the power of two holding its widest list
     auto cap_of = [&](int32_t kq, int32_t efq) {
       int nd = std::max(std::max(kq, efq), std::max((int)sp.ef_upper, (int)sp.ef_l1));
@@ -926,11 +1055,13 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     // the exact layers' keys sit in the visited table; capacity-group launches
     // (default table sizes) use at least 2^10 slots
     const int hb_min = sp.hash_bits > 0 ? hb : 10;
-    require(sp.exact_upper <= (1 << (hb_min - 1)), "exact_upper must be <= 2^(hash_bits - 1) (512 by default)");
+    if (has_exact && sp.exact_method == HENN_EXACT_SORT)
+      require(idx->layers[top_exact].size <= (1 << (hb_min - 1)),
+              "exact_method SORT: the exact layer must have <= 2^(hash_bits - 1) points (512 by default)");
     int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
     require(warps >= 1 && warps <= kSearchWarps, "warps_per_block must be in [1, 4]");
 
-    Scratch sc(st);
+    Scratch sc(st, idx->search_pool());
     const float* dQ = Q;
     const int32_t* dk = sp.k;
     const int32_t* def = sp.ef;
@@ -1013,6 +1144,57 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.descend_all = sp.descend_all;
     a.ef_l1 = sp.ef_l1;
     a.exact_upper = sp.exact_upper;
+    a.top_exact = top_exact;
+    a.exact_method = has_exact ? sp.exact_method : HENN_EXACT_SORT;
+    int32_t launches = 0;
+    if (has_exact && sp.exact_method == HENN_EXACT_TILES) {
+      // batched candidates of the exact layer: queries against all its points
+      const henn_index::EntryOps& eo = entry_ops(idx, top_exact, st);
+      const int64_t s = eo.size;
+      const int32_t dpad = idx->dpad;
+      float* qn = sc.get<float>(nq);
+      uint64_t* pkeys = sc.get<uint64_t>((size_t)nq * 32);
+      int32_t* perr = sc.get<int32_t>(1);
+      CK(cudaMemsetAsync(perr, 0, sizeof(int32_t), st));
+      if (eo.engine == HENN_TILES_TCGEN05) {
+        const int32_t dkk = round_up(dpad, 64);
+        void* qh = sc.get<uint16_t>((size_t)nq * dkk);
+        void* ql = sc.get<uint16_t>((size_t)nq * dkk);
+        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, nullptr, qh, ql, dkk, qn, st);
+        // a small layer: the distance matrix itself (written and read once,
+        // coalesced) and a selection pass at full occupancy; else the
+        // running lists inside the tile epilogue
+        const int64_t ldo = (s + 31) / 32 * 32;
+        if (s <= kDenseExactMax && (double)nq * (double)ldo * 4.0 <= kDenseExactBytes) {
+          float* dm = sc.get<float>((size_t)nq * ldo);
+          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, st));
+          launch_select_top32(dm, nq, s, ldo, pkeys, st);
+          launches += 1;
+        } else {
+          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, st));
+        }
+        // as for the construction tiles: split BF16 products plus FP32
+        // accumulation over 3 * dk terms, doubled
+        a.pre_tile_u = 3.0 * std::ldexp(1.0, -18) + 2.0 * (3.0 * dkk + 8.0) * std::ldexp(1.0, -24);
+        launches += 2;
+      } else {
+        float* qo = sc.get<float>((size_t)nq * dpad);
+        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, qo, nullptr, nullptr, 0, qn, st);
+        const int64_t rb = (nq + 63) / 64;
+        const int32_t splits =
+            (int32_t)std::max<int64_t>(1, std::min<int64_t>((2 * 152 + rb - 1) / rb, (s + 4095) / 4096));
+        uint64_t* cand = splits > 1 ? sc.get<uint64_t>((size_t)splits * nq * 32) : pkeys;
+        launch_tile_topk_simt(qo, qn, nq, eo.xo, eo.norms, s, dpad, 2, 32, splits, cand, st);
+        if (splits > 1) launch_merge_splits(cand, nq, 32, splits, pkeys, st);
+        a.pre_tile_u = (dpad + 8.0) * std::ldexp(1.0, -24);
+        launches += splits > 1 ? 3 : 2;
+      }
+      CKL("exact-layer tiles");
+      a.pre_keys = pkeys;
+      a.pre_qnorm = qn;
+      a.pre_nmax = eo.nmax;
+      a.pre_err = perr;
+    }
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.keys = dkeys;
@@ -1022,6 +1204,14 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.stats = dstats;
     a.counter = counter;
 
+    std::unique_lock<std::mutex> tlk(idx->time_mu, std::defer_lock);
+    if (sp.time_kernel) {
+      tlk.lock();
+      for (cudaEvent_t& e : idx->tev)
+        if (!e) CK(cudaEventCreate(&e));
+      CK(cudaEventRecord(idx->tev[0], st));
+    }
+    launches += groups;
     if (groups == 1) {
       size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
       int64_t blocks_needed = (nq + warps - 1) / warps;
@@ -1058,6 +1248,12 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
       }
       cudaEventDestroy(fork);
     }
+    if (sp.time_kernel) {
+      CK(cudaEventRecord(idx->tev[1], st));
+      idx->t_launches = launches;
+      idx->t_valid = true;
+      tlk.unlock();
+    }
     if (!q_on_device) {
       CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
       CK(cudaMemcpyAsync(out_dists, dd, sizeof(float) * nq * out_stride, cudaMemcpyDeviceToHost, st));
@@ -1071,6 +1267,24 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
   } catch (const std::exception& e) {
     g_error = e.what();
     return HENN_ERR_CUDA;
+  }
+}
+
+extern "C" henn_status henn_last_search_ms(const henn_index* idx, float* ms, int32_t* launches) {
+  g_error.clear();
+  try {
+    require(idx != nullptr, "index is NULL");
+    std::lock_guard<std::mutex> lk(idx->time_mu);
+    require(idx->t_valid, "no search with time_kernel = 1 ran on this index");
+    if (ms) {
+      CK(cudaEventSynchronize(idx->tev[1]));
+      CK(cudaEventElapsedTime(ms, idx->tev[0], idx->tev[1]));
+    }
+    if (launches) *launches = idx->t_launches;
+    return HENN_OK;
+  } catch (const Failure& f) {
+    g_error = f.msg;
+    return f.status;
   }
 }
 

@@ -76,6 +76,19 @@ void launch_merge_splits(const uint64_t* in, int64_t rows, int32_t KP, int32_t s
 bool tc_tiles_supported(int32_t dpad, int32_t KP);
 cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, int32_t dpad, int32_t mode,
                                 uint64_t* out, void* scratch_hi, void* scratch_lo, int32_t* err, cudaStream_t st);
+// FP32 rows (dpad wide) -> BF16 planes hi = bf16(x), lo = bf16(x - hi), dk wide (zero padded)
+void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void* hi, void* lo, cudaStream_t st);
+// mode 2 on tensor cores from pre-split planes: na rows (queries) against nb
+// columns (a layer's points), out = na x 32 keys (distance, column); with
+// out_d (mode 3) the distances themselves instead, na rows of ldo floats
+// (ldo a multiple of 32, >= nb; +inf past column nb)
+// b_maps: the two tensor maps (hi, lo) of make_column_maps, 128 bytes each
+cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
+                                 const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
+                                 float* out_d, int64_t ldo, int32_t* err, cudaStream_t st);
+// Tensor maps of the column operand (hi, lo planes of nb rows, dk wide) for
+// launch_tile_cross_tc, written to maps (2 x 128 bytes); false if not encodable.
+bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk, void* maps);
 // exact FP32 rerank of layer candidates -> forward lists (layer-local ids)
 void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t dpad, int32_t metric,
                        const int32_t* inv, const uint64_t* cand, int32_t KP, int32_t M, const float* norms,

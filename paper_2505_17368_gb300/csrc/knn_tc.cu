@@ -1,10 +1,12 @@
 // knn_tc.cu -- construction distance tiles on the 5th-generation tensor
 // cores (tcgen05 + TMA + TMEM), with the running top-KP per row fused into
-// the epilogue.  Same contract as the SIMT engine in knn.cu: rows and
-// columns are a layer's centred vectors in insertion order, the tile value
-// is |a|^2 + |b|^2 - 2<a,b>, column c is valid for row r iff c < r (causal,
-// NSW) or c != r (kNN graph), and every row keeps its KP smallest
-// (distance, column) keys.
+// the epilogue.  Same contract as the SIMT engine in knn.cu: the tile value
+// is |a|^2 + |b|^2 - 2<a,b> of centred vectors and every row keeps its KP
+// smallest (distance, column) keys.  Modes 0 and 1 take rows and columns
+// from one layer in insertion order, column c valid for row r iff c < r
+// (causal, NSW) or c != r (kNN graph); mode 2 takes the rows from one set
+// (queries) and every column from another (a layer's points); mode 3 is
+// mode 2 writing every tile value (the distance matrix) instead of lists.
 //
 // Precision: each FP32 operand is split into x = hi + lo with hi =
 // bf16(x), lo = bf16(x - hi); the tile accumulates hi.hi + lo.hi + hi.lo in
@@ -48,7 +50,10 @@ struct Smem {
   // 1024-byte aligned operand buffers first
   uint8_t a[2 * MAX_KC][A_CHUNK];  // hi chunks then lo chunks
   uint8_t b[NS][B_CHUNK];
-  uint64_t lists[BM][KP];          // running top-KP per row
+  // running top-KP of each row: a max-heap of keys, 1-based (children of
+  // p at 2p and 2p + 1, so a sibling pair is one 16-byte load), root = the
+  // KP-th smallest so far; slot KP + 1 holds 0 (no child), slot 0 is unused
+  uint64_t heap[BM][KP + 2];
   alignas(16) float ncol[4][BN];   // column norms of the current tile, one copy per epilogue warp
   float s[4][32][S_LD];            // epilogue transposition, one slab per warp
   uint64_t full[NS], empty[NS], tfull[2], tempty[2], afull;
@@ -148,17 +153,19 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
-// One row's list in shared memory <-> warp registers (lane holds one key).
-__device__ __forceinline__ void list_insert_smem(uint64_t* row_list, uint64_t key) {
-  const int lane = lane_id();
-  uint64_t v = row_list[lane];
-  uint64_t up = __shfl_up_sync(0xffffffffu, v, 1);
-  bool dup = __any_sync(0xffffffffu, v == key);
-  if (dup) return;
-  uint64_t nv = v;
-  if (!(v < key)) nv = (lane == 0 || up < key) ? key : up;
-  row_list[lane] = nv;
-  __syncwarp();
+// Replaces the root of a row's max-heap (heap[1..KP], heap[KP + 1] = 0) by
+// a smaller key and sifts it down.
+__device__ __forceinline__ void heap_replace(uint64_t* heap, uint64_t key) {
+  int p = 1;
+  for (int c = 2; c <= KP; c = 2 * p) {
+    const ulonglong2 ch = *reinterpret_cast<const ulonglong2*>(heap + c);
+    const bool right = ch.y > ch.x;
+    const uint64_t mv = right ? ch.y : ch.x;
+    if (mv < key) break;  // keys are distinct
+    heap[p] = mv;
+    p = c + (right ? 1 : 0);
+  }
+  heap[p] = key;
 }
 
 }  // namespace tc
@@ -168,15 +175,17 @@ using namespace tc;
 __global__ void __launch_bounds__(192, 1)
     k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
-                   const float* __restrict__ norms, int64_t s, int32_t kc, int32_t mode,
-                   uint64_t* __restrict__ out, int32_t* __restrict__ err) {
+                   const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
+                   int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
+                   int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nrb = (s + BM - 1) / BM;
   const int64_t rb = (mode == 0) ? (nrb - 1 - blockIdx.x) : blockIdx.x;
   const int64_t r0 = rb * BM;
-  const int64_t cend = (mode == 0) ? min(s, r0 + BM) : s;
+  // s rows; sc columns (== s unless mode 2)
+  const int64_t cend = (mode == 0) ? min(s, r0 + BM) : sc;
   const int nt = (int)((cend + BN - 1) / BN);
   const int chunks_per_tile = 2 * kc;  // (B_hi, B_lo) per 64-wide slice
 
@@ -194,7 +203,8 @@ __global__ void __launch_bounds__(192, 1)
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
   }
-  for (int i = threadIdx.x; i < BM * KP; i += blockDim.x) (&sm.lists[0][0])[i] = kEmpty;
+  for (int i = threadIdx.x; i < BM * (KP + 2); i += blockDim.x)
+    (&sm.heap[0][0])[i] = (i % (KP + 2) == KP + 1) ? 0ull : kEmpty;
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 512;" ::"r"(tc::smem_u32(&sm.tmem_base)));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
@@ -284,12 +294,14 @@ __global__ void __launch_bounds__(192, 1)
     const int64_t grow = r0 + row_l;
     const float nrow = grow < s ? norms[grow] : 0.f;
     // valid columns of this row: [0, lim), minus the row itself for kNN
-    const int32_t lim = grow >= s ? 0 : (int32_t)(mode == 0 ? grow : s);
+    const int32_t lim = grow >= s ? 0 : (int32_t)(mode == 0 ? grow : sc);
     const int32_t self = mode == 1 ? (int32_t)grow : -1;
     const float kInf = __int_as_float(0x7f800000);
     // the row's threshold with its own norm folded in:
     // n_row + n_col - 2v <= thr  <=>  n_col - 2v <= thr - n_row
     float thr_adj = kInf;
+    uint64_t* heap = sm.heap[row_l];
+    uint64_t root = kEmpty;
     bool ok = true;
     for (int t = 0; t < nt; ++t) {
       const int as = t & 1;
@@ -304,7 +316,7 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
       for (int q = 0; q < BN / 32; ++q) {
         const int64_t c = (int64_t)t * BN + q * 32 + lane;
-        ncs[q * 32 + lane] = c < s ? __ldg(norms + c) : 0.f;
+        ncs[q * 32 + lane] = c < sc ? __ldg(norms_c + c) : 0.f;
       }
       __syncwarp();
 #pragma unroll 1
@@ -326,6 +338,25 @@ __global__ void __launch_bounds__(192, 1)
           v[4 * j4 + 3] = fmaf(-2.f, v[4 * j4 + 3], nn.w);
           vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
         }
+        if (mode == 3) {
+          // the row's 32 distances (+inf past the last column; NaN, which
+          // no list would take, as +inf too), one 128-byte run per lane
+          if (grow < s) {
+            float4* dst = reinterpret_cast<float4*>(out_d + grow * ldo + c0);
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              float o[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e) {
+                const float dv = nrow + v[4 * j4 + e];
+                o[e] = (c0 + 4 * j4 + e < sc && dv == dv) ? fmaxf(dv, 0.f) : kInf;
+              }
+              __stcs(dst + j4, make_float4(o[0], o[1], o[2], o[3]));
+            }
+          }
+          __syncwarp();
+          continue;
+        }
         const bool maybe = vmin <= thr_adj;
         if (!__any_sync(0xffffffffu, maybe)) continue;
         unsigned keep = 0;
@@ -339,56 +370,26 @@ __global__ void __launch_bounds__(192, 1)
           for (int j = 0; j < 32; ++j) keep |= (v[j] <= thr_adj) ? (1u << j) : 0u;
           keep &= vmask;
         }
-        unsigned m = __ballot_sync(0xffffffffu, keep != 0);
-        if (!m) continue;
         if (keep) {
+          // this lane's row: stage the passing values, then offer them to
+          // the row's heap one by one (rows in parallel, one per lane)
+          float* srow = sm.s[ew][lane];
 #pragma unroll
-          for (int j = 0; j < 32; ++j)
-            sm.s[ew][lane][j] = (keep >> j) & 1u ? fmaxf(nrow + v[j], 0.f) : kInf;
-        }
-        __syncwarp();
-        while (m) {
-          const int i = __ffs(m) - 1;
-          m &= m - 1;
-          uint64_t* lst = sm.lists[32 * sub + i];
-          const float dv = sm.s[ew][i][lane];
-          const uint64_t key = isinf(dv) ? kEmpty : pack(dv, (uint32_t)(c0 + lane));
-          uint64_t worst = lst[31];
-          unsigned bm = __ballot_sync(0xffffffffu, key < worst);
-          if (__popc(bm) >= 6) {
-            // many candidates (a row's early tiles): sort them across the
-            // warp and merge with the sorted list; the element-wise minimum
-            // of the list and the reversed candidates holds the 32 smallest
-            // as a bitonic sequence, which five half-cleaners sort
-            uint64_t r = warp_sort_asc(key < worst ? key : kEmpty);
-            r = shfl64(r, 31 - lane);
-            const uint64_t l = lst[lane];
-            r = l < r ? l : r;
-#pragma unroll
-            for (int j = 16; j > 0; j >>= 1) {
-              const uint64_t o = shfl_xor64(r, j);
-              r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+          for (int j = 0; j < 32; ++j) srow[j] = v[j];
+          do {
+            const int j = __ffs(keep) - 1;
+            keep &= keep - 1;
+            const float dv = fmaxf(nrow + srow[j], 0.f);
+            const uint64_t key = pack(dv, (uint32_t)(c0 + j));
+            if (!isinf(dv) && key < root) {
+              tc::heap_replace(heap, key);
+              root = heap[1];
+              const float nthr = root == kEmpty ? kInf : key_dist(root);
+              // slightly permissive: rounding of the folded threshold must
+              // not drop a column the certified pool counts on
+              thr_adj = nthr - nrow + 1e-6f * (fabsf(nthr) + fabsf(nrow));
             }
-            __syncwarp();
-            lst[lane] = r;
-            __syncwarp();
-            worst = shfl64(r, 31);
-          } else {
-            while (bm) {
-              const int src = __ffs(bm) - 1;
-              bm &= bm - 1;
-              const uint64_t x = shfl64(key, src);
-              if (x < worst) {
-                tc::list_insert_smem(lst, x);
-                worst = lst[31];
-              }
-            }
-          }
-          const float nthr = worst == kEmpty ? kInf : key_dist(worst);
-          const float nrow_i = __shfl_sync(0xffffffffu, nrow, i);
-          // slightly permissive: rounding of the folded threshold must not
-          // drop a column the certified pool counts on
-          if (lane == i) thr_adj = nthr - nrow_i + 1e-6f * (fabsf(nthr) + fabsf(nrow_i));
+          } while (keep);
         }
         __syncwarp();
       }
@@ -400,10 +401,12 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0) atomicOr(err, 4);
       sm.abort = 1;
     }
-    // write this warp's 32 rows
-    for (int i = 0; i < 32; ++i) {
+    // this warp's 32 rows, each heap sorted ascending across the warp
+    __syncwarp();
+    for (int i = 0; i < 32 && mode != 3; ++i) {
       const int64_t gr = r0 + 32 * sub + i;
-      if (gr < s) out[gr * KP + lane] = sm.lists[32 * sub + i][lane];
+      const uint64_t x = warp_sort_asc(sm.heap[32 * sub + i][1 + lane]);
+      if (gr < s) out[gr * KP + lane] = x;
     }
   }
   tc::fence_before();
@@ -461,6 +464,8 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk,
 
 bool tc_tiles_supported(int32_t dpad, int32_t KPv) { return dpad <= BK * MAX_KC && KPv == KP; }
 
+static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory of one CTA");
+
 size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
 
 cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, int32_t dpad, int32_t mode,
@@ -477,7 +482,42 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (s + BM - 1) / BM;
-  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, norms, s, dk / BK, mode, out, err);
+  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, norms, norms, s, s, dk / BK, mode, out, nullptr,
+                                                   0, err);
+  return cudaGetLastError();
+}
+
+void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void* hi, void* lo, cudaStream_t st) {
+  k_split_bf16<<<152 * 8, 256, 0, st>>>(x, s, dpad, dk, static_cast<__nv_bfloat16*>(hi),
+                                        static_cast<__nv_bfloat16*>(lo));
+}
+
+bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk, void* maps) {
+  CUtensorMap* m = static_cast<CUtensorMap*>(maps);
+  return dk % BK == 0 && dk / BK <= MAX_KC && nb >= 1 && make_map(&m[0], b_hi, nb, dk, BN) &&
+         make_map(&m[1], b_lo, nb, dk, BN);
+}
+
+cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
+                                 const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
+                                 float* out_d, int64_t ldo, int32_t* err, cudaStream_t st) {
+  if (dk % BK != 0 || dk / BK > MAX_KC || na < 1 || nb < 1) return cudaErrorInvalidValue;
+  if (out_d && (ldo % 32 != 0 || ldo < nb)) return cudaErrorInvalidValue;
+  CUtensorMap mah, mal;
+  if (!make_map(&mah, a_hi, na, dk, BM) || !make_map(&mal, a_lo, na, dk, BM)) return cudaErrorInvalidValue;
+  const CUtensorMap& mbh = static_cast<const CUtensorMap*>(b_maps)[0];
+  const CUtensorMap& mbl = static_cast<const CUtensorMap*>(b_maps)[1];
+  static bool attr_set = false;  // the attribute outlives the call; set it once
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)tc_smem_bytes());
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  const size_t smem = tc_smem_bytes();
+  const int64_t nrb = (na + BM - 1) / BM;
+  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, a_norms, b_norms, na, nb, dk / BK,
+                                                   out_d ? 3 : 2, out, out_d, ldo, err);
   return cudaGetLastError();
 }
 

@@ -81,6 +81,12 @@ struct Chunk<float> {
     sqdiff2(v.x, v.y, qv.x, qv.y, a0, a1);
     sqdiff2(v.z, v.w, qv.z, qv.w, a0, a1);
   }
+  __device__ __forceinline__ static void to_float(const uint4& raw, float, float* out) {
+    out[0] = __uint_as_float(raw.x);
+    out[1] = __uint_as_float(raw.y);
+    out[2] = __uint_as_float(raw.z);
+    out[3] = __uint_as_float(raw.w);
+  }
 };
 
 template <>
@@ -94,6 +100,14 @@ struct Chunk<__nv_bfloat16> {
 #pragma unroll
     for (int i = 0; i < 4; ++i)
       sqdiff2(__uint_as_float(w[i] << 16), __uint_as_float(w[i] & 0xFFFF0000u), qq[2 * i], qq[2 * i + 1], a0, a1);
+  }
+  __device__ __forceinline__ static void to_float(const uint4& raw, float, float* out) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      out[2 * i] = __uint_as_float(w[i] << 16);
+      out[2 * i + 1] = __uint_as_float(w[i] & 0xFFFF0000u);
+    }
   }
 };
 
@@ -111,6 +125,20 @@ struct Chunk<__nv_fp8_e4m3> {
       float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&h1));
       sqdiff2(f0.x * scale, f0.y * scale, qv.x, qv.y, a0, a1);
       sqdiff2(f1.x * scale, f1.y * scale, qv.z, qv.w, a0, a1);
+    }
+  }
+  __device__ __forceinline__ static void to_float(const uint4& raw, float scale, float* out) {
+    const uint32_t w[4] = {raw.x, raw.y, raw.z, raw.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      __half2_raw h0 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] & 0xFFFF), __NV_E4M3);
+      __half2_raw h1 = __nv_cvt_fp8x2_to_halfraw2((__nv_fp8x2_storage_t)(w[i] >> 16), __NV_E4M3);
+      float2 f0 = __half22float2(*reinterpret_cast<__half2*>(&h0));
+      float2 f1 = __half22float2(*reinterpret_cast<__half2*>(&h1));
+      out[4 * i] = f0.x * scale;
+      out[4 * i + 1] = f0.y * scale;
+      out[4 * i + 2] = f1.x * scale;
+      out[4 * i + 3] = f1.y * scale;
     }
   }
 };
@@ -322,6 +350,69 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
   return nw;
 }
 
+// The exact candidate set of an upper layer for exact_method 1 / 2: the
+// keys (traversal distance, layer position) of its 32 nearest points,
+// ascending, one per lane (kEmpty past the layer's size).  Method 1 starts
+// from the query's 32 tile candidates, rescored here: a point outside them
+// has a tile distance >= thr (the 32nd candidate's), so a true distance >=
+// thr - beta, beta bounding the tile error for this query; if that exceeds
+// the need-th rescored distance (widened for its own rounding), no outside
+// point belongs to the first `need` keys.  Otherwise, and for method 2,
+// every point of the layer is evaluated into a running top 32 (warp
+// bitonic merge of each sorted batch of 32).
+template <typename VT, int G, int CPL>
+__device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const SearchLayer& Ly, int64_t stride, int nchunk,
+                                             const float* qs, const uint64_t* pre_row, float pre_qn, int need,
+                                             int& evals) {
+  const int lane = lane_id();
+  const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
+  const int s = (int)Ly.size;
+  if (pre_row && *a.pre_err == 0) {
+    const uint64_t tk = pre_row[lane];
+    const int cnt = __popc(__ballot_sync(0xffffffffu, tk != kEmpty));
+    const int32_t id = tk != kEmpty ? (int32_t)key_index(tk) : 0;
+    const float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, id, cnt, qs, nchunk);
+    evals += cnt;
+    const uint64_t mine = warp_sort_asc(lane < cnt ? pack(dn, (uint32_t)id) : kEmpty);
+    bool ok = cnt == s;  // the candidates are the whole layer
+    if (!ok && cnt == 32) {
+      const double thr = (double)key_dist(shfl64(tk, 31));
+      const double dw = (double)key_dist(shfl64(mine, need - 1));
+      // rounding of the rescored distances (FMA chains of <= dpad / 16
+      // steps per accumulator, pairing and butterfly), doubled
+      const double slack = (double)(a.dpad / 16 + 16) * 0x1p-23;
+      // points that can come within dw of the query lie within sqrt(dw)
+      // of it: their centred norm is capped by (|q| + sqrt(dw))^2
+      const double nr = (double)pre_qn;
+      const double rad = sqrt(nr) * (1.0 + 1e-3) + sqrt(dw * (1.0 + 2.0 * slack)) * (1.0 + 1e-3);
+      const double nc = fmin((double)*a.pre_nmax, rad * rad);
+      const double beta = a.pre_tile_u * 4.0 * (nr + nc) + 1e-30;
+      ok = thr - beta > dw * (1.0 + slack);
+    }
+    if (ok) return mine;
+    if (lane == 0 && a.pre_scans) atomicAdd(a.pre_scans, 1);
+  }
+  uint64_t mine = kEmpty;
+  for (int c0 = 0; c0 < s; c0 += 32) {
+    const int cnt = min(32, s - c0);
+    const float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, c0 + lane, cnt, qs, nchunk);
+    uint64_t kk = lane < cnt ? pack(dn, (uint32_t)(c0 + lane)) : kEmpty;
+    if (!__any_sync(0xffffffffu, kk < shfl64(mine, 31))) continue;
+    // the running list and the reversed sorted batch: their element-wise
+    // minimum holds the 32 smallest as a bitonic sequence
+    kk = shfl64(warp_sort_asc(kk), 31 - lane);
+    uint64_t r = mine < kk ? mine : kk;
+#pragma unroll
+    for (int j = 16; j > 0; j >>= 1) {
+      const uint64_t o = shfl_xor64(r, j);
+      r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+    }
+    mine = r;
+  }
+  evals += s;
+  return mine;
+}
+
 // ------------------------------------------------------- the kernel
 
 // G lanes per row (8 for rows of <= 32 chunks of 16 bytes, else 32) and
@@ -405,7 +496,8 @@ __device__ __noinline__ void finish_query(const SearchArgs& a, uint64_t* W, int 
 // `my` is this warp's shared-memory slice.
 template <typename VT, int DMAX>
 __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my, const float* __restrict__ qg, int k,
-                                          int ef, uint64_t key, int64_t* out_ids, float* out_d, int32_t* stats) {
+                                          int ef, uint64_t key, int64_t* out_ids, float* out_d, int32_t* stats,
+                                          const uint64_t* pre_row = nullptr, float pre_qn = 0.f) {
   constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
   constexpr int G32 = RowShape<float, DMAX>::G, CPL32 = RowShape<float, DMAX>::CPL;
   const int lane = lane_id();
@@ -444,7 +536,25 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
   int32_t cur = (int32_t)bounded(derive(a.entry_key, key), (uint64_t)a.layers[a.L].size);
   // S2: upper layers: GreedySearch of Alg. 4, or a beam of width ef_upper
   int nseed = 0;
-  for (int li = a.L; li >= 1; --li) {
+  // the lowest exact layer's set does not depend on the layers above it:
+  // the walk starts there (exact_method 1 / 2 first, so that nothing of it
+  // stays live across the beams)
+  int li = a.top_exact;
+  if (a.exact_method != 0) {
+    const SearchLayer Ly = a.layers[li];
+    const int width = (li == 1 && a.ef_l1 > 0) ? a.ef_l1 : a.ef_upper;
+    // the host keeps width <= 32 when the candidates seed the next layer
+    const bool seeds = a.descend_all && width > 1;
+    const int nw = seeds ? min(min(width, 32), (int)Ly.size) : 1;
+    const uint64_t mine =
+        exact_top32<VT, G, CPL>(a, Ly, stride, nchunk, qs, a.exact_method == 1 ? pre_row : nullptr, pre_qn, nw, evals);
+    if (lane < nw) W[lane] = seeds ? ((mine & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(mine)]) : mine;
+    cur = Ly.down[key_index(shfl64(mine, 0))];
+    if (seeds) nseed = nw;
+    __syncwarp();
+    --li;
+  }
+  for (; li >= 1; --li) {
     const SearchLayer Ly = a.layers[li];
     const int width = (li == 1 && a.ef_l1 > 0) ? a.ef_l1 : a.ef_upper;
     if (Ly.size <= a.exact_upper) {
@@ -560,7 +670,8 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const Se
     const int ef = a.efq ? a.efq[qi] : a.ef_uniform;
     const uint64_t key = a.keys ? a.keys[qi] : (uint64_t)qi;
     run_query<VT, DMAX>(a, my, a.Q + qi * a.d, k, ef, key, a.out_ids + qi * a.out_stride,
-                        a.out_d + qi * a.out_stride, a.stats ? a.stats + qi * 4 : nullptr);
+                        a.out_d + qi * a.out_stride, a.stats ? a.stats + qi * 4 : nullptr,
+                        a.pre_keys ? a.pre_keys + qi * 32 : nullptr, a.pre_qnorm ? a.pre_qnorm[qi] : 0.f);
   }
 }
 
@@ -728,6 +839,151 @@ cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStrea
   if (storage == HENN_BF16) return launch_probe_vt<__nv_bfloat16>(a, st);
   if (storage == HENN_FP8E4M3) return launch_probe_vt<__nv_fp8_e4m3>(a, st);
   return launch_probe_vt<float>(a, st);
+}
+
+// ------------------------------------------- exact-layer preparation
+
+template <typename VT>
+__global__ void k_layer_rows_f32(const VT* __restrict__ vec, const float* __restrict__ scale, int64_t s, int32_t dpad,
+                                 float* __restrict__ out) {
+  constexpr int E = Chunk<VT>::kElems;
+  const int nchunk = dpad / E;
+  const int64_t total = s * nchunk;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = i / nchunk;
+    const int c = (int)(i - r * nchunk);
+    const uint4 raw = reinterpret_cast<const uint4*>(vec + r * dpad)[c];
+    float v[E];
+    Chunk<VT>::to_float(raw, scale ? scale[r] : 1.f, v);
+#pragma unroll
+    for (int e = 0; e < E; ++e) out[r * dpad + c * E + e] = v[e];
+  }
+}
+
+cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s, int storage, int32_t dpad, float* out,
+                                  cudaStream_t st) {
+  if (storage == HENN_BF16)
+    k_layer_rows_f32<__nv_bfloat16><<<152 * 8, 256, 0, st>>>(static_cast<const __nv_bfloat16*>(vec), scale, s, dpad,
+                                                             out);
+  else if (storage == HENN_FP8E4M3)
+    k_layer_rows_f32<__nv_fp8_e4m3><<<152 * 8, 256, 0, st>>>(static_cast<const __nv_fp8_e4m3*>(vec), scale, s, dpad,
+                                                             out);
+  else
+    k_layer_rows_f32<float><<<152 * 8, 256, 0, st>>>(static_cast<const float*>(vec), scale, s, dpad, out);
+  return cudaGetLastError();
+}
+
+// One warp per query: the row exactly as run_query stages it (the angular
+// normalisation in the same order), minus the layer's centre.
+__global__ void k_entry_queries(const float* __restrict__ Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric,
+                                const float* __restrict__ mean, float* __restrict__ xo, __nv_bfloat16* __restrict__ hi,
+                                __nv_bfloat16* __restrict__ lo, int32_t dk, float* __restrict__ norms) {
+  const int lane = threadIdx.x & 31;
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const float* qg = Q + q * d;
+    float inv = 1.f;
+    if (metric == HENN_ANGULAR) {
+      float ss = 0.f;
+      for (int c = lane; c < dpad; c += 32) {
+        const float v = c < d ? qg[c] : 0.f;
+        ss = fmaf(v, v, ss);
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) ss += __shfl_xor_sync(0xffffffffu, ss, o);
+      inv = ss > 0.f ? __fdiv_rn(1.f, __fsqrt_rn(ss)) : 0.f;
+    }
+    float acc = 0.f;
+    for (int c = lane; c < dk; c += 32) {
+      float v = 0.f;
+      if (c < dpad) {
+        float x = c < d ? qg[c] : 0.f;
+        if (metric == HENN_ANGULAR) x *= inv;
+        v = x - mean[c];
+        acc = fmaf(v, v, acc);
+        if (xo) xo[q * dpad + c] = v;
+      }
+      if (hi) {
+        const __nv_bfloat16 h = __float2bfloat16_rn(v);
+        hi[q * dk + c] = h;
+        lo[q * dk + c] = __float2bfloat16_rn(v - __bfloat162float(h));
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) norms[q] = acc;
+  }
+}
+
+void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric, const float* mean,
+                          float* xo, void* hi, void* lo, int32_t dk, float* norms, cudaStream_t st) {
+  int64_t blocks = (nq + 7) / 8;
+  if (blocks > 152 * 16) blocks = 152 * 16;
+  if (blocks < 1) blocks = 1;
+  k_entry_queries<<<(int)blocks, 256, 0, st>>>(Q, nq, d, dpad, metric, mean, xo, static_cast<__nv_bfloat16*>(hi),
+                                               static_cast<__nv_bfloat16*>(lo), hi ? dk : dpad, norms);
+}
+
+// One warp per query: the 32 smallest (distance, column) keys of its row of
+// a tile distance matrix (+inf entries never enter), ascending, one per
+// lane.  Each lane reads 4 columns per step (the next step's load in
+// flight); each of the 4 batches of 32 columns is merged into the running
+// list: a few passing keys by shuffle insertion, many by sorting the batch
+// and a bitonic merge.
+__global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t s, int64_t ldo,
+                               uint64_t* __restrict__ out) {
+  const int lane = threadIdx.x & 31;
+  const float kInf = __int_as_float(0x7f800000);
+  for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
+       q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
+    const float* row = D + q * ldo;
+    uint64_t mine = kEmpty, worst = kEmpty;
+    float4 nxt = 4 * lane < ldo ? __ldcs(reinterpret_cast<const float4*>(row) + lane) : make_float4(kInf, kInf, kInf, kInf);
+    for (int64_t c0 = 0; c0 < s; c0 += 128) {
+      const float4 cur = nxt;
+      const int64_t cn = c0 + 128 + 4 * lane;
+      nxt = cn < ldo ? __ldcs(reinterpret_cast<const float4*>(row + cn)) : make_float4(kInf, kInf, kInf, kInf);
+      const float dvs[4] = {cur.x, cur.y, cur.z, cur.w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float dv = dvs[e];
+        uint64_t kk = isinf(dv) ? kEmpty : pack(dv, (uint32_t)(c0 + 4 * lane + e));
+        unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
+        if (!bm) continue;
+        if (__popc(bm) > 6) {
+          kk = shfl64(warp_sort_asc(kk), 31 - lane);
+          uint64_t r = mine < kk ? mine : kk;
+#pragma unroll
+          for (int j = 16; j > 0; j >>= 1) {
+            const uint64_t o = shfl_xor64(r, j);
+            r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+          }
+          mine = r;
+        } else {
+          do {
+            const int src = __ffs(bm) - 1;
+            bm &= bm - 1;
+            const uint64_t x = shfl64(kk, src);
+            if (x < worst) {
+              const int pos = __popc(__ballot_sync(0xffffffffu, mine < x));
+              const uint64_t up = shfl64(mine, lane > 0 ? lane - 1 : 0);
+              mine = lane < pos ? mine : (lane == pos ? x : up);
+              worst = shfl64(mine, 31);
+            }
+          } while (bm);
+        }
+        worst = shfl64(mine, 31);
+      }
+    }
+    out[q * 32 + lane] = mine;
+  }
+}
+
+void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, cudaStream_t st) {
+  int64_t blocks = (nq + 7) / 8;
+  if (blocks > 152 * 64) blocks = 152 * 64;
+  if (blocks < 1) blocks = 1;
+  k_select_top32<<<(int)blocks, 256, 0, st>>>(D, nq, s, ldo, out);
 }
 
 // ------------------------------------------------------------ dispatch

@@ -34,6 +34,14 @@ struct SearchArgs {
   int32_t descend_all;        // enter each layer at all candidates of the layer above
   int32_t ef_l1;              // beam width on layer 1 (0: ef_upper)
   int32_t exact_upper;        // upper layers of at most this many points: exact candidate set
+  int32_t top_exact;          // the lowest such layer (the layers above it are skipped), else L
+  int32_t exact_method;       // its set by: 0 sort in the visited table, 1 tile candidates, 2 scan
+  const uint64_t* pre_keys;   // method 1: nq x 32 tile keys (distance, layer position), ascending
+  const float* pre_qnorm;     // method 1: squared norm of each centred query
+  const float* pre_nmax;      // method 1: largest squared norm of the layer's centred points
+  const int32_t* pre_err;     // method 1: tile error flags (nonzero: every query scans)
+  int32_t* pre_scans;         // method 1: queries whose certificate failed (nullable)
+  double pre_tile_u;          // method 1: unit error of the tile distances
   int32_t ef_cap, hash_bits;  // beam capacity and log2 visited slots per warp
   const uint64_t* keys;
   uint64_t entry_key;  // derive(seed, ENTR)
@@ -82,6 +90,18 @@ struct GreedyProbeArgs {
 };
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+// Exact-layer preparation for exact_method 1 (tile candidates).
+// Layer rows in traversal precision, as FP32 (dequantised BF16 / FP8 codes).
+cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s, int storage, int32_t dpad, float* out,
+                                  cudaStream_t st);
+// Queries as the search kernel sees them (angular: normalised the same
+// way), minus `mean`: squared norms, and FP32 rows (xo, dpad wide) and / or
+// split BF16 planes (hi, lo, dk wide), each output nullable.
+void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric, const float* mean,
+                          float* xo, void* hi, void* lo, int32_t dk, float* norms, cudaStream_t st);
+// Per query, the 32 smallest keys of its row of a distance matrix (nq rows
+// of ldo floats, s columns): the tile candidates of exact_method 1.
+void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, cudaStream_t st);
 cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStream_t st);
 cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st);
