@@ -4,9 +4,12 @@ batched BF16 traversal + exact FP32 rerank vs plain FP32; build seconds.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
-One step = one persistent search launch over the whole 10,000-query batch
-with the index resident in HBM.  The beam configuration (ef, ef_upper) is
-the cheapest one of a small sweep whose recall@10 against exact ground
+One step = one henn_search call over the whole 10,000-query batch with the
+index resident in HBM: one persistent search launch, preceded, when the
+lowest exact upper layer comes from distance tiles (exact_method TILES), by
+the query preparation, tile and top-32 selection launches.  The beam
+configuration (ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method)
+is the cheapest one of a small sweep whose recall@10 against exact ground
 truth (computed on the device by henn_exact_knn) is >= 0.95.  Under
 torchrun every rank holds its own index replica and its own query batch
 (weak scaling, no collective on the data path); rank 0 prints one JSON
@@ -36,14 +39,18 @@ import synth  # noqa: E402
 
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
-EF_SWEEP = [16, 24, 32, 40, 48, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
-# (ef_upper, descend_all, ef_l1, exact_upper): beam width on the upper layers, whether
-# each layer is entered at all candidates of the layer above, and the beam
-# width on layer 1 (0 = ef_upper)
-UPPER_SWEEP = [(1, 0, 0, 0), (32, 0, 0, 0), (48, 0, 0, 0), (48, 1, 0, 0), (56, 0, 0, 0), (64, 0, 0, 0),
-               (64, 1, 0, 0), (64, 0, 16, 0), (64, 0, 32, 0), (80, 0, 16, 0), (96, 0, 16, 0), (128, 0, 16, 0),
-               (128, 1, 16, 0),
-               (32, 0, 0, 256), (48, 1, 0, 256), (64, 0, 0, 256), (64, 1, 0, 256), (64, 0, 16, 256)]
+EF_SWEEP = [16, 24, 32, 36, 40, 44, 48, 52, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
+# (ef_upper, descend_all, ef_l1, exact_upper, exact_method): beam width on the
+# upper layers, whether each layer is entered at all candidates of the layer
+# above, the beam width on layer 1 (0 = ef_upper), the size up to which an
+# upper layer gives its exact candidate set ("L<i>": the size of layer i of
+# the index at hand) and how that set is found (0 SORT, 1 TILES)
+UPPER_SWEEP = [(1, 0, 0, 0, 0), (32, 0, 0, 0, 0), (48, 0, 0, 0, 0), (48, 1, 0, 0, 0), (56, 0, 0, 0, 0),
+               (64, 0, 0, 0, 0), (64, 1, 0, 0, 0), (64, 0, 16, 0, 0), (64, 0, 32, 0, 0), (80, 0, 16, 0, 0),
+               (96, 0, 16, 0, 0), (128, 0, 16, 0, 0), (128, 1, 16, 0, 0),
+               (32, 0, 0, 256, 0), (48, 1, 0, 256, 0), (64, 0, 0, 256, 0), (64, 1, 0, 256, 0), (64, 0, 16, 256, 0),
+               (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1), (24, 1, 0, "L2", 1), (16, 0, 0, "L2", 1),
+               (32, 0, 0, "L2", 1), (64, 0, 0, "L2", 1), (1, 0, 0, "L1", 1)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -162,8 +169,13 @@ def _recall(found, gt):
     return float(np.mean(hits)) / gt.shape[1]
 
 
-def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0, shape=None):
-    shape = shape or {}
+def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0, shape=None,
+                  kernel_ms=None):
+    """Step times (s) of `steps` calls after `warmup`; with a list in
+    kernel_ms, also the device time of each call's search launches."""
+    shape = dict(shape or {})
+    if kernel_ms is not None:
+        shape["time_kernel"] = True
     import torch
 
     H = sys.modules["paper_2505_17368_gb300"]
@@ -186,6 +198,8 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
+        if kernel_ms is not None:
+            kernel_ms.append(index.last_search_ms())
     return times, ids
 
 
@@ -274,44 +288,65 @@ def run_ours(args):
     # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
     def sweep(index, tag):
         best = None
-        for efu, da, l1, xu in UPPER_SWEEP:
+        sizes = index.info()["sizes"]
+        for efu, da, l1, xu, xm in UPPER_SWEEP:
+            if isinstance(xu, str):
+                li = int(xu[1:])
+                if li >= len(sizes):
+                    continue
+                xu = sizes[li]
             for ef in EF_SWEEP:
                 t, ids = _timed_search(index, Qd, ef, efu, 4, 1, None, stream, descend_all=da, ef_l1=l1,
-                                       shape={"exact_upper": xu})
+                                       shape={"exact_upper": xu, "exact_method": xm})
                 r = _recall(ids.cpu().numpy(), gt)
-                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} exact_upper={xu} ef={ef} "
-                      f"recall@10={r:.4f} ms={1e3 * min(t):.3f}", file=sys.stderr, flush=True)
+                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} exact_upper={xu} "
+                      f"exact_method={xm} ef={ef} recall@10={r:.4f} ms={1e3 * min(t):.3f}", file=sys.stderr,
+                      flush=True)
                 if r >= RECALL_TARGET:
                     # a later configuration must be clearly faster to replace an earlier one
-                    if best is None or min(t) < 0.98 * best[5]:
-                        best = (ef, efu, da, l1, xu, min(t), r)
+                    if best is None or min(t) < 0.98 * best[6]:
+                        best = (ef, efu, da, l1, xu, xm, min(t), r)
                     break
         return best
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
-    chosen = sweep(idx_bf16, "bf16")
-    plain = sweep(idx_f32, "f32")
+    if args.beam:
+        f = args.beam.split(",")
+        b_xu = info["sizes"][int(f[4][1:])] if f[4].startswith("L") else int(f[4])
+        beam = (int(f[0]), int(f[1]), int(f[2]), int(f[3]), b_xu, int(f[5]))
+        picked = []
+        for index in (idx_bf16, idx_f32):
+            t, ids = _timed_search(index, Qd, beam[0], beam[1], 4, 1, None, stream, descend_all=beam[2],
+                                   ef_l1=beam[3], shape={"exact_upper": beam[4], "exact_method": beam[5]})
+            picked.append(beam + (min(t), _recall(ids.cpu().numpy(), gt)))
+        chosen, plain = picked
+    else:
+        chosen = sweep(idx_bf16, "bf16")
+        plain = sweep(idx_f32, "f32")
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, da, l1, xu, _, rec = chosen
+    ef, efu, da, l1, xu, xm, _, rec = chosen
     # ---- launch shape (warps per block, visited-table size) by the autotuner
     from paper_2505_17368_gb300 import autotune
 
     shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
-                          use_cache=False)
-    shape = dict(shape, exact_upper=xu)
+                          exact_method=xm, use_cache=False)
+    shape = dict(shape, exact_upper=xu, exact_method=xm)
     # ---- algorithmic bytes per launch from the kernel's own counters
     _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
     R = min(4 * K, ef)
     alg_bytes = int(st[:, 0].sum() * row_bf16 + st[:, 1].sum() * 128 + args.nq * (R * 128 * 4 + 128 * 4 + K * 12))
+    if xm == 1 and xu > 0:
+        alg_bytes += args.nq * (32 * 8 + 4)  # each query's tile candidates and centred norm
     # ---- timed region
     if ws > 1:
         torch.distributed.barrier()
     torch.cuda.synchronize()
+    kern = []
     with ClockSampler(_smi_id(dev, local)) as clk:
         times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da,
-                                   ef_l1=l1, shape=shape)
+                                   ef_l1=l1, shape=shape, kernel_ms=kern)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -320,9 +355,9 @@ def run_ours(args):
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
     # plain FP32 comparator, same procedure
-    p_ef, p_efu, p_da, p_l1, p_xu, _, p_rec = plain
+    p_ef, p_efu, p_da, p_l1, p_xu, p_xm, _, p_rec = plain
     p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da,
-                               ef_l1=p_l1, shape={"exact_upper": p_xu})
+                               ef_l1=p_l1, shape={"exact_upper": p_xu, "exact_method": p_xm})
     plain_qps = args.nq / statistics.median(p_times)
     # one launch per query, FP32 (latency form), on a sample
     ns = min(200, args.nq)
@@ -331,7 +366,7 @@ def run_ours(args):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, ef_l1=p_l1, exact_upper=p_xu,
-                       stream=stream)
+                       exact_method=p_xm, stream=stream)
         e1.record(stream)
         e1.synchronize()
         t_one.append(e0.elapsed_time(e1) / 1e3)
@@ -346,20 +381,22 @@ def run_ours(args):
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
     peaks, src = _peaks()
-    avg = statistics.mean(times)
-    achieved = alg_bytes / avg / 1e9
-    traffic = _profile_traffic((ef, efu, da, l1, xu))
+    # the search kernel's own device time (events around its launch), not the step's
+    k_avg = statistics.mean(ms for ms, _ in kern) / 1e3
+    launches_per_step = kern[-1][1]
+    achieved = alg_bytes / k_avg / 1e9
+    traffic = _profile_traffic((ef, efu, da, l1, xu, xm))
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
-            "descend_all": da, "ef_l1": l1, "exact_upper": xu, "launch_shape": shape,
+            "descend_all": da, "ef_l1": l1, "exact_upper": xu, "exact_method": xm, "launch_shape": shape,
             "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
             "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
-                          "exact_upper": p_xu,
+                          "exact_upper": p_xu, "exact_method": p_xm,
                           "recall_at_10": p_rec},
             "plain_f32_per_query_launch_qps": per_query_qps,
             "step_ms_median": 1e3 * statistics.median(times), "step_ms_max": 1e3 * max(times),
@@ -370,16 +407,17 @@ def run_ours(args):
         "build_roofline": _build_roofline(info),
         "roofline": {"bound": "hbm", "achieved": achieved, "peak": peaks["hbm_gbs"], "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "frac_nominal": achieved / NOMINAL_HBM_GBS,
-                     "traffic": traffic, "peak_source": src,
+                     "traffic": traffic, "peak_source": src, "kernel_ms": 1e3 * k_avg,
                      "algorithmic_bytes_per_launch": alg_bytes, "kernel": "k_search<bf16>"},
         "e2e": {"value": e2e_units / e2e_tmax, "unit": "queries/s",
                 "h2d_bytes_per_step": int(args.nq * 128 * 4), "d2h_bytes_per_step": int(args.nq * K * 12)},
-        "gpu_launches": args.steps,
+        "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
         qps, cores, secs, (qps_all, ncores) = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq, l1=l1, da=da,
                                                                 xu=xu)
+        # (the oracle computes every exact layer by its definition; exact_method is the GPU's choice of how)
         sample = (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
                   f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, ef_l1={l1}, descend_all={da}, exact_upper={xu}")
         line["cpu_baseline"] = {
@@ -419,8 +457,8 @@ def _build_roofline(info):
 def _profile_traffic(beam):
     """DRAM bytes per launch of the search kernel from the committed ncu
     summary, if it was taken on the current kernel source with the same
-    beam configuration (ef, ef_upper, descend_all, ef_l1, exact_upper);
-    else None."""
+    beam configuration (ef, ef_upper, descend_all, ef_l1, exact_upper,
+    exact_method); else None."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "search_bf16_mixture-1m-d128.md")
@@ -432,7 +470,7 @@ def _profile_traffic(beam):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].rsplit(":", 1)  # keys may hold a colon ("sha256[:16]")
                 kv[k.strip()] = v.strip().strip("`")
-        want = "ef={} ef_upper={} descend_all={} ef_l1={} exact_upper={}".format(*beam)
+        want = "ef={} ef_upper={} descend_all={} ef_l1={} exact_upper={} exact_method={}".format(*beam)
         if kv.get("search.cu sha256[:16]") == sha:
             return float(kv[f"dram bytes per launch [{want}]"])
     except (OSError, KeyError, ValueError):
@@ -455,6 +493,9 @@ def main():
     ap.add_argument("--ref-ef", type=int, default=64)
     ap.add_argument("--ref-ef-upper", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--beam", default=None,
+                    help="ef,ef_upper,descend_all,ef_l1,exact_upper,exact_method: skip the sweep and use this "
+                         "beam for both forms (exact_upper may be L<i>, the size of layer i)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

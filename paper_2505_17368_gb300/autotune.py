@@ -37,22 +37,24 @@ def _default_hash_bits(cap):
     return hb
 
 
-def candidates(k, ef, ef_upper=1, ef_l1=0, exact_upper=0):
-    """Shapes to try; exact_upper > 0 needs 2^(hash_bits - 1) >= exact_upper
-    (the exact layers' keys use the visited table's space)."""
+def candidates(k, ef, ef_upper=1, ef_l1=0, exact_upper=0, exact_method=0):
+    """Shapes to try; exact_upper > 0 with exact_method 0 (SORT) needs
+    2^(hash_bits - 1) >= exact_upper (the exact layer's keys use the visited
+    table's space)."""
     hb = _default_hash_bits(_beam_cap(k, ef, ef_upper, ef_l1))
+    need = exact_upper if exact_method == 0 else 0
     out = []
     for w in (4, 2):
         for h in (hb - 2, hb - 1, hb, hb + 1):
-            if 8 <= h <= 15 and (1 << (h - 1)) >= exact_upper:
+            if 8 <= h <= 15 and (1 << (h - 1)) >= need:
                 out.append({"warps_per_block": w, "hash_bits": h})
     return out
 
 
-def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all, exact_upper=0):
+def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all, exact_upper=0, exact_method=0):
     bucket = 1 << max(0, int(math.ceil(math.log2(max(nq, 1)))))
     return (f"n={index.n},d={index.d},s={index.storage},b={bucket},k={k},ef={ef},eu={ef_upper},l1={ef_l1},"
-            f"da={descend_all},xu={exact_upper}")
+            f"da={descend_all},xu={exact_upper},xm={exact_method}")
 
 
 def _load(path):
@@ -63,11 +65,11 @@ def _load(path):
         return {}
 
 
-def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper=0):
+def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper=0, exact_method=0):
     import torch
 
     def run(shape):
-        shape = dict(shape, exact_upper=exact_upper)
+        shape = dict(shape, exact_upper=exact_upper, exact_method=exact_method)
         index.search(Q, k=k, ef=ef, ef_upper=ef_upper, ef_l1=ef_l1, descend_all=descend_all, **shape)
         torch.cuda.synchronize()
         ts = []
@@ -84,17 +86,17 @@ def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_up
 
 
 def tune(index, Q, k=10, ef=64, ef_upper=1, ef_l1=0, descend_all=0, repeats=3, cache_path=DEFAULT_CACHE,
-         use_cache=True, timer=None, exact_upper=0):
+         use_cache=True, timer=None, exact_upper=0, exact_method=0):
     """Fastest launch shape for this (index, batch, beam); Q is a CUDA
     tensor.  `timer(shape) -> ms` replaces the CUDA-event timing (tests)."""
-    key = _key(index, Q.shape[0], k, ef, ef_upper, ef_l1, descend_all, exact_upper)
+    key = _key(index, Q.shape[0], k, ef, ef_upper, ef_l1, descend_all, exact_upper, exact_method)
     with _LOCK:
         cache = _load(cache_path) if use_cache else {}
         if key in cache:
             return dict(cache[key]["shape"])
-    run = timer or _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper)
+    run = timer or _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper, exact_method)
     best, best_t, table = None, float("inf"), []
-    for shape in candidates(k, ef, ef_upper, ef_l1, exact_upper):
+    for shape in candidates(k, ef, ef_upper, ef_l1, exact_upper, exact_method):
         t = run(shape)
         table.append((shape, t))
         if t < best_t:

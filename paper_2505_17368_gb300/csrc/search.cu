@@ -926,28 +926,42 @@ void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, i
 
 // One warp per query: the 32 smallest (distance, column) keys of its row of
 // a tile distance matrix (+inf entries never enter), ascending, one per
-// lane.  Each lane reads 4 columns per step (the next step's load in
-// flight); each of the 4 batches of 32 columns is merged into the running
-// list: a few passing keys by shuffle insertion, many by sorting the batch
-// and a bitonic merge.
+// lane.  Pass 1: each lane's minimum over its own columns (4 per 128-column
+// step); the largest of the 32 minima, T, is >= the row's 32nd smallest
+// value (32 distinct columns lie at or below it).  Pass 2 (the row again,
+// now mostly from L2) merges only entries <= T into the running list: a few
+// passing keys by shuffle insertion, many by sorting the batch and a
+// bitonic merge.
 __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t s, int64_t ldo,
                                uint64_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
+  const float4 kInf4 = make_float4(kInf, kInf, kInf, kInf);
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const float* row = D + q * ldo;
+    const float4* row = reinterpret_cast<const float4*>(D + q * ldo);
+    const int64_t n4 = ldo / 4;  // float4 per row
+    float m = kInf;
+    for (int64_t i = lane; i < n4; i += 32) {
+      const float4 v = __ldg(row + i);
+      m = fminf(m, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    const float T = m;
     uint64_t mine = kEmpty, worst = kEmpty;
-    float4 nxt = 4 * lane < ldo ? __ldcs(reinterpret_cast<const float4*>(row) + lane) : make_float4(kInf, kInf, kInf, kInf);
-    for (int64_t c0 = 0; c0 < s; c0 += 128) {
+    float4 nxt = lane < n4 ? __ldcs(row + lane) : kInf4;
+    for (int64_t i0 = 0; i0 < n4; i0 += 32) {
       const float4 cur = nxt;
-      const int64_t cn = c0 + 128 + 4 * lane;
-      nxt = cn < ldo ? __ldcs(reinterpret_cast<const float4*>(row + cn)) : make_float4(kInf, kInf, kInf, kInf);
+      nxt = i0 + 32 + lane < n4 ? __ldcs(row + i0 + 32 + lane) : kInf4;
+      const bool any4 = cur.x <= T || cur.y <= T || cur.z <= T || cur.w <= T;
+      if (!__any_sync(0xffffffffu, any4)) continue;
       const float dvs[4] = {cur.x, cur.y, cur.z, cur.w};
+      const int64_t cbase = 4 * (i0 + lane);
 #pragma unroll
       for (int e = 0; e < 4; ++e) {
         const float dv = dvs[e];
-        uint64_t kk = isinf(dv) ? kEmpty : pack(dv, (uint32_t)(c0 + 4 * lane + e));
+        uint64_t kk = (dv <= T && !isinf(dv)) ? pack(dv, (uint32_t)(cbase + e)) : kEmpty;
         unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
         if (!bm) continue;
         if (__popc(bm) > 6) {

@@ -18,6 +18,12 @@ def test_candidates_follow_the_beam():
     assert all(8 <= s["hash_bits"] <= 15 for s in c)
     big = autotune.candidates(10, 512, ef_upper=64)
     assert max(s["hash_bits"] for s in big) > max(s["hash_bits"] for s in c)
+    # the visited-table sort (exact_method 0) needs 2^(hash_bits - 1) slots
+    # per exact-layer point; tiles and scans use none of them
+    sort = autotune.candidates(10, 64, exact_upper=1000, exact_method=0)
+    assert sort and all((1 << (s["hash_bits"] - 1)) >= 1000 for s in sort)
+    assert autotune.candidates(10, 64, exact_upper=4000, exact_method=1) == c
+    assert autotune.candidates(10, 64, exact_upper=100000, exact_method=0) == []
 
 
 def test_tune_picks_fastest_and_caches(tmp_path):
