@@ -28,6 +28,9 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <cstddef>
+#include <cstring>
+
 #include "common.cuh"
 #include "kernels.cuh"
 
@@ -94,6 +97,25 @@ __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volati
     if ((i & 63) == 63 && *abort_flag) return false;
   }
   return false;
+}
+
+// Bulk tensor store of a shared-memory box to global memory (bulk group
+// of the issuing thread), and the waits on this thread's bulk groups.
+__device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void* src, int x, int y) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.bulk_group [%0, {%2, %3}], [%1];" ::"l"(
+                   reinterpret_cast<uint64_t>(map)),
+               "r"(smem_u32(src)), "r"(x), "r"(y)
+               : "memory");
+  asm volatile("cp.async.bulk.commit_group;" ::: "memory");
+}
+__device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
+
+// max(x, 0) that keeps a NaN (max.NaN)
+__device__ __forceinline__ float max_nan0(float x) {
+  float r;
+  asm("max.NaN.f32 %0, %1, 0f00000000;" : "=f"(r) : "f"(x));
+  return r;
 }
 
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
@@ -175,6 +197,7 @@ using namespace tc;
 __global__ void __launch_bounds__(192, 1)
     k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
+                   const __grid_constant__ CUtensorMap to_d,
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
                    int32_t* __restrict__ err) {
@@ -302,7 +325,17 @@ __global__ void __launch_bounds__(192, 1)
     float thr_adj = kInf;
     uint64_t* heap = sm.heap[row_l];
     uint64_t root = kEmpty;
+    // mode 3 keeps no lists: the heap space holds each warp's two 4 KB
+    // store boxes (1024-byte aligned)
+    float* m3_stage = reinterpret_cast<float*>(&sm.heap[0][0]) + ew * 2048;
+    int m3_buf = 0;
     bool ok = true;
+    float pn[BN / 32];  // column norms of the next tile, one per lane and chunk
+#pragma unroll
+    for (int q = 0; q < BN / 32; ++q) {
+      const int64_t c = (int64_t)q * 32 + lane;
+      pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
+    }
     for (int t = 0; t < nt; ++t) {
       const int as = t & 1;
       const uint32_t aph = (uint32_t)((t >> 1) & 1);
@@ -311,12 +344,15 @@ __global__ void __launch_bounds__(192, 1)
         break;
       }
       tc::fence_after();
-      // this tile's column norms, staged once (read back as broadcasts)
+      // this tile's column norms, staged once (read back as broadcasts);
+      // the next tile's are loaded now and land while this one is drained
       float* ncs = sm.ncol[ew];
 #pragma unroll
+      for (int q = 0; q < BN / 32; ++q) ncs[q * 32 + lane] = pn[q];
+#pragma unroll
       for (int q = 0; q < BN / 32; ++q) {
-        const int64_t c = (int64_t)t * BN + q * 32 + lane;
-        ncs[q * 32 + lane] = c < sc ? __ldg(norms_c + c) : 0.f;
+        const int64_t c = (int64_t)(t + 1) * BN + q * 32 + lane;
+        pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
       }
       __syncwarp();
 #pragma unroll 1
@@ -325,6 +361,45 @@ __global__ void __launch_bounds__(192, 1)
         float v[32];
         tc::tmem_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN + q * 32), v);
         if (c0 >= cend) continue;  // warp-uniform
+        if (mode == 3) {
+          // the row's 32 distances, each formed as in the lists below
+          // (+inf past the last column; NaN kept, which no selection
+          // takes, as no list would), staged as this warp's 32 x 32 box in shared memory
+          // (128-byte rows, 16-byte chunks swizzled by row, as the tensor
+          // map's 128B swizzle expects) and written by one bulk tensor store
+          float* buf = m3_stage + m3_buf * 1024;
+          if (lane == 0) tc::bulk_wait_read_le1();  // the store that read buf two chunks ago
+          __syncwarp();
+          const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
+          float4* brow = reinterpret_cast<float4*>(buf + lane * 32);
+          if (c0 + 32 <= sc) {  // warp-uniform: every column of the chunk valid
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              const float4 nn = n4[j4];
+              brow[j4 ^ (lane & 7)] = make_float4(max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 0], nn.x)),
+                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 1], nn.y)),
+                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 2], nn.z)),
+                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 3], nn.w)));
+            }
+          } else {
+#pragma unroll
+            for (int j4 = 0; j4 < 8; ++j4) {
+              const float4 nn = n4[j4];
+              const float nc[4] = {nn.x, nn.y, nn.z, nn.w};
+              float o[4];
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                o[e] = c0 + 4 * j4 + e < sc ? max_nan0(nrow + fmaf(-2.f, v[4 * j4 + e], nc[e])) : kInf;
+              brow[j4 ^ (lane & 7)] = make_float4(o[0], o[1], o[2], o[3]);
+            }
+          }
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          __syncwarp();
+          if (lane == 0) tc::tma_store_2d(&to_d, buf, (int)c0, (int)(r0 + 32 * sub));
+          m3_buf ^= 1;
+          __syncwarp();
+          continue;
+        }
         // n_col - 2<a,b> for the 32 columns and their minimum: most chunks
         // end here, with no column under the row's threshold
         const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
@@ -337,25 +412,6 @@ __global__ void __launch_bounds__(192, 1)
           v[4 * j4 + 2] = fmaf(-2.f, v[4 * j4 + 2], nn.z);
           v[4 * j4 + 3] = fmaf(-2.f, v[4 * j4 + 3], nn.w);
           vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
-        }
-        if (mode == 3) {
-          // the row's 32 distances (+inf past the last column; NaN, which
-          // no list would take, as +inf too), one 128-byte run per lane
-          if (grow < s) {
-            float4* dst = reinterpret_cast<float4*>(out_d + grow * ldo + c0);
-#pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-              float o[4];
-#pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                const float dv = nrow + v[4 * j4 + e];
-                o[e] = (c0 + 4 * j4 + e < sc && dv == dv) ? fmaxf(dv, 0.f) : kInf;
-              }
-              __stcs(dst + j4, make_float4(o[0], o[1], o[2], o[3]));
-            }
-          }
-          __syncwarp();
-          continue;
         }
         const bool maybe = vmin <= thr_adj;
         if (!__any_sync(0xffffffffu, maybe)) continue;
@@ -401,6 +457,7 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0) atomicOr(err, 4);
       sm.abort = 1;
     }
+    if (mode == 3 && lane == 0) tc::bulk_wait_all();
     // this warp's 32 rows, each heap sorted ascending across the warp
     __syncwarp();
     for (int i = 0; i < 32 && mode != 3; ++i) {
@@ -449,6 +506,20 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
+// FP32 matrix of `rows` x ld, stored by 32 x 32 boxes (128B swizzle)
+static bool make_store_map(CUtensorMap* m, const void* base, int64_t rows, int64_t ld) {
+  auto fn = encode_fn();
+  if (!fn) return false;
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
+  cuuint32_t box[2] = {32, 32};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+                  CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                  CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS;
+}
+
 static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk, int box_rows) {
   auto fn = encode_fn();
   if (!fn) return false;
@@ -465,6 +536,8 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk,
 bool tc_tiles_supported(int32_t dpad, int32_t KPv) { return dpad <= BK * MAX_KC && KPv == KP; }
 
 static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(((Smem*)nullptr)->heap) >= 4 * 8192, "mode 3 store boxes fit in the heap space");
+static_assert(offsetof(Smem, heap) % 1024 == 0, "store boxes 1024-byte aligned");
 
 size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
 
@@ -482,8 +555,10 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (s + BM - 1) / BM;
-  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, norms, norms, s, s, dk / BK, mode, out, nullptr,
-                                                   0, err);
+  CUtensorMap none;  // no matrix output in modes 0 and 1
+  std::memset(&none, 0, sizeof(none));
+  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out,
+                                                   nullptr, 0, err);
   return cudaGetLastError();
 }
 
@@ -516,7 +591,10 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   }
   const size_t smem = tc_smem_bytes();
   const int64_t nrb = (na + BM - 1) / BM;
-  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, a_norms, b_norms, na, nb, dk / BK,
+  CUtensorMap mo;
+  std::memset(&mo, 0, sizeof(mo));
+  if (out_d && !make_store_map(&mo, out_d, na, ldo)) return cudaErrorInvalidValue;
+  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
                                                    out_d ? 3 : 2, out, out_d, ldo, err);
   return cudaGetLastError();
 }

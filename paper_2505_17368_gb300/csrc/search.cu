@@ -924,14 +924,29 @@ void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, i
                                                static_cast<__nv_bfloat16*>(lo), hi ? dk : dpad, norms);
 }
 
+// Bitonic sort of one float per lane across the warp, ascending.
+__device__ __forceinline__ float warp_sort_asc_f32(float v) {
+  const int lane = threadIdx.x & 31;
+#pragma unroll
+  for (int size = 2; size <= 32; size <<= 1)
+#pragma unroll
+    for (int stride = size >> 1; stride > 0; stride >>= 1) {
+      const float o = __shfl_xor_sync(0xffffffffu, v, stride);
+      const bool up = (lane & size) == 0;
+      const bool lower = (lane & stride) == 0;
+      v = (lower == up) ? fminf(v, o) : fmaxf(v, o);
+    }
+  return v;
+}
+
 // One warp per query: the 32 smallest (distance, column) keys of its row of
 // a tile distance matrix (+inf entries never enter), ascending, one per
-// lane.  Pass 1: each lane's minimum over its own columns (4 per 128-column
-// step); the largest of the 32 minima, T, is >= the row's 32nd smallest
-// value (32 distinct columns lie at or below it).  Pass 2 (the row again,
-// now mostly from L2) merges only entries <= T into the running list: a few
-// passing keys by shuffle insertion, many by sorting the batch and a
-// bitonic merge.
+// lane.  Pass 1: each lane's two smallest values over its own columns (4
+// per 128-column step); the 32nd smallest of those 64, T, is >= the row's
+// 32nd smallest value (32 distinct columns lie at or below it).  Pass 2 (the
+// row again, now mostly from L2) merges only entries <= T into the running
+// list: a few passing keys by shuffle insertion, many by sorting the batch
+// and a bitonic merge.
 __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t s, int64_t ldo,
                                uint64_t* __restrict__ out) {
   const int lane = threadIdx.x & 31;
@@ -941,14 +956,26 @@ __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t 
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float4* row = reinterpret_cast<const float4*>(D + q * ldo);
     const int64_t n4 = ldo / 4;  // float4 per row
-    float m = kInf;
+    float m1 = kInf, m2 = kInf;  // this lane's two smallest (NaN never enters)
     for (int64_t i = lane; i < n4; i += 32) {
       const float4 v = __ldg(row + i);
-      m = fminf(m, fminf(fminf(v.x, v.y), fminf(v.z, v.w)));
-    }
+      const float x[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
-    const float T = m;
+      for (int e = 0; e < 4; ++e) {
+        // comparisons, so that a NaN is skipped (two distinct columns)
+        const bool lt1 = x[e] < m1, lt2 = x[e] < m2;
+        m2 = lt1 ? m1 : (lt2 ? x[e] : m2);
+        m1 = lt1 ? x[e] : m1;
+      }
+    }
+    // the 32 smallest of the 64: sort both sets across the warp; the
+    // element-wise minimum of one and the other reversed holds them, and
+    // T is their largest
+    const float s1 = warp_sort_asc_f32(m1);
+    const float s2 = __shfl_sync(0xffffffffu, warp_sort_asc_f32(m2), 31 - lane);
+    float T = fminf(s1, s2);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) T = fmaxf(T, __shfl_xor_sync(0xffffffffu, T, o));
     uint64_t mine = kEmpty, worst = kEmpty;
     float4 nxt = lane < n4 ? __ldcs(row + lane) : kInf4;
     for (int64_t i0 = 0; i0 < n4; i0 += 32) {
