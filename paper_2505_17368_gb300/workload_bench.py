@@ -35,7 +35,22 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
-UPPER_SWEEP = [1, 32, 64, 128, 256]
+# (ef_upper, descend_all, exact_upper, exact_method): the width of the upper-layer beams, whether
+# each layer is entered at all candidates of the one above, and the lowest upper layer whose
+# exact candidate set is taken ("L<i>": the size of layer i of the index; 0: none) with how it
+# is found (1: batched distance tiles)
+UPPER_SWEEP = [(1, 0, 0, 0), (32, 0, 0, 0), (64, 0, 0, 0), (128, 0, 0, 0), (256, 0, 0, 0),
+               (16, 1, "L2", 1), (32, 0, "L2", 1), (64, 0, "L2", 1), (128, 0, "L2", 1)]
+
+
+def _beam(b, sizes):
+    efu, da, xu, xm = b
+    if isinstance(xu, str):
+        li = int(xu[1:])
+        if li >= len(sizes):
+            return None
+        xu = sizes[li]
+    return {"ef_upper": efu, "descend_all": da, "exact_upper": xu, "exact_method": xm}
 K = 10
 
 
@@ -121,12 +136,16 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
     gi, _ = H.exact_knn(Xd, Qd, K, metric=metric)
     gt = gi.cpu().numpy()
     best, table = None, []
-    for efu in UPPER_SWEEP:
+    sizes = idx.info()["sizes"]
+    for b in UPPER_SWEEP:
+        bk = _beam(b, sizes)
+        if bk is None:
+            continue
         for ef in EF_SWEEP:
-            ids, _, _ = idx.search(Qd, k=K, ef=ef, ef_upper=efu)
+            ids, _, _ = idx.search(Qd, k=K, ef=ef, **bk)
             rec = _recall(ids.cpu().numpy(), gt)
-            ms = _time(lambda: idx.search(Qd, k=K, ef=ef, ef_upper=efu), flush)
-            table.append({"ef_upper": efu, "ef": ef, "recall_at_10": round(rec, 4), "ms": round(ms, 3)})
+            ms = _time(lambda: idx.search(Qd, k=K, ef=ef, **bk), flush)
+            table.append(dict(bk, ef=ef, recall_at_10=round(rec, 4), ms=round(ms, 3)))
             if rec >= target:
                 if best is None or ms < best["ms"]:
                     best = table[-1]
@@ -138,13 +157,13 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
         "uncertified_rows": inf["uncertified_rows"], "sweep": table,
     }
     if best is not None:
-        res.update(qps=len(Q) / (best["ms"] * 1e-3), ef=best["ef"], ef_upper=best["ef_upper"],
-                   recall_at_10=best["recall_at_10"])
-        ef, efu = best["ef"], best["ef_upper"]
+        bk = {k: best[k] for k in ("ef_upper", "descend_all", "exact_upper", "exact_method")}
+        res.update(qps=len(Q) / (best["ms"] * 1e-3), ef=best["ef"], recall_at_10=best["recall_at_10"], **bk)
+        ef = best["ef"]
     else:
-        ef, efu = EF_SWEEP[-1], UPPER_SWEEP[-1]
+        ef, bk = EF_SWEEP[-1], _beam(UPPER_SWEEP[4], sizes)
     # per-query work at the chosen setting (the paper reports worst cases)
-    _, _, st = idx.search(Qd, k=K, ef=ef, ef_upper=efu, stats=True)
+    _, _, st = idx.search(Qd, k=K, ef=ef, stats=True, **bk)
     st = st.cpu().numpy().astype(np.int64)
     hops = st[:, 1] + st[:, 2]
     res["per_query"] = {"evals_mean": float(st[:, 0].mean()), "evals_max": int(st[:, 0].max()),
@@ -152,14 +171,14 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
                         "upper_layer_expansions_mean": float(st[:, 2].mean())}
     if "ef_per_query" in info:
         efq = torch.from_numpy(np.asarray(info["ef_per_query"], np.int32)).cuda()
-        ids, _, _ = idx.search(Qd, k=K, ef=efq, ef_upper=efu)
+        ids, _, _ = idx.search(Qd, k=K, ef=efq, **bk)
         rec = _recall(ids.cpu().numpy(), gt)
-        ms = _time(lambda: idx.search(Qd, k=K, ef=efq, ef_upper=efu), flush)
-        res["uneven_ef"] = {"ef": "per query, log-uniform in [32, 512]", "ef_upper": efu,
-                            "qps": len(Q) / (ms * 1e-3), "recall_at_10": rec}
+        ms = _time(lambda: idx.search(Qd, k=K, ef=efq, **bk), flush)
+        res["uneven_ef"] = dict(bk, ef="per query, log-uniform in [32, 512]", qps=len(Q) / (ms * 1e-3),
+                                recall_at_10=rec)
     # FP64 check on a query sample at the chosen setting
     s = min(sample, len(Q))
-    ids, dd, _ = idx.search(Qd[:s], k=K, ef=ef, ef_upper=efu)
+    ids, dd, _ = idx.search(Qd[:s], k=K, ef=ef, **bk)
     ids, dd = ids.cpu().numpy(), dd.cpu().numpy().astype(np.float64)
     t64_i, t64_d = _fp64_truth(X, Q[:s], K, angular)
     ref = _pair_dist64(X, Q[:s], ids, angular)
