@@ -49,8 +49,9 @@ UPPER_SWEEP = [(1, 0, 0, 0, 0), (32, 0, 0, 0, 0), (48, 0, 0, 0, 0), (48, 1, 0, 0
                (64, 0, 0, 0, 0), (64, 1, 0, 0, 0), (64, 0, 16, 0, 0), (64, 0, 32, 0, 0), (80, 0, 16, 0, 0),
                (96, 0, 16, 0, 0), (128, 0, 16, 0, 0), (128, 1, 16, 0, 0),
                (32, 0, 0, 256, 0), (48, 1, 0, 256, 0), (64, 0, 0, 256, 0), (64, 1, 0, 256, 0), (64, 0, 16, 256, 0),
-               (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1), (24, 1, 0, "L2", 1), (16, 0, 0, "L2", 1),
-               (32, 0, 0, "L2", 1), (64, 0, 0, "L2", 1), (1, 0, 0, "L1", 1)]
+               (1, 0, 0, "L2", 1), (4, 1, 0, "L2", 1), (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1),
+               (24, 1, 0, "L2", 1), (16, 0, 0, "L2", 1), (32, 0, 0, "L2", 1), (64, 0, 0, "L2", 1),
+               (1, 0, 0, "L1", 1)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
