@@ -200,16 +200,23 @@ __global__ void __launch_bounds__(192, 1)
                    const __grid_constant__ CUtensorMap to_d,
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
-                   int32_t* __restrict__ err) {
+                   int32_t nsplit, int32_t* __restrict__ err) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int64_t nrb = (s + BM - 1) / BM;
-  const int64_t rb = (mode == 0) ? (nrb - 1 - blockIdx.x) : blockIdx.x;
+  // nsplit CTAs per row block (mode 3, which keeps no per-row lists), each
+  // taking a contiguous run of the block's tiles
+  const int64_t bid = blockIdx.x / nsplit;
+  const int sp = (int)(blockIdx.x % nsplit);
+  const int64_t rb = (mode == 0) ? (nrb - 1 - bid) : bid;
   const int64_t r0 = rb * BM;
-  // s rows; sc columns (== s unless mode 2)
+  // s rows; sc columns (== s unless mode 2 or 3)
   const int64_t cend = (mode == 0) ? min(s, r0 + BM) : sc;
-  const int nt = (int)((cend + BN - 1) / BN);
+  const int nt_all = (int)((cend + BN - 1) / BN);
+  const int tps = (nt_all + nsplit - 1) / nsplit;
+  const int t0 = min(nt_all, sp * tps);
+  const int nt = min(nt_all, t0 + tps) - t0;  // this CTA's tiles: t0 .. t0 + nt - 1
   const int chunks_per_tile = 2 * kc;  // (B_hi, B_lo) per 64-wide slice
 
   if (threadIdx.x == 0) {
@@ -248,7 +255,8 @@ __global__ void __launch_bounds__(192, 1)
       }
       long long it = 0;
       bool ok = true;
-      for (int t = 0; t < nt && ok; ++t) {
+      for (int lt = 0; lt < nt && ok; ++lt) {
+        const int t = t0 + lt;
         for (int j = 0; j < chunks_per_tile && ok; ++j, ++it) {
           const int st = (int)(it % NS);
           const uint32_t ph = (uint32_t)((it / NS) & 1);
@@ -271,9 +279,9 @@ __global__ void __launch_bounds__(192, 1)
     if (lane == 0) {
       bool ok = tc::mbar_wait(&sm.afull, 0, abort_flag);
       long long it = 0;
-      for (int t = 0; t < nt && ok; ++t) {
-        const int as = t & 1;
-        const uint32_t aph = (uint32_t)((t >> 1) & 1);
+      for (int lt = 0; lt < nt && ok; ++lt) {
+        const int as = lt & 1;
+        const uint32_t aph = (uint32_t)((lt >> 1) & 1);
         if (!tc::mbar_wait(&sm.tempty[as], aph ^ 1u, abort_flag)) {
           ok = false;
           break;
@@ -333,12 +341,13 @@ __global__ void __launch_bounds__(192, 1)
     float pn[BN / 32];  // column norms of the next tile, one per lane and chunk
 #pragma unroll
     for (int q = 0; q < BN / 32; ++q) {
-      const int64_t c = (int64_t)q * 32 + lane;
+      const int64_t c = (int64_t)t0 * BN + q * 32 + lane;
       pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
     }
-    for (int t = 0; t < nt; ++t) {
-      const int as = t & 1;
-      const uint32_t aph = (uint32_t)((t >> 1) & 1);
+    for (int lt = 0; lt < nt; ++lt) {
+      const int t = t0 + lt;
+      const int as = lt & 1;
+      const uint32_t aph = (uint32_t)((lt >> 1) & 1);
       if (!tc::mbar_wait(&sm.tfull[as], aph, abort_flag)) {
         ok = false;
         break;
@@ -558,7 +567,7 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   CUtensorMap none;  // no matrix output in modes 0 and 1
   std::memset(&none, 0, sizeof(none));
   k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out,
-                                                   nullptr, 0, err);
+                                                   nullptr, 0, 1, err);
   return cudaGetLastError();
 }
 
@@ -591,11 +600,28 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   }
   const size_t smem = tc_smem_bytes();
   const int64_t nrb = (na + BM - 1) / BM;
+  // mode 3: split each row block's tiles over nsplit CTAs (one CTA per SM
+  // fits), choosing the split with the fewest tile-times over all waves
+  int32_t nsplit = 1;
+  if (out_d) {
+    static int sms = 0;
+    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+    const int64_t nt_all = (nb + BN - 1) / BN;
+    double best = 1e300;
+    for (int64_t k = 1; k <= nt_all && k <= 16; ++k) {
+      const int64_t waves = (nrb * k + sms - 1) / sms;
+      const double cost = (double)waves * (double)((nt_all + k - 1) / k + 1);  // +1: a CTA's fixed work
+      if (cost < best) {
+        best = cost;
+        nsplit = (int32_t)k;
+      }
+    }
+  }
   CUtensorMap mo;
   std::memset(&mo, 0, sizeof(mo));
   if (out_d && !make_store_map(&mo, out_d, na, ldo)) return cudaErrorInvalidValue;
-  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
-                                                   out_d ? 3 : 2, out, out_d, ldo, err);
+  k_tile_topk_tc<<<(unsigned)(nrb * nsplit), 192, smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
+                                                             out_d ? 3 : 2, out, out_d, ldo, nsplit, err);
   return cudaGetLastError();
 }
 
