@@ -941,9 +941,10 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 
 // One warp per query: the 32 smallest (distance, column) keys of its row of
 // a tile distance matrix (+inf entries never enter), ascending, one per
-// lane.  Pass 1: each lane's two smallest values over its own columns (4
-// per 128-column step); the 32nd smallest of those 64, T, is >= the row's
-// 32nd smallest value (32 distinct columns lie at or below it).  Pass 2 (the
+// lane.  Pass 1: each lane's minimum over the even and over the odd columns
+// of its 4 per 128-column step (64 disjoint column groups); the 32nd
+// smallest of those 64 minima, T, is >= the row's 32nd smallest value (32
+// distinct columns lie at or below it).  Pass 2 (the
 // row again, now mostly from L2) merges only entries <= T into the running
 // list: a few passing keys by shuffle insertion, many by sorting the batch
 // and a bitonic merge.
@@ -956,21 +957,15 @@ __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t 
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float4* row = reinterpret_cast<const float4*>(D + q * ldo);
     const int64_t n4 = ldo / 4;  // float4 per row
-    float m1 = kInf, m2 = kInf;  // this lane's two smallest (NaN never enters)
+    float m1 = kInf, m2 = kInf;  // minima of this lane's two groups (fminf skips NaN)
     for (int64_t i = lane; i < n4; i += 32) {
       const float4 v = __ldg(row + i);
-      const float x[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        // comparisons, so that a NaN is skipped (two distinct columns)
-        const bool lt1 = x[e] < m1, lt2 = x[e] < m2;
-        m2 = lt1 ? m1 : (lt2 ? x[e] : m2);
-        m1 = lt1 ? x[e] : m1;
-      }
+      m1 = fminf(m1, fminf(v.x, v.z));
+      m2 = fminf(m2, fminf(v.y, v.w));
     }
-    // the 32 smallest of the 64: sort both sets across the warp; the
-    // element-wise minimum of one and the other reversed holds them, and
-    // T is their largest
+    // the 32 smallest of the 64 minima: sort both sets across the warp;
+    // the element-wise minimum of one and the other reversed holds them,
+    // and T is their largest
     const float s1 = warp_sort_asc_f32(m1);
     const float s2 = __shfl_sync(0xffffffffu, warp_sort_asc_f32(m2), 31 - lane);
     float T = fminf(s1, s2);
