@@ -1165,11 +1165,19 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         // coalesced) and a selection pass at full occupancy; else the
         // running lists inside the tile epilogue
         const int64_t ldo = (s + 31) / 32 * 32;
-        if (s <= kDenseExactMax && (double)nq * (double)ldo * 4.0 <= kDenseExactBytes) {
-          float* dm = sc.get<float>((size_t)nq * ldo);
-          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, st));
-          launch_select_top32(dm, nq, s, ldo, pkeys, st);
-          launches += 1;
+        if (s <= kDenseExactMax) {
+          // batches whose matrix exceeds kDenseExactBytes go through it in
+          // chunks of whole 128-query blocks, one matrix buffer reused
+          int64_t qc = (int64_t)(kDenseExactBytes / (4.0 * (double)ldo)) / 128 * 128;
+          qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
+          float* dm = sc.get<float>((size_t)qc * ldo);
+          for (int64_t q0 = 0; q0 < nq; q0 += qc) {
+            const int64_t cn = std::min<int64_t>(qc, nq - q0);
+            CK(launch_tile_cross_tc(static_cast<uint16_t*>(qh) + q0 * dkk, static_cast<uint16_t*>(ql) + q0 * dkk,
+                                    qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, st));
+            launch_select_top32(dm, cn, s, ldo, pkeys + q0 * 32, st);
+            launches += q0 > 0 ? 2 : 1;
+          }
         } else {
           CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, st));
         }

@@ -176,6 +176,11 @@ def test_full_size_tiles_equal_scan():
     sel = np.random.default_rng(13).choice(len(Q), 300, replace=False)
     gi, gd = O.bruteforce(X, Q[sel], 10)
     assert O.recall_at_k(out[H.EXACT_TILES][0][sel], gi, gd).mean() >= 0.95
+    # a batch whose distance matrix exceeds 1 GiB goes through it in chunks
+    _, Qb, _ = synth.workload("mixture-1m-d128", nq=100_000)
+    outb = _run(gidx, Qb, methods=(H.EXACT_TILES, H.EXACT_SCAN), k=10, ef=48, ef_upper=16, descend_all=1,
+                exact_upper=xu)
+    _same(outb)
     # layer 1 (60,577 points): the running lists inside the tile epilogue
     out = _run(gidx, Q[:2000], methods=(H.EXACT_TILES, H.EXACT_SCAN), k=10, ef=48, exact_upper=sizes[1])
     _same(out)
