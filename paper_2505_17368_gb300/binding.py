@@ -357,6 +357,11 @@ class Index:
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
+        exact_upper / exact_method: the lowest upper layer of at most
+        exact_upper points gives its exact candidate set, found by a sort in
+        the visited table (EXACT_SORT), one batched distance-tile launch with
+        a certified rescore (EXACT_TILES) or a scan (EXACT_SCAN).
+        time_kernel: record the search launches' device time (last_search_ms).
         Returns (ids int64 [nq, stride], dists float32 [nq, stride], stats or None)."""
         L = load()
         sp = SearchParams()

@@ -28,6 +28,7 @@
 #include <cudaTypedefs.h>
 #include <stdint.h>
 
+#include <atomic>
 #include <cstddef>
 #include <cstring>
 
@@ -591,12 +592,15 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   if (!make_map(&mah, a_hi, na, dk, BM) || !make_map(&mal, a_lo, na, dk, BM)) return cudaErrorInvalidValue;
   const CUtensorMap& mbh = static_cast<const CUtensorMap*>(b_maps)[0];
   const CUtensorMap& mbl = static_cast<const CUtensorMap*>(b_maps)[1];
-  static bool attr_set = false;  // the attribute outlives the call; set it once
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)tc_smem_bytes());
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  // the attribute outlives the call: set it once per device
+  static std::atomic<bool> attr_set[64];
+  if (dev >= 64 || !attr_set[dev].load()) {
+    e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
     if (e != cudaSuccess) return e;
-    attr_set = true;
+    if (dev < 64) attr_set[dev].store(true);
   }
   const size_t smem = tc_smem_bytes();
   const int64_t nrb = (na + BM - 1) / BM;
@@ -604,8 +608,8 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   // fits), choosing the split with the fewest tile-times over all waves
   int32_t nsplit = 1;
   if (out_d) {
-    static int sms = 0;
-    if (!sms && cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, 0) != cudaSuccess) sms = 1;
+    int sms = 1;
+    if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || sms < 1) sms = 1;
     const int64_t nt_all = (nb + BN - 1) / BN;
     double best = 1e300;
     for (int64_t k = 1; k <= nt_all && k <= 16; ++k) {
