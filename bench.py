@@ -40,18 +40,19 @@ import synth  # noqa: E402
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
 EF_SWEEP = [16, 24, 32, 36, 40, 44, 48, 52, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
-# (ef_upper, descend_all, ef_l1, exact_upper, exact_method): beam width on the
-# upper layers, whether each layer is entered at all candidates of the layer
-# above, the beam width on layer 1 (0 = ef_upper), the size up to which an
-# upper layer gives its exact candidate set ("L<i>": the size of layer i of
-# the index at hand) and how that set is found (0 SORT, 1 TILES)
+# (ef_upper, descend_all, ef_l1, exact_upper, exact_method[, rerank_mult]): beam
+# width on the upper layers, whether each layer is entered at all candidates of
+# the layer above, the beam width on layer 1 (0 = ef_upper), the size up to
+# which an upper layer gives its exact candidate set ("L<i>": the size of layer
+# i of the index at hand), how that set is found (0 SORT, 1 TILES) and the
+# FP32 rerank of the best rerank_mult * k (default 4)
 UPPER_SWEEP = [(1, 0, 0, 0, 0), (32, 0, 0, 0, 0), (48, 0, 0, 0, 0), (48, 1, 0, 0, 0), (56, 0, 0, 0, 0),
                (64, 0, 0, 0, 0), (64, 1, 0, 0, 0), (64, 0, 16, 0, 0), (64, 0, 32, 0, 0), (80, 0, 16, 0, 0),
                (96, 0, 16, 0, 0), (128, 0, 16, 0, 0), (128, 1, 16, 0, 0),
                (32, 0, 0, 256, 0), (48, 1, 0, 256, 0), (64, 0, 0, 256, 0), (64, 1, 0, 256, 0), (64, 0, 16, 256, 0),
                (1, 0, 0, "L2", 1), (4, 1, 0, "L2", 1), (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1),
                (24, 1, 0, "L2", 1), (16, 0, 0, "L2", 1), (32, 0, 0, "L2", 1), (64, 0, 0, "L2", 1),
-               (1, 0, 0, "L1", 1)]
+               (1, 0, 0, "L1", 1), (8, 1, 0, "L2", 1, 2), (16, 1, 0, "L2", 1, 2)]
 K = 10
 RECALL_TARGET = 0.95
 NOMINAL_HBM_GBS = 7900.0
@@ -290,7 +291,9 @@ def run_ours(args):
     def sweep(index, tag):
         best = None
         sizes = index.info()["sizes"]
-        for efu, da, l1, xu, xm in UPPER_SWEEP:
+        for entry in UPPER_SWEEP:
+            efu, da, l1, xu, xm = entry[:5]
+            rm = entry[5] if len(entry) > 5 else 4
             if isinstance(xu, str):
                 li = int(xu[1:])
                 if li >= len(sizes):
@@ -298,26 +301,27 @@ def run_ours(args):
                 xu = sizes[li]
             for ef in EF_SWEEP:
                 t, ids = _timed_search(index, Qd, ef, efu, 4, 1, None, stream, descend_all=da, ef_l1=l1,
-                                       shape={"exact_upper": xu, "exact_method": xm})
+                                       shape={"exact_upper": xu, "exact_method": xm, "rerank_mult": rm})
                 r = _recall(ids.cpu().numpy(), gt)
                 print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} exact_upper={xu} "
-                      f"exact_method={xm} ef={ef} recall@10={r:.4f} ms={1e3 * min(t):.3f}", file=sys.stderr,
-                      flush=True)
+                      f"exact_method={xm} rerank_mult={rm} ef={ef} recall@10={r:.4f} ms={1e3 * min(t):.3f}",
+                      file=sys.stderr, flush=True)
                 if r >= RECALL_TARGET:
                     # a later configuration must be clearly faster to replace an earlier one
-                    if best is None or min(t) < 0.98 * best[6]:
-                        best = (ef, efu, da, l1, xu, xm, min(t), r)
+                    if best is None or min(t) < 0.98 * best[7]:
+                        best = (ef, efu, da, l1, xu, xm, rm, min(t), r)
                     break
         return best
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
     if args.beam:
         f = args.beam.split(",")
         b_xu = info["sizes"][int(f[4][1:])] if f[4].startswith("L") else int(f[4])
-        beam = (int(f[0]), int(f[1]), int(f[2]), int(f[3]), b_xu, int(f[5]))
+        beam = (int(f[0]), int(f[1]), int(f[2]), int(f[3]), b_xu, int(f[5]), int(f[6]) if len(f) > 6 else 4)
         picked = []
         for index in (idx_bf16, idx_f32):
             t, ids = _timed_search(index, Qd, beam[0], beam[1], 4, 1, None, stream, descend_all=beam[2],
-                                   ef_l1=beam[3], shape={"exact_upper": beam[4], "exact_method": beam[5]})
+                                   ef_l1=beam[3], shape={"exact_upper": beam[4], "exact_method": beam[5],
+                                                         "rerank_mult": beam[6]})
             picked.append(beam + (min(t), _recall(ids.cpu().numpy(), gt)))
         chosen, plain = picked
     else:
@@ -325,18 +329,18 @@ def run_ours(args):
         plain = sweep(idx_f32, "f32")
     if chosen is None or plain is None:
         raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, da, l1, xu, xm, _, rec = chosen
+    ef, efu, da, l1, xu, xm, rm, _, rec = chosen
     # ---- launch shape (warps per block, visited-table size) by the autotuner
     from paper_2505_17368_gb300 import autotune
 
     shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
                           exact_method=xm, use_cache=False)
-    shape = dict(shape, exact_upper=xu, exact_method=xm)
+    shape = dict(shape, exact_upper=xu, exact_method=xm, rerank_mult=rm)
     # ---- algorithmic bytes per launch from the kernel's own counters
     _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
-    R = min(4 * K, ef)
+    R = min(rm * K, ef)
     alg_bytes = int(st[:, 0].sum() * row_bf16 + st[:, 1].sum() * 128 + args.nq * (R * 128 * 4 + 128 * 4 + K * 12))
     if xm == 1 and xu > 0:
         alg_bytes += args.nq * (32 * 8 + 4)  # each query's tile candidates and centred norm
@@ -356,7 +360,7 @@ def run_ours(args):
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
     # plain FP32 comparator, same procedure
-    p_ef, p_efu, p_da, p_l1, p_xu, p_xm, _, p_rec = plain
+    p_ef, p_efu, p_da, p_l1, p_xu, p_xm, p_rm, _, p_rec = plain
     p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da,
                                ef_l1=p_l1, shape={"exact_upper": p_xu, "exact_method": p_xm})
     plain_qps = args.nq / statistics.median(p_times)
@@ -386,15 +390,16 @@ def run_ours(args):
     k_avg = statistics.mean(ms for ms, _ in kern) / 1e3
     launches_per_step = kern[-1][1]
     achieved = alg_bytes / k_avg / 1e9
-    traffic = _profile_traffic((ef, efu, da, l1, xu, xm))
+    traffic = _profile_traffic((ef, efu, da, l1, xu, xm), rm)
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "bf16", "data": "synthetic",
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
-            "descend_all": da, "ef_l1": l1, "exact_upper": xu, "exact_method": xm, "launch_shape": shape,
-            "form": "bf16 traversal + fp32 rerank of top 4k", "recall_at_10": rec, "l2": "flushed between steps",
+            "descend_all": da, "ef_l1": l1, "exact_upper": xu, "exact_method": xm, "rerank_mult": rm,
+            "launch_shape": shape,
+            "form": f"bf16 traversal + fp32 rerank of top {rm}k", "recall_at_10": rec, "l2": "flushed between steps",
             "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
             "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
                           "exact_upper": p_xu, "exact_method": p_xm,
@@ -455,11 +460,11 @@ def _build_roofline(info):
             "algorithmic_flops": info["tile_flops"], "peak_source": f"{src} bf16 sustained"}
 
 
-def _profile_traffic(beam):
+def _profile_traffic(beam, rerank_mult=4):
     """DRAM bytes per launch of the search kernel from the committed ncu
     summary, if it was taken on the current kernel source with the same
     beam configuration (ef, ef_upper, descend_all, ef_l1, exact_upper,
-    exact_method); else None."""
+    exact_method, and rerank_mult where it is not 4); else None."""
     import hashlib
 
     path = os.path.join(ROOT, "profiles", "search_bf16_mixture-1m-d128.md")
@@ -472,6 +477,8 @@ def _profile_traffic(beam):
                 k, v = line[2:].rsplit(":", 1)  # keys may hold a colon ("sha256[:16]")
                 kv[k.strip()] = v.strip().strip("`")
         want = "ef={} ef_upper={} descend_all={} ef_l1={} exact_upper={} exact_method={}".format(*beam)
+        if rerank_mult != 4:
+            want += f" rerank_mult={rerank_mult}"
         if kv.get("search.cu sha256[:16]") == sha:
             return float(kv[f"dram bytes per launch [{want}]"])
     except (OSError, KeyError, ValueError):

@@ -2,7 +2,7 @@
 
     python -m paper_2505_17368_gb300.profile_driver search [--n 1000000] [--nq 10000] [--ef 64] [--ef-upper 64]
                                                           [--descend-all 0] [--ef-l1 0] [--exact-upper 0]
-                                                          [--exact-method 0]
+                                                          [--exact-method 0] [--rerank-mult 4]
     python -m paper_2505_17368_gb300.profile_driver tiles  [--n 200000]
 
 `search` builds a BF16 index of the n-point prefix of the 1M x 128 mixture
@@ -38,6 +38,7 @@ def main():
     ap.add_argument("--ef-l1", type=int, default=0)
     ap.add_argument("--exact-upper", type=int, default=0)
     ap.add_argument("--exact-method", type=int, default=0)
+    ap.add_argument("--rerank-mult", type=int, default=4)
     a = ap.parse_args()
     n = a.n or (1_000_000 if a.what == "search" else 200_000)
     X, Q, _ = synth.workload("mixture-1m-d128", n=n, nq=a.nq)
@@ -52,7 +53,7 @@ def main():
     idx = H.Index(Xd, storage=H.BF16, seed=0)
     for _ in range(3):
         ids, _, _ = idx.search(Qd, k=10, ef=a.ef, ef_upper=a.ef_upper, descend_all=a.descend_all, ef_l1=a.ef_l1,
-                               exact_upper=a.exact_upper, exact_method=a.exact_method)
+                               exact_upper=a.exact_upper, exact_method=a.exact_method, rerank_mult=a.rerank_mult)
     torch.cuda.synchronize()
     print("search ok", idx.info()["sizes"], ids[0, :3].tolist())
 
