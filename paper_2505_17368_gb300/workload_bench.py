@@ -40,7 +40,8 @@ EF_SWEEP = [16, 24, 32, 48, 64, 96, 128, 192, 256, 384, 512]
 # exact candidate set is taken ("L<i>": the size of layer i of the index; 0: none) with how it
 # is found (1: batched distance tiles)
 UPPER_SWEEP = [(1, 0, 0, 0), (32, 0, 0, 0), (64, 0, 0, 0), (128, 0, 0, 0), (256, 0, 0, 0),
-               (16, 1, "L2", 1), (32, 0, "L2", 1), (64, 0, "L2", 1), (128, 0, "L2", 1)]
+               (16, 1, "L2", 1), (32, 0, "L2", 1), (64, 0, "L2", 1), (128, 0, "L2", 1), (16, 1, "L3", 1),
+               (64, 0, "L3", 1)]
 
 
 def _beam(b, sizes):
