@@ -221,7 +221,9 @@ typedef enum { HENN_EXACT_SORT = 0, HENN_EXACT_TILES = 1, HENN_EXACT_SCAN = 2 } 
 void henn_search_params_default(henn_search_params* sp);
 
 /*
- * henn_search -- Query of Alg. 4 for a batch, one persistent launch.
+ * henn_search -- Query of Alg. 4 for a batch: one persistent search launch,
+ * preceded with exact_method TILES by the query-preparation, distance-tile
+ * and top-32 selection launches of the exact layer.
  * Q: nq x d float32.  Per query: entry = a random node of the top layer
  * (keyed by query_keys[q]), greedy search (Alg. 4 GreedySearch) on layers
  * L..1 (or a beam of width ef_upper, the candidate set of Sec. 2.2 applied
