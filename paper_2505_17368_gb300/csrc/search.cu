@@ -242,12 +242,14 @@ __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t
 template <typename VT, int G, int CPL>
 __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
                                     uint64_t* W, int32_t* table, int HB, uint64_t* stage, const float* qs,
-                                    int& evals, int& expansions, int& evictions, int nseed = 0) {
+                                    int& evals_out, int& expansions_out, int& evictions_out, int nseed = 0) {
   const int lane = lane_id();
   const unsigned below = (1u << lane) - 1u;  // lanes under this one
   int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
   const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
   const bool bitmap = Ly.size <= ((int64_t)32 << HB);
+  // the counters stay in registers here (the caller's live in its frame)
+  int evals = 0, expansions = 0, evictions = evictions_out;
   auto mark = [&](int32_t id) { return bitmap ? visit_bit(table, id) : visit(table, HB, id, evictions); };
   const int words = bitmap ? (int)((Ly.size + 31) >> 5) : (1 << HB);
   for (int s = lane; s < words; s += 32) table[s] = bitmap ? 0 : -1;
@@ -347,6 +349,9 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     nw = min(ef, nw + ccnt);
     first = min(first, p0);
   }
+  evals_out += evals;
+  expansions_out += expansions;
+  evictions_out = evictions;
   return nw;
 }
 
