@@ -334,7 +334,7 @@ def run_ours(args):
     from paper_2505_17368_gb300 import autotune
 
     shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
-                          exact_method=xm, use_cache=False)
+                          exact_method=xm, rerank_mult=rm, use_cache=False)
     shape = dict(shape, exact_upper=xu, exact_method=xm, rerank_mult=rm)
     # ---- algorithmic bytes per launch from the kernel's own counters
     _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)

@@ -51,10 +51,10 @@ def candidates(k, ef, ef_upper=1, ef_l1=0, exact_upper=0, exact_method=0):
     return out
 
 
-def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all, exact_upper=0, exact_method=0):
+def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all, exact_upper=0, exact_method=0, rerank_mult=4):
     bucket = 1 << max(0, int(math.ceil(math.log2(max(nq, 1)))))
     return (f"n={index.n},d={index.d},s={index.storage},b={bucket},k={k},ef={ef},eu={ef_upper},l1={ef_l1},"
-            f"da={descend_all},xu={exact_upper},xm={exact_method}")
+            f"da={descend_all},xu={exact_upper},xm={exact_method},rm={rerank_mult}")
 
 
 def _load(path):
@@ -65,11 +65,12 @@ def _load(path):
         return {}
 
 
-def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper=0, exact_method=0):
+def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper=0, exact_method=0,
+                rerank_mult=4):
     import torch
 
     def run(shape):
-        shape = dict(shape, exact_upper=exact_upper, exact_method=exact_method)
+        shape = dict(shape, exact_upper=exact_upper, exact_method=exact_method, rerank_mult=rerank_mult)
         index.search(Q, k=k, ef=ef, ef_upper=ef_upper, ef_l1=ef_l1, descend_all=descend_all, **shape)
         torch.cuda.synchronize()
         ts = []
@@ -86,15 +87,16 @@ def _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_up
 
 
 def tune(index, Q, k=10, ef=64, ef_upper=1, ef_l1=0, descend_all=0, repeats=3, cache_path=DEFAULT_CACHE,
-         use_cache=True, timer=None, exact_upper=0, exact_method=0):
+         use_cache=True, timer=None, exact_upper=0, exact_method=0, rerank_mult=4):
     """Fastest launch shape for this (index, batch, beam); Q is a CUDA
     tensor.  `timer(shape) -> ms` replaces the CUDA-event timing (tests)."""
-    key = _key(index, Q.shape[0], k, ef, ef_upper, ef_l1, descend_all, exact_upper, exact_method)
+    key = _key(index, Q.shape[0], k, ef, ef_upper, ef_l1, descend_all, exact_upper, exact_method, rerank_mult)
     with _LOCK:
         cache = _load(cache_path) if use_cache else {}
         if key in cache:
             return dict(cache[key]["shape"])
-    run = timer or _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper, exact_method)
+    run = timer or _cuda_timer(index, Q, k, ef, ef_upper, ef_l1, descend_all, repeats, exact_upper, exact_method,
+                               rerank_mult)
     best, best_t, table = None, float("inf"), []
     for shape in candidates(k, ef, ef_upper, ef_l1, exact_upper, exact_method):
         t = run(shape)
