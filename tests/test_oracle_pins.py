@@ -651,3 +651,135 @@ def test_delete_tombstones_give_live_nearest():
     want = np.argsort(D, axis=1, kind="stable")[:, :10]
     assert np.array_equal(got, want)
     assert not dead[got].any()
+
+
+# ------------------------------- upper-layer candidate sets (Sec. 2.2)
+#
+# Sec. 2.2 keeps "a set of candidates at each step" on the way down.  The
+# pins below remove the edges of the layers under the one being checked, so
+# that those layers' beams can only return what they were seeded with:
+# the search's output is then exactly the hand-down of the checked layer,
+# and scipy brute force over that layer's points fixes it.  A wrong down
+# array, unsorted seeds, or truncation to the wrong width fails them.
+
+def _edgeless(idx, layers):
+    """Copy of idx whose listed layers have no edges (every row -1)."""
+    out = dict(idx)
+    out["adj"] = [np.full_like(a, -1) if i in layers else a for i, a in enumerate(idx["adj"])]
+    return out
+
+
+def _strongly_connected(adj):
+    import networkx as nx
+
+    G = nx.DiGraph()
+    G.add_nodes_from(range(len(adj)))
+    G.add_edges_from((v, int(u)) for v in range(len(adj)) for u in adj[v] if u >= 0)
+    return nx.is_strongly_connected(G)
+
+
+def _nearest_of_layer(X, Q, ids, width):
+    """The `width` points of a layer nearest to each query, ties by
+    position, as global ids (scipy)."""
+    D = cdist(Q.astype(np.float64), X[ids].astype(np.float64), "sqeuclidean")
+    pos = np.array([np.lexsort((np.arange(len(ids)), D[q]))[:width] for q in range(len(Q))])
+    return ids[pos]
+
+
+@pytest.fixture(scope="module")
+def hier3k():
+    X = synth.uniform_cube(3000, 8, seed=41)
+    Q = synth.uniform_cube(40, 8, seed=42)
+    idx = O.build_index(X, seed=9)
+    assert idx["L"] >= 2
+    return X, Q, idx
+
+
+def test_covering_beam_on_layer1_hands_down_its_nearest_set(hier3k):
+    """A beam of width >= |L_1| on a strongly connected layer-1 graph
+    evaluates the whole layer; with descend_all its candidates, sorted,
+    seed layer 0, whose width-ef beam keeps the first ef.  Layer 0 without
+    edges returns those seeds: the ef nearest layer-1 points (global ids)."""
+    X, Q, idx = hier3k
+    s1 = len(idx["ids"][1])
+    assert _strongly_connected(idx["adj"][1])
+    ix = _edgeless(idx, {0})
+    for ef in (1, 7, 30):
+        got, gd, st = O.search(ix, X, Q, k=ef, ef=ef, ef_upper=s1 + 5, descend_all=1)
+        want = _nearest_of_layer(X, Q, idx["ids"][1], ef)
+        assert np.array_equal(got, want), ef
+        # the layer-0 candidate set starts as the first ef seeds: an edgeless
+        # layer expands each of them once and nothing else
+        assert np.all(st[:, 1] == ef), ef
+        D = cdist(Q.astype(np.float64), X.astype(np.float64), "euclidean")
+        assert np.allclose(gd, np.take_along_axis(D, want, 1), rtol=1e-12)
+
+
+def test_best_candidate_only_without_descend_all(hier3k):
+    """Without descend_all only the best candidate of the layer-1 beam goes
+    down (Alg. 4 hands one node to the layer below): with edgeless layer 0
+    the answer is the single nearest layer-1 point, padded."""
+    X, Q, idx = hier3k
+    s1 = len(idx["ids"][1])
+    ix = _edgeless(idx, {0})
+    got, gd, _ = O.search(ix, X, Q, k=3, ef=3, ef_upper=s1 + 5, descend_all=0)
+    want = _nearest_of_layer(X, Q, idx["ids"][1], 1)
+    assert np.array_equal(got[:, :1], want)
+    assert np.all(got[:, 1:] == -1) and np.all(np.isinf(gd[:, 1:]))
+
+
+def test_two_layer_hand_down_and_ef_l1(hier3k):
+    """Layer 2 searched by a covering beam (ef_upper), layer 1 by a beam of
+    width ef_l1 without edges: it keeps the first ef_l1 seeds from layer 2,
+    which go down through both down arrays to edgeless layer 0.  The answer
+    is the ef_l1 nearest layer-2 points, as global ids."""
+    X, Q, idx = hier3k
+    s2 = len(idx["ids"][2])
+    assert _strongly_connected(idx["adj"][2])
+    ix = _edgeless(idx, {0, 1})
+    assert idx["L"] == 2  # layer 2 is the top: its beam starts at the entry
+    for l1 in (1, 3, min(6, s2)):
+        got, _, st = O.search(ix, X, Q, k=l1, ef=l1, ef_upper=s2 + 3, ef_l1=l1, descend_all=1)
+        assert np.array_equal(got, _nearest_of_layer(X, Q, idx["ids"][2], l1)), l1
+        # a beam wider than its layer never fills, so it expands every node
+        # of the connected layer 2; the edgeless layer-1 beam expands its l1
+        # seeds (width 1 is GreedySearch instead, which makes no move there)
+        assert np.all(st[:, 2] == s2 + (l1 if l1 > 1 else 0)), l1
+    # ef_l1 = 0 falls back to ef_upper on layer 1: all of layer 2 goes down
+    got, _, _ = O.search(ix, X, Q, k=s2, ef=s2, ef_upper=s2 + 3, ef_l1=0, descend_all=1)
+    assert np.array_equal(got, _nearest_of_layer(X, Q, idx["ids"][2], s2))
+
+
+def test_exact_sets_equal_covering_beams(hier3k):
+    """Reading of Sec. 2.2 for small layers: the exact candidate set of a
+    layer (exact_upper) is what a covering beam returns on a connected
+    layer, so the two searches agree query by query, and both equal the
+    brute-force hand-down on an edgeless layer 0."""
+    X, Q, idx = hier3k
+    s1 = len(idx["ids"][1])
+    for ix in (idx, _edgeless(idx, {0})):
+        a, ad, _ = O.search(ix, X, Q, k=10, ef=24, ef_upper=s1 + 5, descend_all=1)
+        b, bd, _ = O.search(ix, X, Q, k=10, ef=24, ef_upper=s1 + 5, descend_all=1, exact_upper=s1)
+        assert np.array_equal(a, b) and np.array_equal(ad, bd)
+
+
+def test_greedy_upper_layers_chain_alg4(hier3k):
+    """ef_upper = 1 is Alg. 4: GreedySearch on each layer from the copy of
+    the previous result, starting at the reported entry node of the top
+    layer; with k = ef = 1 the answer is the end of the layer-0 walk."""
+    X, Q, idx = hier3k
+    L = idx["L"]
+    got, _, st = O.search(idx, X, Q, k=1, ef=1, ef_upper=1)
+    for q in range(len(Q)):
+        cur = int(st[q, 3])
+        assert 0 <= cur < len(idx["ids"][L])
+        for i in range(L, 0, -1):
+            cur, _, _ = O.greedy_layer(X, idx["ids"][i], idx["adj"][i], Q[q], cur)
+            cur = int(idx["down"][i][cur])
+        end, _, _ = O.greedy_layer(X, None, idx["adj"][0], Q[q], cur)
+        assert got[q, 0] == end
+    # the entry node is uniform over the top layer's keys (Alg. 4: random root)
+    many = synth.uniform_cube(4000, 8, seed=43)
+    _, _, st = O.search(idx, X, many, k=1, ef=1)
+    counts = np.bincount(st[:, 3], minlength=len(idx["ids"][L]))
+    assert counts.min() > 0
