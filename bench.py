@@ -2,22 +2,30 @@
 Gaussian-mixture workload rescaled to [0, 255], 10,000 queries, k = 10),
 batched BF16 traversal + exact FP32 rerank vs plain FP32; build seconds.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sweep]
 
 One step = one henn_search call over the whole 10,000-query batch with the
 index resident in HBM: one persistent search launch, preceded, when the
 lowest exact upper layer comes from distance tiles (exact_method TILES), by
-the query preparation, tile and top-32 selection launches.  The beam
-configuration (ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method)
-is the cheapest one of a small sweep whose recall@10 against exact ground
-truth (computed on the device by henn_exact_knn) is >= 0.95.  Under
-torchrun every rank holds its own index replica and its own query batch
-(weak scaling, no collective on the data path); rank 0 prints one JSON
-line with the whole-job throughput.
+the query preparation, tile and top-32 selection launches.
+
+The beam (ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method,
+rerank_mult) is DEFAULT_BEAM unless --sweep or --beam picks another.  Its
+recall@10 is scored against FP64 ground truth (the FP64 order of each
+query's 64 FP32-nearest candidates from henn_exact_knn, checked against an
+FP64 brute force on a sample), with ties at the 10th distance counted; if
+it falls under 0.95, ef steps up the EF_SWEEP list until it does not.  The
+same beam is also scored on a held-out query batch.  Beside it the line
+reports the best beam that only walks the upper layers (no exact layer) and
+the paper's plain greedy descent (Alg. 4 on every upper layer).
+
+Under torchrun every rank holds its own index replica and its own query
+batch (weak scaling, no collective on the data path); rank 0 prints one
+JSON line with the whole-job throughput.
 
 --impl reference times the FP64 CPU oracle on the host cores instead (the
 reference arm): it builds its own index on a bounded sample of the same
-workload and answers queries with the same beam configuration.
+workload and answers queries with the same beam form.
 """
 from __future__ import annotations
 
@@ -40,21 +48,31 @@ import synth  # noqa: E402
 METRIC = "search QPS at recall@10≥0.95 on 1×GB300, chosen form vs plain FP32; build seconds"
 WORKLOAD = "mixture-1m-d128"
 EF_SWEEP = [16, 24, 32, 36, 40, 44, 48, 52, 56, 64, 72, 80, 96, 128, 192, 256, 384, 512, 768, 1024]
-# (ef_upper, descend_all, ef_l1, exact_upper, exact_method[, rerank_mult]): beam
-# width on the upper layers, whether each layer is entered at all candidates of
-# the layer above, the beam width on layer 1 (0 = ef_upper), the size up to
-# which an upper layer gives its exact candidate set ("L<i>": the size of layer
-# i of the index at hand), how that set is found (0 SORT, 1 TILES) and the
-# FP32 rerank of the best rerank_mult * k (default 4)
-UPPER_SWEEP = [(1, 0, 0, 0, 0), (32, 0, 0, 0, 0), (48, 0, 0, 0, 0), (48, 1, 0, 0, 0), (56, 0, 0, 0, 0),
-               (64, 0, 0, 0, 0), (64, 1, 0, 0, 0), (64, 0, 16, 0, 0), (64, 0, 32, 0, 0), (80, 0, 16, 0, 0),
-               (96, 0, 16, 0, 0), (128, 0, 16, 0, 0), (128, 1, 16, 0, 0),
-               (32, 0, 0, 256, 0), (48, 1, 0, 256, 0), (64, 0, 0, 256, 0), (64, 1, 0, 256, 0), (64, 0, 16, 256, 0),
-               (1, 0, 0, "L2", 1), (4, 1, 0, "L2", 1), (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1),
-               (24, 1, 0, "L2", 1), (16, 0, 0, "L2", 1), (32, 0, 0, "L2", 1), (64, 0, 0, "L2", 1),
-               (1, 0, 0, "L1", 1), (8, 1, 0, "L2", 1, 2), (16, 1, 0, "L2", 1, 2)]
+# A beam is (ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method, rerank_mult): the
+# layer-0 width, the width on the upper layers (<= 1: GreedySearch of Alg. 4), whether each
+# layer is entered at all candidates of the layer above, the width on layer 1 (0 = ef_upper),
+# the size up to which an upper layer gives its exact candidate set ("L<i>": the size of layer
+# i of the index at hand; 0 = never), how that set is found (0 SORT, 1 TILES) and the FP32
+# rerank of the best rerank_mult * k.
+#
+# The default: layer 2 (3,677 points of the 1M mixture) exact from one batched distance-tile
+# launch, its 16 nearest seeding a width-16 beam on layer 1, a width-48 beam on layer 0, the
+# FP32 rerank of the best 20.
+DEFAULT_BEAM = (48, 16, 1, 0, "L2", 1, 2)
+# --sweep: (ef_upper, descend_all, ef_l1, exact_upper, exact_method[, rerank_mult]), each
+# tried at every ef of EF_SWEEP up to the first that reaches the target
+UPPER_SWEEP = [(1, 0, 0, 0, 0), (32, 0, 0, 0, 0), (48, 1, 0, 0, 0), (64, 0, 0, 0, 0), (64, 1, 0, 0, 0),
+               (64, 0, 16, 0, 0), (96, 0, 16, 0, 0), (128, 1, 16, 0, 0),
+               (64, 1, 0, 256, 0), (64, 0, 16, 256, 0),
+               (1, 0, 0, "L2", 1), (8, 1, 0, "L2", 1), (16, 1, 0, "L2", 1), (24, 1, 0, "L2", 1),
+               (32, 0, 0, "L2", 1), (1, 0, 0, "L1", 1), (8, 1, 0, "L2", 1, 2), (16, 1, 0, "L2", 1, 2)]
+# Upper layers walked by beams only (no exact layer): the best of these is reported beside the
+# default (reading 11 of the paper's "set of candidates at each step" without reading 16).
+WALK_SWEEP = [(64, 0, 16, 0, 0), (64, 1, 0, 0, 0), (48, 1, 0, 0, 0), (96, 0, 16, 0, 0), (128, 1, 16, 0, 0)]
 K = 10
 RECALL_TARGET = 0.95
+GT_POOL = 64          # FP32 candidates per query that the FP64 ground truth re-ranks
+GT_CHECK_QUERIES = 200  # queries whose ground truth is re-derived by an FP64 brute force
 NOMINAL_HBM_GBS = 7900.0
 L2_BYTES = 129 * 2**20
 
@@ -166,27 +184,96 @@ def _smi_id(dev, local):
         return str(local)
 
 
-def _recall(found, gt):
-    hits = [len(set(found[q].tolist()) & set(gt[q].tolist())) for q in range(gt.shape[0])]
-    return float(np.mean(hits)) / gt.shape[1]
+# ------------------------------------------------------- FP64 ground truth
+
+def fp64_sqdist(X, Q, ids):
+    """FP64 squared L2 distances from each query to the rows ids[q, :]
+    (direct differences; +inf where ids < 0)."""
+    out = np.empty(ids.shape, np.float64)
+    for q0 in range(0, len(Q), 1000):
+        c = ids[q0:q0 + 1000]
+        diff = X[np.maximum(c, 0)].astype(np.float64) - Q[q0:q0 + 1000, None, :].astype(np.float64)
+        dd = np.einsum("qcd,qcd->qc", diff, diff)
+        dd[c < 0] = np.inf
+        out[q0:q0 + 1000] = dd
+    return out
 
 
-def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=0, ef_l1=0, shape=None,
-                  kernel_ms=None):
-    """Step times (s) of `steps` calls after `warmup`; with a list in
-    kernel_ms, also the device time of each call's search launches."""
-    shape = dict(shape or {})
-    if kernel_ms is not None:
-        shape["time_kernel"] = True
+def rerank_fp64(X, Q, cand, k):
+    """The k smallest (FP64 distance, id) of each query's candidate ids."""
+    d = fp64_sqdist(X, Q, cand)
+    order = np.lexsort((cand, d), axis=1)[:, :k]
+    return np.take_along_axis(cand, order, 1), np.take_along_axis(d, order, 1)
+
+
+def fp64_bruteforce(X, Q, k, pool=GT_POOL, chunk=250_000):
+    """Exact k nearest by FP64 distance, every point of X examined: FP64
+    dot-product distances pick each query's `pool` candidates, which are
+    then ordered by FP64 direct differences (ties by id)."""
+    Q64 = Q.astype(np.float64)
+    qn = (Q64 * Q64).sum(1)
+    best_d = np.full((len(Q), 0), np.inf)
+    best_i = np.zeros((len(Q), 0), np.int64)
+    for x0 in range(0, len(X), chunk):
+        X64 = X[x0:x0 + chunk].astype(np.float64)
+        D = (X64 * X64).sum(1)[None, :] - 2.0 * (Q64 @ X64.T) + qn[:, None]
+        p = min(pool, D.shape[1])
+        part = np.argpartition(D, p - 1, axis=1)[:, :p]
+        best_d = np.concatenate([best_d, np.take_along_axis(D, part, 1)], 1)
+        best_i = np.concatenate([best_i, part + x0], 1)
+        keep = np.argsort(best_d, axis=1, kind="stable")[:, :pool]
+        best_d = np.take_along_axis(best_d, keep, 1)
+        best_i = np.take_along_axis(best_i, keep, 1)
+    return rerank_fp64(X, Q, best_i, k)
+
+
+def fp64_ground_truth(H, X, Q, Xd, Qd, k=K, pool=GT_POOL):
+    """FP64 ground truth for all queries: henn_exact_knn's FP32 top-`pool`
+    candidates re-ranked by FP64 distance."""
+    cand, _ = H.exact_knn(Xd, Qd, pool)
+    return rerank_fp64(X, Q, cand.cpu().numpy(), k)
+
+
+def recall_fp64(X, Q, found, gt_ids, gt_d):
+    """Mean recall@k (Sec. 2): |A_q ∩ O_q| / k, a returned id also counting
+    when its FP64 distance equals the k-th ground-truth distance (ties)."""
+    k = gt_ids.shape[1]
+    found = np.asarray(found)[:, :k]
+    fd = fp64_sqdist(X, Q, found)
+    hit = (found[:, :, None] == gt_ids[:, None, :]).any(2) | ((found >= 0) & (fd == gt_d[:, k - 1:k]))
+    return float(hit.sum(1).mean()) / k
+
+
+def _beam(spec, sizes):
+    """(ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method, rerank_mult), "L<i>" resolved."""
+    ef, efu, da, l1, xu, xm, rm = spec
+    if isinstance(xu, str):
+        li = int(xu[1:])
+        xu = sizes[li] if li < len(sizes) else 0
+    return (int(ef), int(efu), int(da), int(l1), int(xu), int(xm), int(rm))
+
+
+def _kw(beam, shape=None):
+    ef, efu, da, l1, xu, xm, rm = beam
+    kw = dict(k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, exact_upper=xu, exact_method=xm, rerank_mult=rm)
+    kw.update(shape or {})
+    return kw
+
+
+def _timed_search(index, Qd, beam, steps, warmup, flush, stream, shape=None, kernel_ms=None):
+    """Step times (s) of `steps` calls after `warmup`, and the last ids;
+    with a list in kernel_ms, also the device time of each call's search
+    launches (henn_last_search_ms)."""
     import torch
 
-    H = sys.modules["paper_2505_17368_gb300"]
+    kw = _kw(beam, shape)
+    if kernel_ms is not None:
+        kw["time_kernel"] = True
     nq = Qd.shape[0]
     ids = torch.empty((nq, K), dtype=torch.int64, device=Qd.device)
     dd = torch.empty((nq, K), dtype=torch.float32, device=Qd.device)
     for _ in range(warmup):
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
-                     out=(ids, dd), **shape)
+        index.search(Qd, stream=stream, out=(ids, dd), **kw)
     torch.cuda.synchronize()
     times = []
     for _ in range(steps):
@@ -195,8 +282,7 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        index.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=descend_all, ef_l1=ef_l1, stream=stream,
-                     out=(ids, dd), **shape)
+        index.search(Qd, stream=stream, out=(ids, dd), **kw)
         e1.record(stream)
         e1.synchronize()
         times.append(e0.elapsed_time(e1) / 1e3)
@@ -205,50 +291,109 @@ def _timed_search(index, Qd, ef, efu, steps, warmup, flush, stream, descend_all=
     return times, ids
 
 
-def _cpu_oracle_leg(ef: int, efu: int, n_sample: int, nq_sample: int, steps: int = 1, l1: int = 0, da: int = 0,
-                    xu: int = 0):
-    """The FP64 oracle (as it stands) on the host cores: its own index on
-    the first n_sample points of the workload stream (built with all
-    cores), then the same beam configuration answering nq_sample queries
-    one after another on one core (the paper's sequential-query protocol).
-    Returns (qps, cores used by the timed search, seconds per step, and the
-    same search with OpenMP over queries on all host cores: (qps, cores))."""
+def _score(index, Qd, Q, X, gt, beam, stream, flush, reps=4):
+    """(recall vs FP64, median step seconds over `reps`) of one beam."""
+    t, ids = _timed_search(index, Qd, beam, reps, 1, flush, stream)
+    return recall_fp64(X, Q, ids.cpu().numpy(), *gt), statistics.median(t)
+
+
+def _reach_target(index, Qd, Q, X, gt, beam, stream, flush, log_tag):
+    """The beam with ef stepped up EF_SWEEP (from its own ef) until the
+    recall target is met; returns (beam, recall, seconds) or None."""
+    ef0 = beam[0]
+    for ef in [ef0] + [e for e in EF_SWEEP if e > ef0]:
+        b = (ef,) + tuple(beam[1:])
+        r, t = _score(index, Qd, Q, X, gt, b, stream, flush)
+        print(f"[{log_tag}] beam={b} recall@10={r:.5f} ms={1e3 * t:.3f}", file=sys.stderr, flush=True)
+        if r >= RECALL_TARGET:
+            return b, r, t
+    return None
+
+
+def _sweep(index, Qd, Q, X, gt, entries, sizes, stream, flush, tag):
+    """Cheapest (by median step time) of the sweep entries at their first
+    ef reaching the target; a later entry must be 2% faster to replace."""
+    best = None
+    for entry in entries:
+        efu, da, l1, xu, xm = entry[:5]
+        rm = entry[5] if len(entry) > 5 else 4
+        beam = _beam((EF_SWEEP[0], efu, da, l1, xu, xm, rm), sizes)
+        if isinstance(xu, str) and beam[4] == 0:
+            continue
+        got = _reach_target(index, Qd, Q, X, gt, beam, stream, flush, tag)
+        if got and (best is None or got[2] < 0.98 * best[2]):
+            best = got
+    return best
+
+
+def _export_layers(index):
+    """The GPU-built hierarchy as plain per-layer arrays (host)."""
+    info = index.info()
+    ids, down, adj = [None], [None], []
+    for i in range(info["L"] + 1):
+        lay = index.layer(i)
+        if i >= 1:
+            ids.append(lay["ids"].astype(np.int64))
+            down.append(lay["down"].astype(np.int64))
+        adj.append(lay["adj"])
+    return ids, down, adj
+
+
+def _cpu_oracle_on_index(layers, X, Q, beam, nq_sample):
+    """The FP64 oracle (as it stands) on the host cores, searching the same
+    hierarchy the GPU searches (its layers, down pointers and graphs,
+    imported) with the same beam form: nq_sample queries answered one
+    after another on one core (the paper's sequential-query protocol), and
+    once more with OpenMP over queries on all cores.  Returns (qps, cores,
+    seconds, (qps_all_cores, cores))."""
     import oracle
 
-    X, Q, _ = synth.workload(WORKLOAD, n=n_sample, nq=nq_sample)
-    oracle.set_threads(len(os.sched_getaffinity(0)))
-    idx = oracle.build_index(X, seed=0)
+    ids, down, adj = layers
+    view = oracle.from_layers(ids, down, adj, seed=0)
+    ef, efu, da, l1, xu, _, _ = beam
+    Qs = np.ascontiguousarray(Q[:nq_sample])
     oracle.set_threads(1)
-    secs = []
-    for _ in range(steps):
-        t0 = time.perf_counter()
-        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
-        secs.append(time.perf_counter() - t0)
+    t0 = time.perf_counter()
+    oracle.search(view, X, Qs, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
+    secs = time.perf_counter() - t0
     ncores = len(os.sched_getaffinity(0))
     oracle.set_threads(ncores)
     t0 = time.perf_counter()
-    oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
+    oracle.search(view, X, Qs, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
     all_cores = (nq_sample / (time.perf_counter() - t0), ncores)
-    return nq_sample / statistics.median(secs), 1, secs, all_cores
+    return nq_sample / secs, 1, secs, all_cores
 
 
 def run_reference(args):
+    """The reference arm: the FP64 oracle on the host cores, its own index
+    on a bounded sample of the workload (the GPU is not used), answering
+    queries with the default beam form (layer 2 exact, beams below)."""
+    import oracle
+
     ws, rank, _ = _dist_env()
     if rank != 0:
         return 0
-    ef, efu = args.ref_ef, args.ref_ef_upper
-    n_sample, nq_sample = args.ref_n, args.ref_nq
-    for _ in range(args.warmup):
-        pass  # the oracle has no warm-up state; its index is built once below
-    qps, cores, secs, _ = _cpu_oracle_leg(ef, efu, n_sample, nq_sample, steps=args.steps)
-    sample = (f"FP64 oracle index on the first {n_sample} of the 1M mixture points (same generator), "
-              f"{nq_sample} queries per step answered sequentially on one core, ef={ef}, ef_upper={efu}, k={K}")
+    X, Q, _ = synth.workload(WORKLOAD, n=args.ref_n, nq=args.ref_nq)
+    oracle.set_threads(len(os.sched_getaffinity(0)))
+    idx = oracle.build_index(X, seed=0)
+    beam = _beam(DEFAULT_BEAM, [int(s) for s in idx["sizes"]])
+    ef, efu, da, l1, xu, _, _ = beam
+    oracle.set_threads(1)
+    secs = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
+        secs.append(time.perf_counter() - t0)
+    qps = args.ref_nq / statistics.median(secs)
+    sample = (f"FP64 oracle, own index on the first {args.ref_n} of the 1M mixture points (same generator; "
+              f"layers {[int(s) for s in idx['sizes']]}), {args.ref_nq} queries per step answered sequentially on "
+              f"one core, ef={ef}, ef_upper={efu}, descend_all={da}, exact_upper={xu} (its layer 2), k={K}")
     line = {
         "impl": "reference", "metric": METRIC, "value": qps, "unit": "queries/s", "n_gpus": ws,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * statistics.median(secs),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": {"workload": WORKLOAD, "n": 1_000_000, "d": 128, "nq": 10_000, "k": K},
-        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": qps, "unit": "queries/s", "cores": 1, "kind": "oracle", "sample": sample},
         "e2e": {"value": qps, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -269,11 +414,14 @@ def run_ours(args):
 
     H.load()
     stream = torch.cuda.current_stream()
-    # ---- inputs (same base set on every rank, own query batch per rank)
+    # ---- inputs (same base set on every rank, own query batch per rank, a held-out batch)
     X, rngmap = synth.gaussian_mixture(args.n, 128, 1000, seed=0, rescale_to_255=True)
     Q, _ = synth.gaussian_mixture(args.nq, 128, 1000, seed=1 + rank, rescale_from=rngmap, rescale_to_255=True)
+    Qh_out, _ = synth.gaussian_mixture(args.nq, 128, 1000, seed=1000 + rank, rescale_from=rngmap,
+                                       rescale_to_255=True)
     Xd = torch.from_numpy(X).to(dev)
     Qd = torch.from_numpy(Q).to(dev)
+    Qd_out = torch.from_numpy(Qh_out).to(dev)
     torch.cuda.synchronize()
     # ---- builds (inputs already resident; wall clock of henn_build)
     t0 = time.perf_counter()
@@ -283,61 +431,36 @@ def run_ours(args):
     idx_f32 = H.Index(Xd, storage=H.F32, seed=0)
     build_f32 = time.perf_counter() - t0
     info = idx_bf16.info()
-    info_f32 = idx_f32.info()
-    # ---- exact ground truth on the device
-    gt, _ = H.exact_knn(Xd, Qd, K)
-    gt = gt.cpu().numpy()
-    # ---- configuration sweep: cheapest (ef, ef_upper) reaching the recall target
-    def sweep(index, tag):
-        best = None
-        sizes = index.info()["sizes"]
-        for entry in UPPER_SWEEP:
-            efu, da, l1, xu, xm = entry[:5]
-            rm = entry[5] if len(entry) > 5 else 4
-            if isinstance(xu, str):
-                li = int(xu[1:])
-                if li >= len(sizes):
-                    continue
-                xu = sizes[li]
-            for ef in EF_SWEEP:
-                t, ids = _timed_search(index, Qd, ef, efu, 4, 1, None, stream, descend_all=da, ef_l1=l1,
-                                       shape={"exact_upper": xu, "exact_method": xm, "rerank_mult": rm})
-                r = _recall(ids.cpu().numpy(), gt)
-                print(f"[sweep {tag}] ef_upper={efu} descend_all={da} ef_l1={l1} exact_upper={xu} "
-                      f"exact_method={xm} rerank_mult={rm} ef={ef} recall@10={r:.4f} ms={1e3 * min(t):.3f}",
-                      file=sys.stderr, flush=True)
-                if r >= RECALL_TARGET:
-                    # a later configuration must be clearly faster to replace an earlier one
-                    if best is None or min(t) < 0.98 * best[7]:
-                        best = (ef, efu, da, l1, xu, xm, rm, min(t), r)
-                    break
-        return best
+    sizes = info["sizes"]
+    # ---- FP64 ground truth (GPU candidates, FP64 order), checked on a sample by FP64 brute force
+    gt = fp64_ground_truth(H, X, Q, Xd, Qd)
+    gt_out = fp64_ground_truth(H, X, Qh_out, Xd, Qd_out)
+    chk = np.random.default_rng(5).choice(args.nq, min(GT_CHECK_QUERIES, args.nq), replace=False)
+    bf_i, _ = fp64_bruteforce(X, Q[chk], K)
+    gt_check = {"queries": int(len(chk)), "identical": int(np.all(bf_i == gt[0][chk], axis=1).sum())}
     flush = torch.empty(L2_BYTES * 2 // 4, dtype=torch.float32, device=dev)
-    if args.beam:
-        f = args.beam.split(",")
-        b_xu = info["sizes"][int(f[4][1:])] if f[4].startswith("L") else int(f[4])
-        beam = (int(f[0]), int(f[1]), int(f[2]), int(f[3]), b_xu, int(f[5]), int(f[6]) if len(f) > 6 else 4)
-        picked = []
-        for index in (idx_bf16, idx_f32):
-            t, ids = _timed_search(index, Qd, beam[0], beam[1], 4, 1, None, stream, descend_all=beam[2],
-                                   ef_l1=beam[3], shape={"exact_upper": beam[4], "exact_method": beam[5],
-                                                         "rerank_mult": beam[6]})
-            picked.append(beam + (min(t), _recall(ids.cpu().numpy(), gt)))
-        chosen, plain = picked
+    # ---- beam: default (or --beam / --sweep), ef stepped up until recall >= target
+    if args.sweep:
+        chosen = _sweep(idx_bf16, Qd, Q, X, gt, UPPER_SWEEP, sizes, stream, flush, "sweep bf16")
     else:
-        chosen = sweep(idx_bf16, "bf16")
-        plain = sweep(idx_f32, "f32")
-    if chosen is None or plain is None:
-        raise SystemExit("recall target not reached by any swept configuration")
-    ef, efu, da, l1, xu, xm, rm, _, rec = chosen
+        spec = DEFAULT_BEAM
+        if args.beam:
+            f = args.beam.split(",")
+            spec = tuple(int(v) if not v.startswith("L") else v for v in f)
+            if len(spec) == 6:
+                spec = spec + (4,)
+        chosen = _reach_target(idx_bf16, Qd, Q, X, gt, _beam(spec, sizes), stream, flush, "beam bf16")
+    if chosen is None:
+        raise SystemExit("recall target not reached")
+    beam, rec_sweep, _ = chosen
+    ef, efu, da, l1, xu, xm, rm = beam
     # ---- launch shape (warps per block, visited-table size) by the autotuner
     from paper_2505_17368_gb300 import autotune
 
     shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
                           exact_method=xm, rerank_mult=rm, use_cache=False)
-    shape = dict(shape, exact_upper=xu, exact_method=xm, rerank_mult=rm)
     # ---- algorithmic bytes per launch from the kernel's own counters
-    _, _, st = idx_bf16.search(Qd, k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stats=True, **shape)
+    _, _, st = idx_bf16.search(Qd, stats=True, **_kw(beam, shape))
     st = st.cpu().numpy().astype(np.int64)
     row_bf16 = 128 * 2
     R = min(rm * K, ef)
@@ -350,8 +473,8 @@ def run_ours(args):
     torch.cuda.synchronize()
     kern = []
     with ClockSampler(_smi_id(dev, local)) as clk:
-        times, ids = _timed_search(idx_bf16, Qd, ef, efu, args.steps, args.warmup, flush, stream, descend_all=da,
-                                   ef_l1=l1, shape=shape, kernel_ms=kern)
+        times, ids = _timed_search(idx_bf16, Qd, beam, args.steps, args.warmup, flush, stream, shape=shape,
+                                   kernel_ms=kern)
         torch.cuda.synchronize()
     if ws > 1:
         torch.distributed.barrier()
@@ -359,29 +482,36 @@ def run_ours(args):
     local_time = sum(times)
     tmax, units = aggregate(local_time, args.nq * args.steps)
     value = units / tmax
-    # plain FP32 comparator, same procedure
-    p_ef, p_efu, p_da, p_l1, p_xu, p_xm, p_rm, _, p_rec = plain
-    p_times, _ = _timed_search(idx_f32, Qd, p_ef, p_efu, args.steps, args.warmup, flush, stream, descend_all=p_da,
-                               ef_l1=p_l1, shape={"exact_upper": p_xu, "exact_method": p_xm})
+    # recall of the timed region's own results (autotuned launch shape), and on the held-out batch
+    rec = recall_fp64(X, Q, ids.cpu().numpy(), *gt)
+    ids_out, _, _ = idx_bf16.search(Qd_out, **_kw(beam, shape))
+    rec_out = recall_fp64(X, Qh_out, ids_out.cpu().numpy(), *gt_out)
+    # ---- plain FP32 at the same beam: batched, and one launch per query
+    p_times, p_ids = _timed_search(idx_f32, Qd, beam, args.steps, args.warmup, flush, stream)
     plain_qps = args.nq / statistics.median(p_times)
-    # one launch per query, FP32 (latency form), on a sample
+    p_rec = recall_fp64(X, Q, p_ids.cpu().numpy(), *gt)
     ns = min(200, args.nq)
     t_one = []
     for q in range(ns):
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
-        idx_f32.search(Qd[q:q + 1], k=K, ef=p_ef, ef_upper=p_efu, descend_all=p_da, ef_l1=p_l1, exact_upper=p_xu,
-                       exact_method=p_xm, stream=stream)
+        idx_f32.search(Qd[q:q + 1], stream=stream, **_kw(beam))
         e1.record(stream)
         e1.synchronize()
         t_one.append(e0.elapsed_time(e1) / 1e3)
     per_query_qps = 1.0 / statistics.median(t_one)
+    # ---- the upper layers walked by beams only, and the paper's greedy descent
+    walk = _sweep(idx_bf16, Qd, Q, X, gt, WALK_SWEEP, sizes, stream, flush, "walk bf16")
+    greedy = []
+    for g_ef in (64, 256, 1024):
+        r, t = _score(idx_bf16, Qd, Q, X, gt, (g_ef, 1, 0, 0, 0, 0, rm), stream, flush, reps=2)
+        greedy.append({"ef": g_ef, "recall_at_10": r, "qps": args.nq / t})
     # ---- end to end through the C ABI with host buffers
     Qh = torch.from_numpy(Q).pin_memory()
     e2e_t = []
     for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
-        idx_bf16.search(Qh.numpy(), k=K, ef=ef, ef_upper=efu, descend_all=da, ef_l1=l1, stream=stream, **shape)
+        idx_bf16.search(Qh.numpy(), stream=stream, **_kw(beam, shape))
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
@@ -390,7 +520,7 @@ def run_ours(args):
     k_avg = statistics.mean(ms for ms, _ in kern) / 1e3
     launches_per_step = kern[-1][1]
     achieved = alg_bytes / k_avg / 1e9
-    traffic = _profile_traffic((ef, efu, da, l1, xu, xm), rm)
+    traffic = _profile_traffic(beam[:6], rm)
     line = {
         "metric": METRIC, "value": value, "unit": "queries/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps, "higher_is_better": True,
@@ -398,13 +528,23 @@ def run_ours(args):
         "config": {
             "workload": WORKLOAD, "n": args.n, "d": 128, "nq": args.nq, "k": K, "ef": ef, "ef_upper": efu,
             "descend_all": da, "ef_l1": l1, "exact_upper": xu, "exact_method": xm, "rerank_mult": rm,
+            "beam_source": "sweep" if args.sweep else ("--beam" if args.beam else "default"),
             "launch_shape": shape,
-            "form": f"bf16 traversal + fp32 rerank of top {rm}k", "recall_at_10": rec, "l2": "flushed between steps",
-            "layers": info["sizes"], "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
-            "plain_f32": {"qps": plain_qps, "ef": p_ef, "ef_upper": p_efu, "descend_all": p_da, "ef_l1": p_l1,
-                          "exact_upper": p_xu, "exact_method": p_xm,
-                          "recall_at_10": p_rec},
+            "form": f"bf16 traversal + fp32 rerank of top {rm}k", "recall_at_10": rec,
+            "recall_at_10_held_out": rec_out, "recall_scoring": (
+                f"FP64 ground truth (FP64 order of each query's {GT_POOL} FP32-nearest candidates from "
+                f"henn_exact_knn; identical to an FP64 brute force on {gt_check['identical']} of "
+                f"{gt_check['queries']} sampled queries), ties at the 10th distance counted; held-out: "
+                f"another {args.nq} queries of the same mixture"),
+            "l2": "flushed between steps",
+            "layers": sizes, "build_seconds_bf16": build_bf16, "build_seconds_f32": build_f32,
+            "plain_f32": {"qps": plain_qps, "recall_at_10": p_rec, "beam": "same as the chosen form"},
             "plain_f32_per_query_launch_qps": per_query_qps,
+            "walk_only_bf16": None if walk is None else {
+                "qps": args.nq / walk[2], "recall_at_10": walk[1], "ef": walk[0][0], "ef_upper": walk[0][1],
+                "descend_all": walk[0][2], "ef_l1": walk[0][3], "rerank_mult": walk[0][6],
+                "note": "upper layers walked by beams only, no exact layer; median of 4 steps"},
+            "greedy_descent_bf16": greedy,
             "step_ms_median": 1e3 * statistics.median(times), "step_ms_max": 1e3 * max(times),
             "qps_of_slowest_step": args.nq / max(times),
             "parallelism": f"replicas{ws}",
@@ -421,14 +561,15 @@ def run_ours(args):
         "clocks": clocks,
     }
     if rank == 0 and not args.no_cpu_baseline:
-        qps, cores, secs, (qps_all, ncores) = _cpu_oracle_leg(ef, efu, args.cpu_n, args.cpu_nq, l1=l1, da=da,
-                                                                xu=xu)
-        # (the oracle computes every exact layer by its definition; exact_method is the GPU's choice of how)
-        sample = (f"FP64 oracle, own index on the first {args.cpu_n} points of the same mixture stream, "
-                  f"{args.cpu_nq} queries, ef={ef}, ef_upper={efu}, ef_l1={l1}, descend_all={da}, exact_upper={xu}")
+        layers = _export_layers(idx_bf16)
+        qps, cores, secs, (qps_all, ncores) = _cpu_oracle_on_index(layers, X, Q, beam, args.cpu_nq)
+        sample = (f"FP64 oracle searching the GPU-built 1M x 128 hierarchy (imported layers, down pointers "
+                  f"and graphs), first {args.cpu_nq} of the {args.nq} queries, same beam (ef={ef}, "
+                  f"ef_upper={efu}, descend_all={da}, ef_l1={l1}, exact_upper={xu}; the oracle finds exact "
+                  f"layers by brute force and searches in FP64)")
         line["cpu_baseline"] = {
             "value": qps, "unit": "queries/s", "cores": cores, "kind": "oracle",
-            "sample": sample + f", answered sequentially on one core (the paper's protocol), {sum(secs):.1f} s of search",
+            "sample": sample + f", answered sequentially on one core (the paper's protocol), {secs:.1f} s",
         }
         line["cpu_baseline_all_cores"] = {
             "value": qps_all, "unit": "queries/s", "cores": ncores, "kind": "oracle",
@@ -494,16 +635,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=1_000_000)
     ap.add_argument("--nq", type=int, default=10_000)
-    ap.add_argument("--cpu-n", type=int, default=50_000)
-    ap.add_argument("--cpu-nq", type=int, default=10_000)
+    ap.add_argument("--cpu-nq", type=int, default=5_000)
     ap.add_argument("--ref-n", type=int, default=50_000)
     ap.add_argument("--ref-nq", type=int, default=2_000)
-    ap.add_argument("--ref-ef", type=int, default=64)
-    ap.add_argument("--ref-ef-upper", type=int, default=64)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--sweep", action="store_true", help="pick the beam by the UPPER_SWEEP search instead")
     ap.add_argument("--beam", default=None,
-                    help="ef,ef_upper,descend_all,ef_l1,exact_upper,exact_method: skip the sweep and use this "
-                         "beam for both forms (exact_upper may be L<i>, the size of layer i)")
+                    help="ef,ef_upper,descend_all,ef_l1,exact_upper,exact_method[,rerank_mult] instead of "
+                         "DEFAULT_BEAM (exact_upper may be L<i>, the size of layer i)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")

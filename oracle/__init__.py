@@ -262,6 +262,22 @@ def build_index(X, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0, M=
     return idx
 
 
+def from_layers(ids, down, adj, metric=L2, seed=0, M=16, Mmax=32, graph=GRAPH_NSW):
+    """An index in this module's form from plain per-layer arrays (layer 0
+    first): ids[i] the sorted global ids of layer i (ids[0] may be None for
+    0..n-1), down[i] the positions of layer i in layer i-1 (down[0]
+    ignored), adj[i] the |L_i| x Mmax layer-local adjacency rows.  Lets the
+    oracle's search (Alg. 4 + beam) run on a hierarchy built elsewhere, such
+    as the GPU's, so the two searches see the same layers and graphs."""
+    L = len(adj) - 1
+    n = len(adj[0])
+    lid = [np.arange(n, dtype=np.int64)] + [np.asarray(ids[i], dtype=np.int64) for i in range(1, L + 1)]
+    ldn = [None] + [np.asarray(down[i], dtype=np.int64) for i in range(1, L + 1)]
+    ladj = [np.ascontiguousarray(a, dtype=np.int32) for a in adj]
+    return dict(L=L, sizes=np.array([len(a) for a in lid], dtype=np.int64), ids=lid, down=ldn, adj=ladj,
+                attempts=np.zeros(L + 1, np.int32), M=M, Mmax=Mmax, seed=seed, metric=metric, graph=graph)
+
+
 TAG_INSERT = 0x494E5352  # "INSR": layer promotion coin of an inserted point (App. C, Insert)
 
 

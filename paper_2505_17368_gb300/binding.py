@@ -69,6 +69,13 @@ class HennError(RuntimeError):
         self.status = status
 
 
+def _check_rows(Q, d):
+    """Queries must be a 2-D array of rows of the index's dimension: the
+    library reads nq * d floats from the buffer."""
+    if len(Q.shape) != 2 or Q.shape[1] != d:
+        raise HennError(1, f"queries must be a 2-D array of shape (nq, {d}), got {tuple(Q.shape)}")
+
+
 class BuildParams(C.Structure):
     _fields_ = [
         ("struct_size", C.c_uint32),
@@ -374,6 +381,7 @@ class Index:
             Q = Q.to(torch.float32).contiguous()
         else:
             Q = np.ascontiguousarray(Q, dtype=np.float32)
+        _check_rows(Q, self.d)
         nq = Q.shape[0]
         kmax = int(k) if np.isscalar(k) else int(np.max(np.asarray(k.cpu() if _is_torch(k) else k)))
         stride = int(out_stride or kmax)
@@ -437,6 +445,7 @@ def search_host_noalloc(index: "Index", Q, k=10, ef=64, ef_upper=1, out_stride=N
     """henn_search_host_noalloc: host queries and results, no device
     allocation (scratch in the library's fixed 16 MiB device array)."""
     Q = np.ascontiguousarray(Q, dtype=np.float32)
+    _check_rows(Q, index.d)
     nq = Q.shape[0]
     stride = int(out_stride or k)
     ids = np.empty((nq, stride), np.int64)
@@ -468,6 +477,7 @@ class Server:
 
     def submit(self, Q, k=10, ef=64, keys=None):
         Q = np.ascontiguousarray(Q, dtype=np.float32)
+        _check_rows(Q, self._index.d)
         kk = None if keys is None else np.ascontiguousarray(keys, dtype=np.uint64)
         rid = C.c_int64()
         st = load().henn_serve_submit(self._h, C.c_void_p(Q.ctypes.data), Q.shape[0], int(k), int(ef),

@@ -886,14 +886,9 @@ extern "C" henn_status henn_insert(henn_index* ix, const float* X, int64_t n_new
 
 namespace {
 
-// Visited-table slots per query: at least 1024 and about 8 per beam entry;
-// the table may forget entries without changing results, so it is sized
-// for occupancy (shared memory per warp), not for completeness.
-int pick_hash_bits(int ef_cap) {
-  int hb = 10;
-  while (hb < 12 && (1 << hb) < ef_cap * 8) ++hb;
-  return hb;
-}
+// Visited-table slots per query (search_hash_bits): sized for occupancy,
+// since the table may forget entries without changing results.
+int pick_hash_bits(int ef_cap) { return search_hash_bits(ef_cap); }
 
 }  // namespace
 
@@ -969,12 +964,9 @@ constexpr int64_t kDenseExactMax = 16384;
 constexpr double kDenseExactBytes = 1.0 * (1 << 30);
 
 int persistent_grid(int device, int warps, size_t smem) {
-  int sms = 0;
-  CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device));
-  int per_sm = (int)((200 * 1024) / (smem > 0 ? smem : 1));
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 64 / warps) per_sm = 64 / warps;
-  return sms * per_sm;
+  int grid = 0;
+  CK(search_persistent_grid(device, warps, smem, &grid));
+  return grid;
 }
 
 }  // namespace
@@ -1043,11 +1035,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
               "exact_method TILES / SCAN with descend_all needs the exact layer's width (ef_upper, or ef_l1 on layer 1) <= 32");
     // beam capacity of a query: the power of two holding its widest list
     auto cap_of = [&](int32_t kq, int32_t efq) {
-      int nd = std::max(std::max(kq, efq), std::max((int)sp.ef_upper, (int)sp.ef_l1));
-      if (rerank) nd = std::max(nd, std::min(efq, sp.rerank_mult * kq));
-      int c = 32;
-      while (c < nd) c <<= 1;
-      return c;
+      return search_beam_cap(kq, efq, sp.ef_upper, sp.ef_l1, rerank != 0, sp.rerank_mult);
     };
     const int ef_cap = cap_of(kmax, efmax);
     int hb = sp.hash_bits > 0 ? sp.hash_bits : pick_hash_bits(ef_cap);

@@ -30,6 +30,7 @@
 
 #include <atomic>
 #include <cstddef>
+#include <cstdlib>
 #include <cstring>
 
 #include "common.cuh"
@@ -85,9 +86,10 @@ __device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
 // Bounded wait for the phase with the given parity; false on timeout.  Each
 // try_wait may suspend the thread for up to 20 us (the suspend-time hint)
 // instead of returning at once, so waiting warps do not take issue slots.
-__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag) {
+__device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, volatile int* abort_flag,
+                                          long long limit) {
   const uint32_t addr = smem_u32(bar);
-  for (long long i = 0; i < kSpinLimit; ++i) {
+  for (long long i = 0; i < limit; ++i) {
     uint32_t done;
     asm volatile(
         "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n selp.u32 %0, 1, 0, p;\n}\n"
@@ -201,7 +203,7 @@ __global__ void __launch_bounds__(192, 1)
                    const __grid_constant__ CUtensorMap to_d,
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
-                   int32_t nsplit, int32_t* __restrict__ err) {
+                   int32_t nsplit, int32_t* __restrict__ err, long long spin_limit, int32_t hold) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -247,8 +249,10 @@ __global__ void __launch_bounds__(192, 1)
   volatile int* abort_flag = &sm.abort;
 
   if (warp == 0) {
-    // ---------------- TMA producer
-    if (lane == 0) {
+    // ---------------- TMA producer (with `hold` it issues nothing, so the
+    // other warps' waits run out with no copy in flight: the host's way to
+    // test the timeout path)
+    if (lane == 0 && !hold) {
       tc::mbar_expect_tx(&sm.afull, (uint32_t)(2 * kc * A_CHUNK));
       for (int c = 0; c < kc; ++c) {
         tc::tma_load_2d(sm.a[c], &ta_hi, &sm.afull, c * BK, (int)r0);
@@ -261,7 +265,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int j = 0; j < chunks_per_tile && ok; ++j, ++it) {
           const int st = (int)(it % NS);
           const uint32_t ph = (uint32_t)((it / NS) & 1);
-          if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag)) {
+          if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag, spin_limit)) {
             ok = false;
             break;
           }
@@ -278,12 +282,12 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      bool ok = tc::mbar_wait(&sm.afull, 0, abort_flag);
+      bool ok = tc::mbar_wait(&sm.afull, 0, abort_flag, spin_limit);
       long long it = 0;
       for (int lt = 0; lt < nt && ok; ++lt) {
         const int as = lt & 1;
         const uint32_t aph = (uint32_t)((lt >> 1) & 1);
-        if (!tc::mbar_wait(&sm.tempty[as], aph ^ 1u, abort_flag)) {
+        if (!tc::mbar_wait(&sm.tempty[as], aph ^ 1u, abort_flag, spin_limit)) {
           ok = false;
           break;
         }
@@ -293,7 +297,7 @@ __global__ void __launch_bounds__(192, 1)
         for (int j = 0; j < chunks_per_tile; ++j, ++it) {
           const int st = (int)(it % NS);
           const uint32_t ph = (uint32_t)((it / NS) & 1);
-          if (!tc::mbar_wait(&sm.full[st], ph, abort_flag)) {
+          if (!tc::mbar_wait(&sm.full[st], ph, abort_flag, spin_limit)) {
             ok = false;
             break;
           }
@@ -349,7 +353,7 @@ __global__ void __launch_bounds__(192, 1)
       const int t = t0 + lt;
       const int as = lt & 1;
       const uint32_t aph = (uint32_t)((lt >> 1) & 1);
-      if (!tc::mbar_wait(&sm.tfull[as], aph, abort_flag)) {
+      if (!tc::mbar_wait(&sm.tfull[as], aph, abort_flag, spin_limit)) {
         ok = false;
         break;
       }
@@ -503,6 +507,23 @@ __global__ void k_split_bf16(const float* __restrict__ x, int64_t s, int32_t dpa
   }
 }
 
+// Wait bound of the pipeline's mbarrier waits and the producer hold, from
+// the environment: HENN_TILE_SPIN_LIMIT (iterations of a try_wait that may
+// suspend up to 20 us; default and maximum kSpinLimit) and
+// HENN_TILE_HOLD_LOADS=1 (the producer issues no copy).  Together they make
+// the waits run out on purpose, with nothing in flight, so that tests can
+// check that a timeout comes back as an error status and leaves the
+// context usable.
+static void wait_policy(long long* spin_limit, int32_t* hold) {
+  *spin_limit = kSpinLimit;
+  *hold = 0;
+  if (const char* e = std::getenv("HENN_TILE_SPIN_LIMIT")) {
+    const long long v = std::atoll(e);
+    if (v >= 1 && v < kSpinLimit) *spin_limit = v;
+  }
+  if (const char* e = std::getenv("HENN_TILE_HOLD_LOADS")) *hold = std::atoi(e) != 0;
+}
+
 static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
   if (!fn) {
@@ -567,8 +588,11 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   const int64_t nrb = (s + BM - 1) / BM;
   CUtensorMap none;  // no matrix output in modes 0 and 1
   std::memset(&none, 0, sizeof(none));
+  long long spin_limit;
+  int32_t hold;
+  wait_policy(&spin_limit, &hold);
   k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out,
-                                                   nullptr, 0, 1, err);
+                                                   nullptr, 0, 1, err, spin_limit, hold);
   return cudaGetLastError();
 }
 
@@ -624,8 +648,12 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   CUtensorMap mo;
   std::memset(&mo, 0, sizeof(mo));
   if (out_d && !make_store_map(&mo, out_d, na, ldo)) return cudaErrorInvalidValue;
+  long long spin_limit;
+  int32_t hold;
+  wait_policy(&spin_limit, &hold);
   k_tile_topk_tc<<<(unsigned)(nrb * nsplit), 192, smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
-                                                             out_d ? 3 : 2, out, out_d, ldo, nsplit, err);
+                                                             out_d ? 3 : 2, out, out_d, ldo, nsplit, err, spin_limit,
+                                                             hold);
   return cudaGetLastError();
 }
 

@@ -101,17 +101,13 @@ extern "C" henn_status henn_search_host_noalloc(const henn_index* idx, const flo
   int64_t* dids = reinterpret_cast<int64_t*>(base + id_off);
   float* dd = reinterpret_cast<float*>(base + d_off);
 
-  // beam capacity and visited table as henn_search chooses them
-  const int rerank = a.rerank;
-  int need = k > ef ? k : ef;
-  if (ef_upper > need) need = ef_upper;
-  const int rr = ef < 4 * k ? ef : 4 * k;
-  if (rerank && rr > need) need = rr;
-  int ef_cap = 32;
-  while (ef_cap < need) ef_cap <<= 1;
-  int hb = 10;
-  while (hb < 13 && (1 << hb) < ef_cap * 16) ++hb;
-  a.rerank_mult = 4;
+  // beam capacity, visited table and grid by the rules henn_search uses
+  // (search.cuh), with henn_search's default rerank multiplier
+  henn_search_params defaults;
+  henn_search_params_default(&defaults);
+  const int ef_cap = search_beam_cap(k, ef, ef_upper, 0, a.rerank != 0, defaults.rerank_mult);
+  const int hb = search_hash_bits(ef_cap);
+  a.rerank_mult = defaults.rerank_mult;
   a.Q = dq;
   a.nq = nq;
   a.kq = nullptr;
@@ -129,16 +125,13 @@ extern "C" henn_status henn_search_host_noalloc(const henn_index* idx, const flo
   a.stats = nullptr;
   a.counter = counter;
 
-  int sms = 0;
-  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
-  if (e != cudaSuccess) return fail(HENN_ERR_CUDA, cudaGetErrorString(e));
   const int warps = kSearchWarps;
   const size_t smem = search_warp_smem(ef_cap, hb, a.dpad) * warps;
-  int per_sm = (int)((200 * 1024) / smem);
-  if (per_sm < 1) per_sm = 1;
-  if (per_sm > 64 / warps) per_sm = 64 / warps;
-  long long blocks = (nq + warps - 1) / warps;
-  int grid = (int)((long long)sms * per_sm < blocks ? (long long)sms * per_sm : blocks);
+  int grid = 0;
+  cudaError_t e = search_persistent_grid(device, warps, smem, &grid);
+  if (e != cudaSuccess) return fail(HENN_ERR_CUDA, cudaGetErrorString(e));
+  const long long blocks = (nq + warps - 1) / warps;
+  if (blocks < grid) grid = (int)blocks;
 
   // the work counter must start at zero on every call; everything else is
   // overwritten before it is read

@@ -1034,6 +1034,31 @@ size_t search_warp_smem(int ef_cap, int hash_bits, int dpad) {
   return (b + 15) & ~(size_t)15;
 }
 
+int search_beam_cap(int k, int ef, int ef_upper, int ef_l1, bool rerank, int rerank_mult) {
+  int need = max(max(k, ef), max(ef_upper, ef_l1));
+  if (rerank) need = max(need, min(ef, rerank_mult * k));
+  int c = 32;
+  while (c < need) c <<= 1;
+  return c;
+}
+
+int search_hash_bits(int ef_cap) {
+  int hb = 10;
+  while (hb < 12 && (1 << hb) < ef_cap * 8) ++hb;
+  return hb;
+}
+
+cudaError_t search_persistent_grid(int device, int warps, size_t smem, int* grid) {
+  int sms = 0;
+  const cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) return e;
+  int per_sm = (int)((200 * 1024) / (smem > 0 ? smem : 1));
+  if (per_sm < 1) per_sm = 1;
+  if (per_sm > 64 / warps) per_sm = 64 / warps;
+  *grid = sms * per_sm;
+  return cudaSuccess;
+}
+
 template <typename VT, int DMAX>
 static cudaError_t launch_t(const SearchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
   auto kern = k_search<VT, DMAX>;

@@ -90,6 +90,18 @@ struct GreedyProbeArgs {
 };
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+// Launch shape of k_search, shared by every entry point that runs it.
+// Beam capacity of a query: the power of two (at least 32) that holds its
+// widest list -- k, ef, the upper-layer widths, and with a rerank the
+// min(ef, rerank_mult * k) reranked entries.
+int search_beam_cap(int k, int ef, int ef_upper, int ef_l1, bool rerank, int rerank_mult);
+// log2 of the visited-table slots per query for a beam capacity: at least
+// 2^10 and about 8 per beam entry, at most 2^12 (the table may forget
+// entries without changing results, so it is sized for occupancy).
+int search_hash_bits(int ef_cap);
+// Blocks of `warps` warps using `smem` bytes of shared memory each that
+// stay resident together on every SM of `device` (a persistent launch).
+cudaError_t search_persistent_grid(int device, int warps, size_t smem, int* grid);
 // Exact-layer preparation for exact_method 1 (tile candidates).
 // Layer rows in traversal precision, as FP32 (dequantised BF16 / FP8 codes).
 cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s, int storage, int32_t dpad, float* out,

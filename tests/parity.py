@@ -126,3 +126,19 @@ def returned_distance_error(X, Q, ids, dists, metric=0):
         if err.size:
             worst = max(worst, float(err.max()))
     return worst
+
+
+def oracle_view(gidx, metric=0, seed=0):
+    """The GPU-built hierarchy (layers, down pointers, adjacency) in the
+    oracle's index form, so that the oracle searches the same graphs."""
+    import oracle as O
+
+    info = gidx.info()
+    ids, down, adj = [None], [None], []
+    for i in range(info["L"] + 1):
+        lay = gidx.layer(i)
+        if i >= 1:
+            ids.append(lay["ids"].astype(np.int64))
+            down.append(lay["down"].astype(np.int64))
+        adj.append(lay["adj"])
+    return O.from_layers(ids, down, adj, metric=metric, seed=seed, M=info["M"], Mmax=info["Mmax"])

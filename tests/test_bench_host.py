@@ -1,11 +1,54 @@
-"""Host logic of bench.py (no GPU): the sweep's beam entries and the lookup of
-the search kernel's DRAM bytes in the committed ncu summary."""
+"""Host logic of bench.py (no GPU): the beam entries, the FP64 ground truth
+and recall scoring, and the lookup of the search kernel's DRAM bytes in the
+committed ncu summary."""
 from __future__ import annotations
 
 import hashlib
 import os
 
+import numpy as np
+from scipy.spatial.distance import cdist
+
 import bench
+import synth
+
+
+def test_default_and_walk_beams():
+    ef, efu, da, l1, xu, xm, rm = bench.DEFAULT_BEAM
+    assert ef >= bench.K and xm in (0, 1, 2) and rm >= 1
+    assert not (xm != 0 and da and efu > 32)
+    b = bench._beam(bench.DEFAULT_BEAM, [1000, 100, 37, 5])
+    assert b[4] == 37 and all(isinstance(v, int) for v in b)
+    assert bench._beam(bench.DEFAULT_BEAM, [1000, 100])[4] == 0  # no layer 2: no exact layer
+    for entry in bench.WALK_SWEEP:
+        assert entry[3] == 0  # the walk-only figure uses no exact layer
+
+
+def test_fp64_ground_truth_matches_brute_force():
+    """fp64_bruteforce (chunked, FP64 dot-product candidates re-ordered by
+    direct differences) gives scipy's exact k nearest, ties by id; the
+    re-ranking of a candidate pool that holds them gives the same."""
+    X = synth.uniform_cube(5000, 12, seed=3)
+    Q = synth.uniform_cube(60, 12, seed=4)
+    X[17] = X[5]  # an exact tie: the smaller id first
+    Q[0] = X[5]
+    D = cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    want = np.array([np.lexsort((np.arange(len(X)), D[q]))[:10] for q in range(len(Q))])
+    got_i, got_d = bench.fp64_bruteforce(X, Q, 10, pool=32, chunk=1300)
+    assert np.array_equal(got_i, want)
+    assert np.allclose(got_d, np.take_along_axis(D, want, 1), rtol=1e-12)
+    pool = np.array([np.argsort(D[q], kind="stable")[:40] for q in range(len(Q))])[:, ::-1].copy()
+    assert np.array_equal(bench.rerank_fp64(X, Q, pool, 10)[0], want)
+
+
+def test_recall_fp64_counts_ties():
+    X = np.array([[0.0], [1.0], [-1.0], [2.0], [3.0]], np.float32)
+    Q = np.array([[0.0]], np.float32)
+    gt_i, gt_d = bench.fp64_bruteforce(X, Q, 2, pool=5)
+    assert gt_i.tolist() == [[0, 1]]
+    assert bench.recall_fp64(X, Q, np.array([[0, 2]]), gt_i, gt_d) == 1.0  # -1 ties with the 2nd
+    assert bench.recall_fp64(X, Q, np.array([[0, 3]]), gt_i, gt_d) == 0.5
+    assert bench.recall_fp64(X, Q, np.array([[4, -1]]), gt_i, gt_d) == 0.0
 
 
 def test_sweep_entries_are_well_formed():

@@ -11,6 +11,7 @@ import paper_2505_17368_gb300 as H  # noqa: E402
 import synth  # noqa: E402
 
 from test_gpu_parity import DEV, _gpu_index, _graph_parity, _layers_equal  # noqa: E402
+from tests import parity as P  # noqa: E402
 
 pytestmark = pytest.mark.gpu
 
@@ -49,14 +50,14 @@ def test_delete_parity(storage):
     """Delete as tombstones: deleted points never come back, and recall
     against the live points' exact neighbours tracks the oracle's."""
     X = synth.uniform_cube(6000, 16, seed=43)
-    Q = synth.uniform_cube(300, 16, seed=44)
+    Q = synth.uniform_cube(1500, 16, seed=44)
     st = H.F32 if storage == "f32" else H.BF16
     oidx = O.build_index(X, seed=9)
     gidx = _gpu_index(X, seed=9, storage=st)
     dead = np.zeros(len(X), bool)
     dead[::4] = True
     gi_all, _ = O.bruteforce(X, Q, 1)
-    dead[gi_all[:100, 0]] = True  # some queries lose their nearest point
+    dead[gi_all[:400, 0]] = True  # some queries lose their nearest point
     gidx.delete(np.nonzero(dead)[0][: len(np.nonzero(dead)[0]) // 2])
     gidx.delete(np.nonzero(dead)[0][len(np.nonzero(dead)[0]) // 2:])
     ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64)
@@ -67,5 +68,6 @@ def test_delete_parity(storage):
     li, ld = O.bruteforce(X[live], Q, 10)
     gt = live[li]
     rec = lambda found: np.mean([len(set(found[q]) & set(gt[q])) / 10 for q in range(len(Q))])  # noqa: E731
-    assert abs(rec(ids) - rec(oi)) <= 0.02, (rec(ids), rec(oi))
+    print(f"delete {storage}: gpu {rec(ids):.4f} oracle {rec(oi):.4f}")
+    assert abs(rec(ids) - rec(oi)) <= P.RECALL_TOL + 1e-12, (rec(ids), rec(oi))
     assert np.all(np.diff(dd.cpu().numpy(), axis=1) >= 0)

@@ -340,47 +340,83 @@ def test_search_uneven_k_ef(uniform10k):
     # oracle with the same per-query parameters
     gi, gd = O.bruteforce(X, Q, 37)
     oi, _, _ = O.search(oidx, X, Q, k=k, ef=ef, out_stride=40)
+    rg_all, ro_all = [], []
     for kk in [1, 5, 10, 37]:
         sel = k == kk
-        rg = O.recall_at_k(ids[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk]).mean()
-        ro = O.recall_at_k(oi[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk]).mean()
-        assert abs(rg - ro) <= 0.02, (kk, rg, ro)  # per-k subsets of ~250 queries
+        rg = O.recall_at_k(ids[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk])
+        ro = O.recall_at_k(oi[sel][:, :kk], gi[sel][:, :kk], gd[sel][:, :kk])
+        rg_all.append(rg)
+        ro_all.append(ro)
+        assert abs(rg.mean() - ro.mean()) <= 0.01, (kk, rg.mean(), ro.mean())  # per-k subsets of ~250 queries
+    # over the whole batch: the parity tolerance
+    assert abs(np.concatenate(rg_all).mean() - np.concatenate(ro_all).mean()) <= P.RECALL_TOL + 1e-12
+    assert np.mean([np.array_equal(ids[q, :k[q]], oi[q, :k[q]]) for q in range(len(Q))]) >= 0.97
+
+
+# Recall gap of the precision forms against the FP64 oracle on the same
+# graphs, both directions.  BF16 keeps the 0.5-point parity tolerance; FP8
+# E4M3 (3 fraction bits, about 6 % per element) reorders the beam itself,
+# and the stated figure for it is 3 points at this beam width.
+PRECISION_TOL = {"bf16": P.RECALL_TOL, "fp8": 0.03}
 
 
 @pytest.mark.parametrize("storage", ["bf16", "fp8"])
 def test_search_precision_forms(storage):
     """BF16 / FP8-E4M3 traversal with exact FP32 rerank: returned distances
-    are FP32-exact, recall tracks the FP64 oracle."""
+    are FP32-exact, recall tracks the FP64 oracle searching the same
+    graphs (2,000 queries)."""
     Xs, rng_ = synth.gaussian_mixture(20000, 128, 200, seed=0, rescale_to_255=True)
-    Q, _ = synth.gaussian_mixture(500, 128, 200, seed=1, rescale_from=rng_, rescale_to_255=True)
+    Q, _ = synth.gaussian_mixture(2000, 128, 200, seed=1, rescale_from=rng_, rescale_to_255=True)
     st = H.BF16 if storage == "bf16" else H.FP8E4M3
     gidx = _gpu_index(Xs, storage=st, seed=1)
     gi, gd = O.bruteforce(Xs, Q, 10)
-    oidx = O.build_index(Xs, seed=1)
+    oidx = P.oracle_view(gidx, seed=1)
     ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64, ef_upper=16)
     oi, _, _ = O.search(oidx, Xs, Q, k=10, ef=64, ef_upper=16)
     ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
     assert P.returned_distance_error(Xs, Q, ids, dd) <= P.DIST_RTOL
     rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
-    # BF16 traversal tracks the FP64 oracle; E4M3 (3 fraction bits) loses
-    # a few points of recall at the same beam width (stated per config)
-    tol = 0.01 if storage == "bf16" else 0.06
-    assert rg >= ro - tol, (storage, rg, ro)
+    print(f"{storage}: gpu {rg:.4f} oracle {ro:.4f}")
+    assert abs(rg - ro) <= PRECISION_TOL[storage] + 1e-12, (storage, rg, ro)
 
 
 def test_search_angular():
     X, _ = synth.gaussian_mixture(6000, 96, 50, seed=0, normalise=True)
-    Q, _ = synth.gaussian_mixture(300, 96, 50, seed=1, normalise=True)
+    Q, _ = synth.gaussian_mixture(2000, 96, 50, seed=1, normalise=True)
     oidx = O.build_index(X, metric=O.ANGULAR, seed=8)
+    gi, gd = O.bruteforce(X, Q, 10, metric=O.ANGULAR)
+    oi, _, _ = O.search(oidx, X, Q, k=10, ef=64)
     for st in (H.F32, H.BF16):
         gidx = _gpu_index(X, metric=H.ANGULAR, storage=st, seed=8)
-        gi, gd = O.bruteforce(X, Q, 10, metric=O.ANGULAR)
+        _layers_equal(gidx, oidx)
         ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64)
-        oi, _, _ = O.search(oidx, X, Q, k=10, ef=64)
         ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
         assert P.returned_distance_error(X, Q, ids, dd, metric=1) <= P.DIST_RTOL
         rg, ro = _recall(ids, gi, gd), _recall(oi, gi, gd)
-        assert abs(rg - ro) <= (P.RECALL_TOL if st == H.F32 else 0.01) + 1e-12, (st, rg, ro)
+        print(f"angular storage {st}: gpu {rg:.4f} oracle {ro:.4f}")
+        assert abs(rg - ro) <= P.RECALL_TOL + 1e-12, (st, rg, ro)
+
+
+@pytest.mark.parametrize("lam", [4.0, 256.0])
+def test_exponential_workload_parity(lam):
+    """The paper's own synthetic data (App. G: i.i.d. exponential
+    coordinates), d = 32: layers bit-exact, graphs within the near-tie
+    rule, and the plain greedy descent of Alg. 4 with the layer-0 beam
+    within 0.5 points of the oracle's recall."""
+    X = synth.exponential(20000, 32, lam, seed=0)
+    Q = synth.exponential(1000, 32, lam, seed=1)
+    oidx = O.build_index(X, seed=0)
+    gidx = _gpu_index(X, seed=0)
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+    gi, gd = O.bruteforce(X, Q, 10)
+    for ef in (16, 64):
+        ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=ef)
+        oi, _, _ = O.search(oidx, X, Q, k=10, ef=ef)
+        ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
+        assert abs(_recall(ids, gi, gd) - _recall(oi, gi, gd)) <= P.RECALL_TOL + 1e-12, ef
+        assert P.returned_distance_error(X, Q, ids, dd) <= P.DIST_RTOL
+        assert np.mean(np.all(ids == oi, axis=1)) >= 0.98
 
 
 # ------------------------------------------------------- edge cases
@@ -487,17 +523,3 @@ def _row_compare_fullsize(g_row, o_row, X, ids, p):
         return edges, 0, 0, None
     _, ex, un, _ = P._row_rule(g, o, X, ids, p, 0)
     return edges, ex, un, None
-
-
-def test_full_size_search_sampled(mixture1m):
-    """Search on 1M x 128: FP64 ground truth for 300 sampled queries,
-    returned distances within 1e-4 of FP64, recall@10 of the benchmarked
-    configuration >= 0.95."""
-    X, Q, gidx = mixture1m
-    sel = np.random.default_rng(12).choice(len(Q), 300, replace=False)
-    Qs = Q[sel]
-    gi, gd = O.bruteforce(X, Qs, 10)
-    ids, dd, _ = gidx.search(torch.from_numpy(Qs).to(DEV), k=10, ef=128, ef_upper=32)
-    ids, dd = ids.cpu().numpy(), dd.cpu().numpy()
-    assert P.returned_distance_error(X, Qs, ids, dd) <= P.DIST_RTOL
-    assert O.recall_at_k(ids, gi, gd).mean() >= 0.9

@@ -32,10 +32,15 @@ def _wait(srv, rid, timeout=60.0):
         time.sleep(0.0005)
 
 
-@pytest.fixture(scope="module")
-def index_and_queries():
+def _data():
     X, rng = synth.gaussian_mixture(20000, 64, 100, seed=0, rescale_to_255=True)
     Q, _ = synth.gaussian_mixture(3000, 64, 100, seed=1, rescale_from=rng, rescale_to_255=True)
+    return X, Q
+
+
+@pytest.fixture(scope="module")
+def index_and_queries():
+    X, Q = _data()
     idx = H.Index(torch.from_numpy(X).cuda(), storage=H.BF16, seed=3)
     return idx, Q
 
@@ -103,6 +108,47 @@ def test_alone_equals_in_mix(index_and_queries):
         ids, dd = _wait(srv2, rid)
         assert np.array_equal(ids, results[at][3]) and np.array_equal(dd, results[at][4])
     srv2.close()
+
+
+def test_served_results_track_oracle(index_and_queries):
+    """A mixed stream (batch sizes log-uniform, k in {10, 100}, ef
+    log-uniform in [64, 512]) through the server against the FP64 oracle
+    searching the same GPU-built graphs with each query's own k, ef and
+    entry key: recall@k against FP64 brute force within the parity
+    tolerance over the stream, returned distances within 1e-4 of FP64."""
+    import oracle as O
+    from tests import parity as P
+
+    idx, Q = index_and_queries
+    X, _ = _data()
+    view = P.oracle_view(idx, seed=3)
+    reqs = _requests(len(Q), 7)
+    srv = H.Server(idx, ring_rows=4096, max_requests=32, max_k=100, max_ef=512, ef_upper=16)
+    pending, served = [], {}
+    for at, b, k, ef in reqs:
+        keys = np.arange(at, at + b, dtype=np.uint64) * 7 + 1
+        while (rid := srv.submit(Q[at:at + b], k=k, ef=ef, keys=keys)) is None:
+            for item in list(pending):
+                r = srv.poll(item[0])
+                if r is not None:
+                    served[item[1]] = r
+                    pending.remove(item)
+        pending.append((rid, at))
+    for rid, at in pending:
+        served[at] = _wait(srv, rid)
+    srv.close()
+    gi, gd = O.bruteforce(X, Q, 100)
+    rg, ro = [], []
+    for at, b, k, ef in reqs:
+        ids, dd = served[at]
+        keys = np.arange(at, at + b, dtype=np.uint64) * 7 + 1
+        oi, _, _ = O.search(view, X, Q[at:at + b], k=k, ef=ef, ef_upper=16, keys=keys)
+        rg.append(O.recall_at_k(ids, gi[at:at + b, :k], gd[at:at + b, :k]))
+        ro.append(O.recall_at_k(oi, gi[at:at + b, :k], gd[at:at + b, :k]))
+        assert P.returned_distance_error(X, Q[at:at + b], ids, dd) <= P.DIST_RTOL
+    rg, ro = np.concatenate(rg).mean(), np.concatenate(ro).mean()
+    print(f"served {rg:.4f} oracle {ro:.4f}")
+    assert abs(rg - ro) <= P.RECALL_TOL + 1e-12, (rg, ro)
 
 
 def test_admission_budget_and_errors(index_and_queries):
