@@ -85,7 +85,8 @@ typedef enum { HENN_GRAPH_NSW = 0, HENN_GRAPH_KNN = 1 } henn_graph;
 typedef enum { HENN_SAMPLER_SAMPLING = 0, HENN_SAMPLER_HALVING = 1 } henn_sampler;
 
 /* Engine for the construction distance tiles: AUTO = tcgen05 where it
- * applies (d <= 128, M <= 16), else SIMT FP32. */
+ * applies (M <= 16; rows of up to 128 values keep the row block resident in
+ * shared memory, wider rows stream it slice by slice), else SIMT FP32. */
 typedef enum { HENN_TILES_AUTO = 0, HENN_TILES_SIMT = 1, HENN_TILES_TCGEN05 = 2 } henn_tiles;
 
 /* ------------------------------------------------------------------ build */
@@ -202,8 +203,8 @@ typedef struct {
                                  SORT: per query, every point evaluated and sorted
                                  in the visited table (layer of at most
                                  2^(hash_bits - 1) points; default);
-                                 TILES: one batched distance-tile launch (tcgen05
-                                 for dpad <= 128, else SIMT) gives each query 32
+                                 TILES: one batched distance-tile launch
+                                 (tcgen05) gives each query 32
                                  candidates, rescored in traversal precision and
                                  kept when a tile-error certificate proves them
                                  to hold the set, else a scan of the layer;

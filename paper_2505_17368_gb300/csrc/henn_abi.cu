@@ -406,7 +406,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
   const int32_t mode = ix->graph == HENN_GRAPH_KNN ? 1 : 0;
   const bool tc_ok = tc_tiles_supported(dpad, KP);
   if (p.tiles == HENN_TILES_TCGEN05 && !tc_ok)
-    throw Failure(HENN_ERR_UNSUPPORTED, "tcgen05 tiles need d <= 128 and M <= 16");
+    throw Failure(HENN_ERR_UNSUPPORTED, "tcgen05 tiles need M <= 16");
   const bool use_tc = tc_ok && p.tiles != HENN_TILES_SIMT;
   double tile_u;
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;

@@ -16,12 +16,17 @@
 //
 // Layout of one CTA (192 threads): warp 0 issues TMA loads, warp 1 owns
 // TMEM and issues the MMAs (one thread), warps 2-5 drain the accumulators
-// (TMEM lanes 32*(w%4)..+31 = rows of the 128-row block).  The A block (128
-// rows, hi and lo planes, d <= 128) stays in shared memory; B tiles (256
-// columns x 64 values of one plane) stream through a 3-stage ring.  Two
-// 256-column FP32 accumulators in TMEM let the epilogue of tile t overlap
-// the MMAs of tile t+1.  Every wait is bounded; a timeout sets an error
-// flag and the CTA releases its TMEM and returns.
+// (TMEM lanes 32*(w%4)..+31 = rows of the 128-row block).  Rows of at most
+// 128 values: the A block (128 rows, hi and lo planes) stays in shared
+// memory and B tiles (256 columns x 64 values of one plane) stream through
+// a 3-stage ring.  Wider rows (up to 1024 values): the A block no longer
+// fits, so each 64-wide slice of the tile arrives as three items of a
+// 5-stage ring -- the slice of A (hi and lo planes, 16 KB each), then B hi,
+// then B lo (32 KB each) -- and the A block is read again for every tile
+// (from L2, where one CTA's block stays hot).  Two 256-column FP32
+// accumulators in TMEM let the epilogue of tile t overlap the MMAs of tile
+// t+1.  Every wait is bounded; a timeout sets an error flag and the CTA
+// releases its TMEM and returns.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -32,6 +37,7 @@
 #include <cstddef>
 #include <cstdlib>
 #include <cstring>
+#include <type_traits>
 
 #include "common.cuh"
 #include "kernels.cuh"
@@ -43,17 +49,20 @@ namespace tc {
 constexpr int BM = 128;          // rows per block (TMEM lanes)
 constexpr int BN = 256;          // columns per tile (UMMA N)
 constexpr int BK = 64;           // BF16 values per 128-byte swizzle row
-constexpr int NS = 3;            // B pipeline stages
+constexpr int NS = 3;            // B pipeline stages (resident A)
+constexpr int NS_STR = 5;        // pipeline stages (streamed A)
 constexpr int A_CHUNK = BM * BK * 2;  // 16 KB
 constexpr int B_CHUNK = BN * BK * 2;  // 32 KB
-constexpr int MAX_KC = 2;        // dpad <= 128: at most 2 chunks of 64 per plane
+constexpr int MAX_KC_RES = 2;    // resident A: dpad <= 128, at most 2 chunks of 64 per plane
+constexpr int MAX_KC = 16;       // streamed A: dpad <= 1024
 constexpr int KP = 32;
 constexpr int S_LD = 33;
 constexpr long long kSpinLimit = 1ll << 18;  // x 20 us hint: seconds at most
 
-struct Smem {
+// Resident A (rows of at most 128 values).
+struct SmemRes {
   // 1024-byte aligned operand buffers first
-  uint8_t a[2 * MAX_KC][A_CHUNK];  // hi chunks then lo chunks
+  uint8_t a[2 * MAX_KC_RES][A_CHUNK];  // hi chunks then lo chunks
   uint8_t b[NS][B_CHUNK];
   // running top-KP of each row: a max-heap of keys, 1-based (children of
   // p at 2p and 2p + 1, so a sibling pair is one 16-byte load), root = the
@@ -62,6 +71,19 @@ struct Smem {
   alignas(16) float ncol[4][BN];   // column norms of the current tile, one copy per epilogue warp
   float s[4][32][S_LD];            // epilogue transposition, one slab per warp
   uint64_t full[NS], empty[NS], tfull[2], tempty[2], afull;
+  uint32_t tmem_base;
+  int abort;
+};
+
+// Streamed A (wider rows): a ring of 32 KB stages, each holding the A slice
+// of one 64-wide slice (hi plane, then lo plane) or one plane of a B slice;
+// the rest as above.
+struct SmemStr {
+  uint8_t ring[NS_STR][B_CHUNK];
+  uint64_t heap[BM][KP + 2];
+  alignas(16) float ncol[4][BN];
+  float s[4][32][S_LD];
+  uint64_t full[NS_STR], empty[NS_STR], tfull[2], tempty[2], afull;
   uint32_t tmem_base;
   int abort;
 };
@@ -197,6 +219,7 @@ __device__ __forceinline__ void heap_replace(uint64_t* heap, uint64_t key) {
 
 using namespace tc;
 
+template <bool kStream>
 __global__ void __launch_bounds__(192, 1)
     k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
@@ -204,6 +227,8 @@ __global__ void __launch_bounds__(192, 1)
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
                    int32_t nsplit, int32_t* __restrict__ err, long long spin_limit, int32_t hold) {
+  using Smem = typename std::conditional<kStream, SmemStr, SmemRes>::type;
+  constexpr int NST = kStream ? NS_STR : NS;
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -223,7 +248,7 @@ __global__ void __launch_bounds__(192, 1)
   const int chunks_per_tile = 2 * kc;  // (B_hi, B_lo) per 64-wide slice
 
   if (threadIdx.x == 0) {
-    for (int i = 0; i < NS; ++i) {
+    for (int i = 0; i < NST; ++i) {
       tc::mbar_init(&sm.full[i], 1);
       tc::mbar_init(&sm.empty[i], 1);
     }
@@ -253,25 +278,50 @@ __global__ void __launch_bounds__(192, 1)
     // other warps' waits run out with no copy in flight: the host's way to
     // test the timeout path)
     if (lane == 0 && !hold) {
-      tc::mbar_expect_tx(&sm.afull, (uint32_t)(2 * kc * A_CHUNK));
-      for (int c = 0; c < kc; ++c) {
-        tc::tma_load_2d(sm.a[c], &ta_hi, &sm.afull, c * BK, (int)r0);
-        tc::tma_load_2d(sm.a[MAX_KC + c], &ta_lo, &sm.afull, c * BK, (int)r0);
-      }
       long long it = 0;
       bool ok = true;
-      for (int lt = 0; lt < nt && ok; ++lt) {
-        const int t = t0 + lt;
-        for (int j = 0; j < chunks_per_tile && ok; ++j, ++it) {
-          const int st = (int)(it % NS);
-          const uint32_t ph = (uint32_t)((it / NS) & 1);
-          if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag, spin_limit)) {
-            ok = false;
-            break;
+      if constexpr (!kStream) {
+        tc::mbar_expect_tx(&sm.afull, (uint32_t)(2 * kc * A_CHUNK));
+        for (int c = 0; c < kc; ++c) {
+          tc::tma_load_2d(sm.a[c], &ta_hi, &sm.afull, c * BK, (int)r0);
+          tc::tma_load_2d(sm.a[MAX_KC_RES + c], &ta_lo, &sm.afull, c * BK, (int)r0);
+        }
+        for (int lt = 0; lt < nt && ok; ++lt) {
+          const int t = t0 + lt;
+          for (int j = 0; j < chunks_per_tile && ok; ++j, ++it) {
+            const int st = (int)(it % NST);
+            const uint32_t ph = (uint32_t)((it / NST) & 1);
+            if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag, spin_limit)) {
+              ok = false;
+              break;
+            }
+            tc::mbar_expect_tx(&sm.full[st], (uint32_t)B_CHUNK);
+            const int slice = j >> 1;
+            tc::tma_load_2d(sm.b[st], (j & 1) ? &tb_lo : &tb_hi, &sm.full[st], slice * BK, t * BN);
           }
-          tc::mbar_expect_tx(&sm.full[st], (uint32_t)B_CHUNK);
-          const int slice = j >> 1;
-          tc::tma_load_2d(sm.b[st], (j & 1) ? &tb_lo : &tb_hi, &sm.full[st], slice * BK, t * BN);
+        }
+      } else {
+        // per slice: the A slice (hi | lo), B hi, B lo, in this order
+        for (int lt = 0; lt < nt && ok; ++lt) {
+          const int t = t0 + lt;
+          for (int j = 0; j < kc && ok; ++j) {
+            for (int part = 0; part < 3; ++part, ++it) {
+              const int st = (int)(it % NST);
+              const uint32_t ph = (uint32_t)((it / NST) & 1);
+              if (!tc::mbar_wait(&sm.empty[st], ph ^ 1u, abort_flag, spin_limit)) {
+                ok = false;
+                break;
+              }
+              if (part == 0) {
+                tc::mbar_expect_tx(&sm.full[st], (uint32_t)(2 * A_CHUNK));
+                tc::tma_load_2d(sm.ring[st], &ta_hi, &sm.full[st], j * BK, (int)r0);
+                tc::tma_load_2d(sm.ring[st] + A_CHUNK, &ta_lo, &sm.full[st], j * BK, (int)r0);
+              } else {
+                tc::mbar_expect_tx(&sm.full[st], (uint32_t)B_CHUNK);
+                tc::tma_load_2d(sm.ring[st], part == 1 ? &tb_hi : &tb_lo, &sm.full[st], j * BK, t * BN);
+              }
+            }
+          }
         }
       }
       if (!ok) {
@@ -282,7 +332,7 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1) {
     // ---------------- MMA issuer
     if (lane == 0) {
-      bool ok = tc::mbar_wait(&sm.afull, 0, abort_flag, spin_limit);
+      bool ok = kStream ? true : tc::mbar_wait(&sm.afull, 0, abort_flag, spin_limit);
       long long it = 0;
       for (int lt = 0; lt < nt && ok; ++lt) {
         const int as = lt & 1;
@@ -294,25 +344,59 @@ __global__ void __launch_bounds__(192, 1)
         tc::fence_after();
         const uint32_t dt = tmem + (uint32_t)(as * BN);
         uint32_t acc = 0;
-        for (int j = 0; j < chunks_per_tile; ++j, ++it) {
-          const int st = (int)(it % NS);
-          const uint32_t ph = (uint32_t)((it / NS) & 1);
-          if (!tc::mbar_wait(&sm.full[st], ph, abort_flag, spin_limit)) {
-            ok = false;
-            break;
-          }
-          tc::fence_after();
-          const int slice = j >> 1;
-          const bool b_is_lo = (j & 1);
+        if constexpr (!kStream) {
+          for (int j = 0; j < chunks_per_tile; ++j, ++it) {
+            const int st = (int)(it % NST);
+            const uint32_t ph = (uint32_t)((it / NST) & 1);
+            if (!tc::mbar_wait(&sm.full[st], ph, abort_flag, spin_limit)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            const int slice = j >> 1;
+            const bool b_is_lo = (j & 1);
 #pragma unroll
-          for (int k = 0; k < BK / 16; ++k) {
-            const uint64_t bd = tc::smem_desc(sm.b[st] + k * 32);
-            // B_hi pairs with A_hi and A_lo; B_lo pairs with A_hi
-            tc::mma_bf16(dt, tc::smem_desc(sm.a[slice] + k * 32), bd, acc);
-            acc = 1;
-            if (!b_is_lo) tc::mma_bf16(dt, tc::smem_desc(sm.a[MAX_KC + slice] + k * 32), bd, 1);
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t bd = tc::smem_desc(sm.b[st] + k * 32);
+              // B_hi pairs with A_hi and A_lo; B_lo pairs with A_hi
+              tc::mma_bf16(dt, tc::smem_desc(sm.a[slice] + k * 32), bd, acc);
+              acc = 1;
+              if (!b_is_lo) tc::mma_bf16(dt, tc::smem_desc(sm.a[MAX_KC_RES + slice] + k * 32), bd, 1);
+            }
+            tc::mma_commit(&sm.empty[st]);
           }
-          tc::mma_commit(&sm.empty[st]);
+        } else {
+          for (int j = 0; j < kc && ok; ++j, it += 3) {
+            const int sa = (int)(it % NST), sh = (int)((it + 1) % NST), sl = (int)((it + 2) % NST);
+            if (!tc::mbar_wait(&sm.full[sa], (uint32_t)((it / NST) & 1), abort_flag, spin_limit) ||
+                !tc::mbar_wait(&sm.full[sh], (uint32_t)(((it + 1) / NST) & 1), abort_flag, spin_limit)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            const uint8_t* a_hi = sm.ring[sa];
+            const uint8_t* a_lo = sm.ring[sa] + A_CHUNK;
+            // B hi pairs with A hi and A lo; its stage is free after these
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k) {
+              const uint64_t bd = tc::smem_desc(sm.ring[sh] + k * 32);
+              tc::mma_bf16(dt, tc::smem_desc(a_hi + k * 32), bd, acc);
+              acc = 1;
+              tc::mma_bf16(dt, tc::smem_desc(a_lo + k * 32), bd, 1);
+            }
+            tc::mma_commit(&sm.empty[sh]);
+            if (!tc::mbar_wait(&sm.full[sl], (uint32_t)(((it + 2) / NST) & 1), abort_flag, spin_limit)) {
+              ok = false;
+              break;
+            }
+            tc::fence_after();
+            // B lo pairs with A hi
+#pragma unroll
+            for (int k = 0; k < BK / 16; ++k)
+              tc::mma_bf16(dt, tc::smem_desc(a_hi + k * 32), tc::smem_desc(sm.ring[sl] + k * 32), 1);
+            tc::mma_commit(&sm.empty[sa]);
+            tc::mma_commit(&sm.empty[sl]);
+          }
         }
         if (!ok) break;
         tc::mma_commit(&sm.tfull[as]);
@@ -566,11 +650,37 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk,
 
 bool tc_tiles_supported(int32_t dpad, int32_t KPv) { return dpad <= BK * MAX_KC && KPv == KP; }
 
-static_assert(sizeof(Smem) + 1024 <= 227 * 1024, "shared memory of one CTA");
-static_assert(sizeof(((Smem*)nullptr)->heap) >= 4 * 8192, "mode 3 store boxes fit in the heap space");
-static_assert(offsetof(Smem, heap) % 1024 == 0, "store boxes 1024-byte aligned");
+static_assert(sizeof(SmemRes) + 1024 <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(SmemStr) + 1024 <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(((SmemRes*)nullptr)->heap) >= 4 * 8192, "mode 3 store boxes fit in the heap space");
+static_assert(offsetof(SmemRes, heap) % 1024 == 0, "store boxes 1024-byte aligned");
+static_assert(offsetof(SmemStr, heap) % 1024 == 0, "store boxes 1024-byte aligned");
+static_assert((2 * A_CHUNK) <= B_CHUNK && A_CHUNK % 1024 == 0, "an A slice (hi | lo) fills one stage");
 
-size_t tc_smem_bytes() { return sizeof(Smem) + 1024; }
+// The kernel variant for kc slices of 64 values per plane, and its shared
+// memory; the dynamic shared-memory attribute is set once per device and
+// variant.
+struct TileVariant {
+  void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const float*, const float*, int64_t,
+             int64_t, int32_t, int32_t, uint64_t*, float*, int64_t, int32_t, int32_t*, long long, int32_t);
+  size_t smem;
+};
+
+static cudaError_t tile_variant(int32_t kc, TileVariant* v) {
+  static std::atomic<bool> attr_set[2][64];
+  const int stream = kc > MAX_KC_RES ? 1 : 0;
+  v->fn = stream ? k_tile_topk_tc<true> : k_tile_topk_tc<false>;
+  v->smem = (stream ? sizeof(SmemStr) : sizeof(SmemRes)) + 1024;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev >= 64 || !attr_set[stream][dev].load()) {
+    e = cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
+    if (e != cudaSuccess) return e;
+    if (dev < 64) attr_set[stream][dev].store(true);
+  }
+  return cudaSuccess;
+}
 
 cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, int32_t dpad, int32_t mode,
                                 uint64_t* out, void* scratch_hi, void* scratch_lo, int32_t* err, cudaStream_t st) {
@@ -582,8 +692,8 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   if (!make_map(&mah, hi, s, dk, BM) || !make_map(&mal, lo, s, dk, BM) || !make_map(&mbh, hi, s, dk, BN) ||
       !make_map(&mbl, lo, s, dk, BN))
     return cudaErrorInvalidValue;
-  const size_t smem = tc_smem_bytes();
-  cudaError_t e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  TileVariant v;
+  cudaError_t e = tile_variant(dk / BK, &v);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (s + BM - 1) / BM;
   CUtensorMap none;  // no matrix output in modes 0 and 1
@@ -591,8 +701,8 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   long long spin_limit;
   int32_t hold;
   wait_policy(&spin_limit, &hold);
-  k_tile_topk_tc<<<(unsigned)nrb, 192, smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out,
-                                                   nullptr, 0, 1, err, spin_limit, hold);
+  v.fn<<<(unsigned)nrb, 192, v.smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out, nullptr,
+                                           0, 1, err, spin_limit, hold);
   return cudaGetLastError();
 }
 
@@ -619,14 +729,9 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  // the attribute outlives the call: set it once per device
-  static std::atomic<bool> attr_set[64];
-  if (dev >= 64 || !attr_set[dev].load()) {
-    e = cudaFuncSetAttribute(k_tile_topk_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)tc_smem_bytes());
-    if (e != cudaSuccess) return e;
-    if (dev < 64) attr_set[dev].store(true);
-  }
-  const size_t smem = tc_smem_bytes();
+  TileVariant v;
+  e = tile_variant(dk / BK, &v);
+  if (e != cudaSuccess) return e;
   const int64_t nrb = (na + BM - 1) / BM;
   // mode 3: split each row block's tiles over nsplit CTAs (one CTA per SM
   // fits), choosing the split with the fewest tile-times over all waves
@@ -651,9 +756,8 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   long long spin_limit;
   int32_t hold;
   wait_policy(&spin_limit, &hold);
-  k_tile_topk_tc<<<(unsigned)(nrb * nsplit), 192, smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
-                                                             out_d ? 3 : 2, out, out_d, ldo, nsplit, err, spin_limit,
-                                                             hold);
+  v.fn<<<(unsigned)(nrb * nsplit), 192, v.smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
+                                                     out_d ? 3 : 2, out, out_d, ldo, nsplit, err, spin_limit, hold);
   return cudaGetLastError();
 }
 
