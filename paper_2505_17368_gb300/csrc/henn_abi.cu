@@ -958,10 +958,11 @@ const henn_index::EntryOps& entry_ops(const henn_index* idx, int32_t li, cudaStr
   return e;
 }
 
-// exact_method TILES: layers up to this size (and matrices up to this many
-// bytes) go through the distance matrix instead of in-epilogue lists
+// exact_method TILES: layers up to this size go through the distance
+// matrix instead of in-epilogue lists, in chunks of whole 128-query blocks
+// whose matrix takes at most a third of L2 (written by the tile launch, read
+// by the selection from L2 and dropped there, so it never reaches DRAM)
 constexpr int64_t kDenseExactMax = 16384;
-constexpr double kDenseExactBytes = 1.0 * (1 << 30);
 
 int persistent_grid(int device, int warps, size_t smem) {
   int grid = 0;
@@ -1154,16 +1155,17 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         // running lists inside the tile epilogue
         const int64_t ldo = (s + 31) / 32 * 32;
         if (s <= kDenseExactMax) {
-          // batches whose matrix exceeds kDenseExactBytes go through it in
-          // chunks of whole 128-query blocks, one matrix buffer reused
-          int64_t qc = (int64_t)(kDenseExactBytes / (4.0 * (double)ldo)) / 128 * 128;
+          int l2 = 0;
+          CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, idx->device));
+          const double chunk_bytes = std::max(8.0 * (1 << 20), (double)l2 / 3.0);
+          int64_t qc = (int64_t)(chunk_bytes / (4.0 * (double)ldo)) / 128 * 128;
           qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
           float* dm = sc.get<float>((size_t)qc * ldo);
           for (int64_t q0 = 0; q0 < nq; q0 += qc) {
             const int64_t cn = std::min<int64_t>(qc, nq - q0);
             CK(launch_tile_cross_tc(static_cast<uint16_t*>(qh) + q0 * dkk, static_cast<uint16_t*>(ql) + q0 * dkk,
                                     qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, st));
-            launch_select_top32(dm, cn, s, ldo, pkeys + q0 * 32, st);
+            launch_select_top32(dm, cn, s, ldo, pkeys + q0 * 32, true, st);
             launches += q0 > 0 ? 2 : 1;
           }
         } else {

@@ -239,19 +239,22 @@ __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t
 // sorted ascending (with expanded flags) and returns its length.
 // nseed > 0: W[0..nseed) already holds sorted, unexpanded entries (the
 // copies of the layer above's candidates) and `entry` is ignored.
+// The layer comes as its arrays and size (not a reference to a descriptor,
+// which would put a memory load before every adjacency-row address).
 template <typename VT, int G, int CPL>
-__device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchunk, int32_t entry, int ef,
-                                    uint64_t* W, int32_t* table, int HB, uint64_t* stage, const float* qs,
-                                    int& evals_out, int& expansions_out, int& evictions_out, int nseed = 0) {
+__device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* vec_, const float* __restrict__ scale,
+                                 int64_t size, int64_t stride, int nchunk, int32_t entry, int ef, uint64_t* W,
+                                 int32_t* table, int HB, uint64_t* stage, const float* qs, int& evals_out,
+                                 int& expansions_out, int& evictions_out, int nseed = 0) {
   const int lane = lane_id();
   const unsigned below = (1u << lane) - 1u;  // lanes under this one
   int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
-  const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
-  const bool bitmap = Ly.size <= ((int64_t)32 << HB);
+  const VT* vec = reinterpret_cast<const VT*>(vec_);
+  const bool bitmap = size <= ((int64_t)32 << HB);
   // the counters stay in registers here (the caller's live in its frame)
   int evals = 0, expansions = 0, evictions = evictions_out;
   auto mark = [&](int32_t id) { return bitmap ? visit_bit(table, id) : visit(table, HB, id, evictions); };
-  const int words = bitmap ? (int)((Ly.size + 31) >> 5) : (1 << HB);
+  const int words = bitmap ? (int)((size + 31) >> 5) : (1 << HB);
   for (int s = lane; s < words; s += 32) table[s] = bitmap ? 0 : -1;
   __syncwarp();
   int nw;
@@ -261,7 +264,7 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
       for (int j = 0; j < nw; ++j) mark((int32_t)key_index(W[j] & kKeyMask));
   } else {
     if (lane == 0) mark(entry);
-    float d0 = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, entry, 1, qs, nchunk);
+    float d0 = rows_dist<VT, G, CPL>(vec, scale, stride, entry, 1, qs, nchunk);
     d0 = __shfl_sync(0xffffffffu, d0, 0);
     ++evals;
     if (lane == 0) W[0] = pack(d0, (uint32_t)entry);
@@ -290,11 +293,11 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     first = pos + 1;
     ++expansions;
     const int32_t c = (int32_t)key_index(e & kKeyMask);
-    int32_t nb = Ly.adj[(int64_t)c * kMmax + lane];
+    int32_t nb = adj[(int64_t)c * kMmax + lane];
     // the next unexpanded entry is the likely next expansion: pull its
     // adjacency line towards the SM while this one is processed
     if (lane == 0 && after >= 0) {
-      const int32_t* nxt = Ly.adj + (int64_t)key_index(W[after] & kKeyMask) * kMmax;
+      const int32_t* nxt = adj + (int64_t)key_index(W[after] & kKeyMask) * kMmax;
       asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
     }
     __syncwarp();
@@ -306,7 +309,7 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
     if (fresh) stage32[__popc(fm & below)] = nb;
     __syncwarp();
     const int32_t packed_id = lane < cnt ? stage32[lane] : -1;
-    float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, packed_id, cnt, qs, nchunk);
+    float dn = rows_dist<VT, G, CPL>(vec, scale, stride, packed_id, cnt, qs, nchunk);
     evals += cnt;
     const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
     uint64_t kk = lane < cnt ? pack(dn, (uint32_t)packed_id) : kEmpty;
@@ -366,17 +369,17 @@ __device__ __noinline__ int beam(const SearchLayer& Ly, int64_t stride, int nchu
 // every point of the layer is evaluated into a running top 32 (warp
 // bitonic merge of each sorted batch of 32).
 template <typename VT, int G, int CPL>
-__device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const SearchLayer& Ly, int64_t stride, int nchunk,
-                                             const float* qs, const uint64_t* pre_row, float pre_qn, int need,
-                                             int& evals) {
+__device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const void* vec_, const float* __restrict__ scale,
+                                             int64_t size, int64_t stride, int nchunk, const float* qs,
+                                             const uint64_t* pre_row, float pre_qn, int need, int& evals) {
   const int lane = lane_id();
-  const VT* vec = reinterpret_cast<const VT*>(Ly.vec);
-  const int s = (int)Ly.size;
+  const VT* vec = reinterpret_cast<const VT*>(vec_);
+  const int s = (int)size;
   if (pre_row && *a.pre_err == 0) {
     const uint64_t tk = pre_row[lane];
     const int cnt = __popc(__ballot_sync(0xffffffffu, tk != kEmpty));
     const int32_t id = tk != kEmpty ? (int32_t)key_index(tk) : 0;
-    const float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, id, cnt, qs, nchunk);
+    const float dn = rows_dist<VT, G, CPL>(vec, scale, stride, id, cnt, qs, nchunk);
     evals += cnt;
     const uint64_t mine = warp_sort_asc(lane < cnt ? pack(dn, (uint32_t)id) : kEmpty);
     bool ok = cnt == s;  // the candidates are the whole layer
@@ -400,7 +403,7 @@ __device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const SearchLa
   uint64_t mine = kEmpty;
   for (int c0 = 0; c0 < s; c0 += 32) {
     const int cnt = min(32, s - c0);
-    const float dn = rows_dist<VT, G, CPL>(vec, Ly.scale, stride, c0 + lane, cnt, qs, nchunk);
+    const float dn = rows_dist<VT, G, CPL>(vec, scale, stride, c0 + lane, cnt, qs, nchunk);
     uint64_t kk = lane < cnt ? pack(dn, (uint32_t)(c0 + lane)) : kEmpty;
     if (!__any_sync(0xffffffffu, kk < shfl64(mine, 31))) continue;
     // the running list and the reversed sorted batch: their element-wise
@@ -551,8 +554,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
     // the host keeps width <= 32 when the candidates seed the next layer
     const bool seeds = a.descend_all && width > 1;
     const int nw = seeds ? min(min(width, 32), (int)Ly.size) : 1;
-    const uint64_t mine =
-        exact_top32<VT, G, CPL>(a, Ly, stride, nchunk, qs, a.exact_method == 1 ? pre_row : nullptr, pre_qn, nw, evals);
+    const uint64_t mine = exact_top32<VT, G, CPL>(a, Ly.vec, Ly.scale, Ly.size, stride, nchunk, qs,
+                                                  a.exact_method == 1 ? pre_row : nullptr, pre_qn, nw, evals);
     if (lane < nw) W[lane] = seeds ? ((mine & 0xFFFFFFFF00000000ull) | (uint32_t)Ly.down[key_index(mine)]) : mine;
     cur = Ly.down[key_index(shfl64(mine, 0))];
     if (seeds) nseed = nw;
@@ -607,8 +610,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
       __syncwarp();
     } else if (width > 1) {
       int ex = 0;
-      int nw = beam<VT, G, CPL>(Ly, stride, nchunk, cur, min(width, EFCAP), W, table, HB, stage, qs, evals, ex,
-                                evictions, nseed);
+      int nw = beam<VT, G, CPL>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, min(width, EFCAP), W, table,
+                                HB, stage, qs, evals, ex, evictions, nseed);
       moves += ex;
       cur = (int32_t)key_index(W[0] & kKeyMask);
       if (a.descend_all) {
@@ -646,8 +649,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 
   // S3: layer-0 beam
   const SearchLayer B = a.layers[0];
-  int nw = beam<VT, G, CPL>(B, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals, expansions, evictions,
-                            nseed);
+  int nw = beam<VT, G, CPL>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals,
+                            expansions, evictions, nseed);
 
   // S4 + output
   finish_query<G32, CPL32>(a, W, nw, k, qs, out_ids, out_d);
@@ -661,7 +664,7 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 }
 
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const SearchArgs a) {
+__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const __grid_constant__ SearchArgs a) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
   unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * a.warp_smem;
@@ -704,7 +707,7 @@ __device__ __forceinline__ long long ld_acquire_gpu(const long long* p) {
 // items are published and it has ended.  A finished query bumps its
 // request's counter in mapped host memory after a system-scope fence.
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const ServeArgs s) {
+__global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const __grid_constant__ ServeArgs s) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
   unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * s.base.warp_smem;
@@ -761,7 +764,7 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const Ser
 // is strictly closer.  The local minimum it ends at is what the recall
 // bound rho_delta of Def. 3 ranks among the query's true neighbours.
 template <typename VT, int DMAX>
-__global__ void __launch_bounds__(128) k_greedy_probe(const GreedyProbeArgs a) {
+__global__ void __launch_bounds__(128) k_greedy_probe(const __grid_constant__ GreedyProbeArgs a) {
   constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
@@ -954,7 +957,7 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 // list: a few passing keys by shuffle insertion, many by sorting the batch
 // and a bitonic merge.
 __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t s, int64_t ldo,
-                               uint64_t* __restrict__ out) {
+                               uint64_t* __restrict__ out, int32_t discard) {
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
   const float4 kInf4 = make_float4(kInf, kInf, kInf, kInf);
@@ -1017,14 +1020,25 @@ __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t 
       }
     }
     out[q * 32 + lane] = mine;
+    // the row is not read again: drop its lines from L2 without writing
+    // them back (the buffer is rewritten or freed next), so a matrix that
+    // fit in L2 never reaches DRAM
+    __syncwarp();
+    if (discard) {
+      const char* rb = reinterpret_cast<const char*>(D + q * ldo);
+      for (int64_t l = lane; l < ldo / 32; l += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(rb + l * 128) : "memory");
+    }
   }
 }
 
-void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, cudaStream_t st) {
+void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, bool discard,
+                         cudaStream_t st) {
   int64_t blocks = (nq + 7) / 8;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
-  k_select_top32<<<(int)blocks, 256, 0, st>>>(D, nq, s, ldo, out);
+  // discard works on whole 128-byte lines: rows must start on one
+  const bool lines = (reinterpret_cast<uintptr_t>(D) & 127) == 0 && ldo % 32 == 0;
+  k_select_top32<<<(int)blocks, 256, 0, st>>>(D, nq, s, ldo, out, discard && lines ? 1 : 0);
 }
 
 // ------------------------------------------------------------ dispatch
