@@ -275,6 +275,11 @@ typedef struct {
   double tile_flops;                       /* their algorithmic flops: 2 d per
                                               valid (row, column) pair        */
   int32_t tile_engine;                     /* henn_tiles used for layer 0     */
+  int32_t graph_instantiations;            /* build steps run as CUDA graphs:
+                                              executable graphs instantiated  */
+  int32_t graph_updates;                   /* ... and steps that relaunched an
+                                              instantiated graph updated in
+                                              place (same topology)           */
 } henn_index_info;
 
 henn_status henn_index_get_info(const henn_index* idx, henn_index_info* info);

@@ -150,6 +150,8 @@ class IndexInfo(C.Structure):
         ("tile_seconds", C.c_double),
         ("tile_flops", C.c_double),
         ("tile_engine", C.c_int32),
+        ("graph_instantiations", C.c_int32),
+        ("graph_updates", C.c_int32),
     ]
 
 
@@ -329,6 +331,7 @@ class Index:
             device_bytes=inf.device_bytes, uncertified_rows=inf.uncertified_rows,
             build_seconds=inf.build_seconds, M=inf.M, Mmax=inf.Mmax, tile_seconds=inf.tile_seconds,
             tile_flops=inf.tile_flops, tile_engine=inf.tile_engine,
+            graph_instantiations=inf.graph_instantiations, graph_updates=inf.graph_updates,
         )
 
     def layer(self, i: int) -> dict:

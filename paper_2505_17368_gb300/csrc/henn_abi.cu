@@ -97,28 +97,58 @@ struct BuildTrace {
   }
 };
 
-// Captures the launches that f() enqueues on st into a CUDA graph and runs
-// it once (st must not be the legacy default stream).  Device memory used
-// inside must be allocated before the capture.
-template <class F>
-void run_captured(cudaStream_t st, F&& f) {
-  cudaGraph_t g = nullptr;
-  cudaGraphExec_t ge = nullptr;
-  CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
-  try {
-    f();
-  } catch (...) {
-    cudaStreamEndCapture(st, &g);
-    if (g) cudaGraphDestroy(g);
-    throw;
+// One build step run as a CUDA graph, again and again: each run captures
+// the launches f() enqueues on st (not the legacy default stream; device
+// memory used inside is allocated before the capture) and launches them as
+// one graph.  The executable graph is kept: a capture with the same
+// topology (the next epsilon-net attempt, the next layer -- only kernel
+// arguments, grid sizes and copy sizes differ) updates it in place, which
+// costs far less than instantiating; a different topology instantiates anew.
+struct CapturedGraph {
+  cudaGraphExec_t exec = nullptr;
+  int32_t instantiations = 0, updates = 0;
+  CapturedGraph() = default;
+  CapturedGraph(const CapturedGraph&) = delete;
+  CapturedGraph& operator=(const CapturedGraph&) = delete;
+  ~CapturedGraph() {
+    if (exec) cudaGraphExecDestroy(exec);
   }
-  CK(cudaStreamEndCapture(st, &g));
-  cudaError_t e = cudaGraphInstantiate(&ge, g, 0);
-  if (e == cudaSuccess) e = cudaGraphLaunch(ge, st);
-  if (ge) cudaGraphExecDestroy(ge);
-  cudaGraphDestroy(g);
-  CK(e);
-}
+  template <class F>
+  void run(cudaStream_t st, F&& f) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(st, cudaStreamCaptureModeThreadLocal));
+    try {
+      f();
+    } catch (...) {
+      cudaStreamEndCapture(st, &g);
+      if (g) cudaGraphDestroy(g);
+      throw;
+    }
+    CK(cudaStreamEndCapture(st, &g));
+    bool updated = false;
+    if (exec) {
+      cudaGraphExecUpdateResultInfo info;
+      if (cudaGraphExecUpdate(exec, g, &info) == cudaSuccess) {
+        updated = true;
+      } else {
+        cudaGetLastError();  // an update refused for topology is not an error
+        cudaGraphExecDestroy(exec);
+        exec = nullptr;
+      }
+    }
+    cudaError_t e = cudaSuccess;
+    if (updated) {
+      ++updates;
+    } else {
+      e = cudaGraphInstantiate(&exec, g, 0);
+      if (e == cudaSuccess) ++instantiations;
+      else exec = nullptr;
+    }
+    if (e == cudaSuccess) e = cudaGraphLaunch(exec, st);
+    cudaGraphDestroy(g);
+    CK(e);
+  }
+};
 
 int64_t ring_window(double c0, int32_t d, int64_t s, int32_t m) {
   // eps(s) * s with eps from Eq. 1 (natural log), evaluated as
@@ -131,6 +161,18 @@ int64_t ring_window(double c0, int32_t d, int64_t s, int32_t m) {
 }
 
 int32_t round_up(int32_t v, int32_t m) { return (v + m - 1) / m * m; }
+
+// Relative error bound (per unit of sum |a_i b_i|) of a split-BF16 tile dot
+// product over dk values: each product hi.hi + lo.hi + hi.lo misses lo.lo
+// and the rounding of lo, 3 * 2^-18 of |a_i b_i|; the products themselves
+// are exact in FP32 (8-bit significands).  The tensor core sums them as a
+// blocked sum: 16 products per MMA (at most 15 additions inside a block),
+// then one accumulation into the FP32 accumulator per MMA, 3 * dk / 16 MMAs
+// in all, each addition with a relative error of at most 2^-24, doubled to
+// allow for truncation instead of rounding inside the tensor core.
+double tc_tile_unit_error(int32_t dk) {
+  return 3.0 * std::ldexp(1.0, -18) + 2.0 * (15.0 + 3.0 * dk / 16.0 + 8.0) * std::ldexp(1.0, -24);
+}
 
 }  // namespace
 
@@ -169,6 +211,7 @@ struct henn_index {
   double build_seconds = 0.0;
   double tile_seconds = 0.0, tile_flops = 0.0;
   int32_t tile_engine = 0;
+  int32_t graph_instantiations = 0, graph_updates = 0;
   int device = 0;
 
   template <typename T>
@@ -296,7 +339,7 @@ namespace {
 int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32_t layer, int64_t s,
                                const int32_t* prev_ids, Scratch& sc, uint8_t* flags, int64_t* tile_buf,
                                int64_t* d_total, int32_t* pos, int32_t* ids, int64_t* out_count,
-                               int32_t* out_ambiguous, cudaStream_t st) {
+                               int32_t* out_ambiguous, CapturedGraph& graph, cudaStream_t st) {
   const int64_t decay = 1LL << p.m;
   const int64_t t = (s + decay - 1) / decay;
   const int64_t w = ring_window(p.eps_c0, ix->d, s, p.m);
@@ -325,7 +368,7 @@ int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32
     const uint64_t base = derive(derive(derive(ix->seed, HENN_TAG_SAMPLE), (uint64_t)layer), (uint64_t)a);
     const uint64_t bc = derive(derive(derive(ix->seed, HENN_TAG_RCENTRE), (uint64_t)layer), (uint64_t)a);
     const uint64_t bs = derive(derive(derive(ix->seed, HENN_TAG_RSTART), (uint64_t)layer), (uint64_t)a);
-    run_captured(st, [&] {
+    graph.run(st, [&] {
       CK(cudaMemsetAsync(flags, 0, (size_t)s, st));
       LayerSampleArgs la;
       la.base = base;
@@ -382,7 +425,8 @@ int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32
   return -1;
 }
 
-void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, cudaStream_t st, BuildTrace& tr) {
+void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, CapturedGraph& graph, cudaStream_t st,
+                       BuildTrace& tr) {
   LayerDev& Ly = ix->layers[li];
   const int64_t s = Ly.size;
   const int32_t dpad = ix->dpad, M = ix->M;
@@ -424,9 +468,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     CK(cudaMemcpyAsync(&herr, err, sizeof(int32_t), cudaMemcpyDeviceToHost, st));
     CK(cudaStreamSynchronize(st));
     if (herr) throw Failure(HENN_ERR_TIMEOUT, "tensor-core tile pipeline wait timed out (code " + std::to_string(herr) + ")");
-    // split BF16 products (3 * 2^-18 each) plus FP32 accumulation over 3 * dk
-    // terms, doubled for non-IEEE accumulation inside the tensor core
-    tile_u = 3.0 * std::ldexp(1.0, -18) + 2.0 * (3.0 * dk + 8.0) * std::ldexp(1.0, -24);
+    tile_u = tc_tile_unit_error(dk);
   } else {
     launch_tile_topk_simt(xo, norms, s, xo, norms, s, dpad, mode, KP, 1, cand, st);
     CKL("distance tiles");
@@ -475,7 +517,7 @@ void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, c
     Ly.vec = ix->alloc<uint8_t>((size_t)s * dpad);
     Ly.vscale = ix->alloc<float>(s);
   }
-  run_captured(st, [&] {
+  graph.run(st, [&] {
     CK(cudaMemsetAsync(cnt, 0, sizeof(int32_t) * s, st));
     CK(cudaMemsetAsync(fill, 0, sizeof(int32_t) * s, st));
     launch_rev_count(Ly.fwd, s, M, cnt, st);
@@ -581,6 +623,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     ix->layers[0].size = n;
     ix->attempts.push_back(0);
     ix->ambiguous.push_back(0);
+    CapturedGraph attempt_graph, layer_graph;
     {
       Scratch sc(st);
       uint8_t* flags = sc.get<uint8_t>(n);
@@ -603,7 +646,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
           CKL("halving");
         } else {
           a = build_layer_membership(ix, p, layer, s, ix->layers[layer - 1].ids, sc, flags, tile_buf, d_total, pos,
-                                     ids, &count, &amb, st);
+                                     ids, &count, &amb, attempt_graph, st);
         }
         if (a < 0)
           throw Failure(HENN_ERR_EPSNET_NOT_FOUND,
@@ -630,9 +673,11 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
       Ly.adj = ix->alloc<int32_t>((size_t)Ly.size * kMmax);
       Ly.fwd = ix->alloc<int32_t>((size_t)Ly.size * ix->M);
       Ly.fwd_d = ix->alloc<float>((size_t)Ly.size * ix->M);
-      build_layer_graph(ix, p, li, st, tr);
+      build_layer_graph(ix, p, li, layer_graph, st, tr);
       tr.mark("scratch release", li);
     }
+    ix->graph_instantiations = attempt_graph.instantiations + layer_graph.instantiations;
+    ix->graph_updates = attempt_graph.updates + layer_graph.updates;
 
     // ---- search-side layer table
     std::vector<SearchLayer> h(ix->L + 1);
@@ -963,6 +1008,9 @@ const henn_index::EntryOps& entry_ops(const henn_index* idx, int32_t li, cudaStr
 // whose matrix takes at most a third of L2 (written by the tile launch, read
 // by the selection from L2 and dropped there, so it never reaches DRAM)
 constexpr int64_t kDenseExactMax = 16384;
+#ifndef HENN_EXACT_L2_SHARE
+#define HENN_EXACT_L2_SHARE 3  // a chunk's matrix takes at most L2 / this (0: one chunk)
+#endif
 
 int persistent_grid(int device, int warps, size_t smem) {
   int grid = 0;
@@ -1157,7 +1205,8 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         if (s <= kDenseExactMax) {
           int l2 = 0;
           CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, idx->device));
-          const double chunk_bytes = std::max(8.0 * (1 << 20), (double)l2 / 3.0);
+          const double chunk_bytes =
+              HENN_EXACT_L2_SHARE > 0 ? std::max(8.0 * (1 << 20), (double)l2 / HENN_EXACT_L2_SHARE) : 1e18;
           int64_t qc = (int64_t)(chunk_bytes / (4.0 * (double)ldo)) / 128 * 128;
           qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
           float* dm = sc.get<float>((size_t)qc * ldo);
@@ -1171,9 +1220,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         } else {
           CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, st));
         }
-        // as for the construction tiles: split BF16 products plus FP32
-        // accumulation over 3 * dk terms, doubled
-        a.pre_tile_u = 3.0 * std::ldexp(1.0, -18) + 2.0 * (3.0 * dkk + 8.0) * std::ldexp(1.0, -24);
+        a.pre_tile_u = tc_tile_unit_error(dkk);
         launches += 2;
       } else {
         float* qo = sc.get<float>((size_t)nq * dpad);
@@ -1356,6 +1403,8 @@ extern "C" henn_status henn_index_get_info(const henn_index* idx, henn_index_inf
   info->tile_seconds = idx->tile_seconds;
   info->tile_flops = idx->tile_flops;
   info->tile_engine = idx->tile_engine;
+  info->graph_instantiations = idx->graph_instantiations;
+  info->graph_updates = idx->graph_updates;
   return HENN_OK;
 }
 

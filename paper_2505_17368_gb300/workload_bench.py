@@ -198,11 +198,35 @@ def run(workload, storage, n=None, nq=None, sample=100, target=0.95):
     return res
 
 
+def _query_times(idx, Qd, ef, ef_upper, sample=300, runs=3):
+    """Device time (us) of one query answered alone (a single-query launch,
+    CUDA events on the stream), for `sample` queries, each `runs` times:
+    per query the maximum over its runs (the paper's worst-case protocol,
+    Sec. 4: max over runs)."""
+    import torch
+
+    out = []
+    for q in range(min(sample, Qd.shape[0])):
+        one = Qd[q:q + 1]
+        ts = []
+        for _ in range(runs):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            idx.search(one, k=K, ef=ef, ef_upper=ef_upper)
+            e1.record()
+            e1.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e3)
+        out.append(max(ts))
+    return np.array(out)
+
+
 def scaling(workload, ns, ef, ef_upper, storage="f32"):
     """Work per query against n (the paper's hops and worst-case time against
-    n): for each prefix size n of the workload, build, search the queries at
-    a fixed beam, and report recall@10, batch QPS and the mean / maximum of
-    distance evaluations and hops per query."""
+    n, Sec. 4): for each prefix size n of the workload, build, search the
+    queries at a fixed beam, and report recall@10, batch QPS, the mean /
+    maximum of distance evaluations and hops per query, and the time of a
+    query answered alone -- max over 3 runs per query, then the median, 99th
+    percentile and maximum over 300 queries."""
     import torch
 
     import paper_2505_17368_gb300 as H
@@ -220,10 +244,13 @@ def scaling(workload, ns, ef, ef_upper, storage="f32"):
         st = st.cpu().numpy().astype(np.int64)
         hops = st[:, 1] + st[:, 2]
         ms = _time(lambda: idx.search(Qd, k=K, ef=ef, ef_upper=ef_upper), flush)
+        qt = _query_times(idx, Qd, ef, ef_upper)
         out.append({"workload": workload, "n": n, "layers": idx.info()["sizes"], "ef": ef, "ef_upper": ef_upper,
                     "recall_at_10": _recall(ids.cpu().numpy(), gi.cpu().numpy()), "qps": len(Q) / (ms * 1e-3),
                     "evals_mean": float(st[:, 0].mean()), "evals_max": int(st[:, 0].max()),
-                    "hops_mean": float(hops.mean()), "hops_max": int(hops.max())})
+                    "hops_mean": float(hops.mean()), "hops_max": int(hops.max()),
+                    "query_us_median": float(np.median(qt)), "query_us_p99": float(np.percentile(qt, 99)),
+                    "query_us_max": float(qt.max())})
         del idx
         torch.cuda.empty_cache()
     return out
