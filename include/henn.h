@@ -398,6 +398,11 @@ typedef struct {
   int32_t descend_all;   /* as in henn_search_params (default 0)                */
   int32_t rerank_mult;   /* as in henn_search_params (default 4)                */
   int32_t idle_ms;       /* kernel idle exit, milliseconds (default 20)         */
+  int32_t ef_l1;         /* as in henn_search_params (default 0)                */
+  int32_t exact_upper;   /* as in henn_search_params, by the SORT method: the
+                            lowest upper layer of at most exact_upper points
+                            (and at most 2048) gives its exact candidate set
+                            (default 0 = never)                               */
 } henn_serve_params;
 
 typedef struct henn_server henn_server; /* opaque */

@@ -127,6 +127,8 @@ class ServeParams(C.Structure):
         ("descend_all", C.c_int32),
         ("rerank_mult", C.c_int32),
         ("idle_ms", C.c_int32),
+        ("ef_l1", C.c_int32),
+        ("exact_upper", C.c_int32),
     ]
 
 
@@ -466,12 +468,13 @@ class Server:
     (ids int64 [nq, k], dists float32 [nq, k])."""
 
     def __init__(self, index: "Index", ring_rows=65536, max_requests=1024, max_k=100, max_ef=512, ef_upper=1,
-                 descend_all=0, rerank_mult=4, idle_ms=20):
+                 descend_all=0, rerank_mult=4, idle_ms=20, ef_l1=0, exact_upper=0):
         L = load()
         p = ServeParams()
         L.henn_serve_params_default(C.byref(p))
         p.ring_rows, p.max_requests, p.max_k, p.max_ef = ring_rows, max_requests, max_k, max_ef
         p.ef_upper, p.descend_all, p.rerank_mult, p.idle_ms = ef_upper, descend_all, rerank_mult, idle_ms
+        p.ef_l1, p.exact_upper = ef_l1, exact_upper
         h = C.c_void_p()
         _check(L.henn_serve_create(index.handle, C.byref(p), C.byref(h)))
         self._h = h

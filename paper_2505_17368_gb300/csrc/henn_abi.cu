@@ -1009,7 +1009,7 @@ const henn_index::EntryOps& entry_ops(const henn_index* idx, int32_t li, cudaStr
 // by the selection from L2 and dropped there, so it never reaches DRAM)
 constexpr int64_t kDenseExactMax = 16384;
 #ifndef HENN_EXACT_L2_SHARE
-#define HENN_EXACT_L2_SHARE 3  // a chunk's matrix takes at most L2 / this (0: one chunk)
+#define HENN_EXACT_L2_SHARE 0  // a chunk's matrix takes at most L2 / this (0: up to 1 GiB, one chunk here)
 #endif
 
 int persistent_grid(int device, int warps, size_t smem) {
@@ -1206,7 +1206,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
           int l2 = 0;
           CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, idx->device));
           const double chunk_bytes =
-              HENN_EXACT_L2_SHARE > 0 ? std::max(8.0 * (1 << 20), (double)l2 / HENN_EXACT_L2_SHARE) : 1e18;
+              HENN_EXACT_L2_SHARE > 0 ? std::max(8.0 * (1 << 20), (double)l2 / HENN_EXACT_L2_SHARE) : 1.0 * (1 << 30);
           int64_t qc = (int64_t)(chunk_bytes / (4.0 * (double)ldo)) / 128 * 128;
           qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
           float* dm = sc.get<float>((size_t)qc * ldo);
@@ -1630,8 +1630,21 @@ extern "C" henn_status henn_serve_create(const henn_index* idx, const henn_serve
     require(p.max_k >= 1 && p.max_k <= 1024, "max_k must be in [1, 1024]");
     require(p.max_ef >= 1 && p.max_ef <= 1024, "max_ef must be in [1, 1024]");
     require(p.ef_upper >= 0 && p.ef_upper <= 1024, "ef_upper must be in [0, 1024]");
+    require(p.ef_l1 >= 0 && p.ef_l1 <= 1024, "ef_l1 must be in [0, 1024]");
+    require(p.exact_upper >= 0, "exact_upper must be >= 0");
     require(p.idle_ms >= 1 && p.idle_ms <= 10000, "idle_ms must be in [1, 10000]");
     if (p.rerank_mult <= 0) p.rerank_mult = 4;
+    // the lowest upper layer with at most exact_upper points: its exact set
+    // by the in-kernel sort (in the visited table's space), so that no
+    // separate launch has to share the GPU with the resident kernel
+    int32_t top_exact = idx->L;
+    bool has_exact = false;
+    for (int32_t li = 1; p.exact_upper > 0 && li <= idx->L; ++li)
+      if (idx->layers[li].size <= p.exact_upper) {
+        top_exact = li;
+        has_exact = true;
+        break;
+      }
     sv = new henn_server();
     sv->idx = idx;
     sv->p = p;
@@ -1654,15 +1667,26 @@ extern "C" henn_status henn_serve_create(const henn_index* idx, const henn_serve
     std::memset(sv->done_h, 0, sizeof(int) * p.max_requests);
     sv->slots.resize(p.max_requests);
     // kernel shape: the shared-memory class of the widest admitted beam
-    const int need = std::max(std::max(p.max_k, p.max_ef), std::max(p.ef_upper, std::min(p.max_ef, p.rerank_mult * p.max_k)));
+    const int need = std::max(std::max(std::max(p.max_k, p.max_ef), std::max(p.ef_upper, p.ef_l1)),
+                              std::min(p.max_ef, p.rerank_mult * p.max_k));
     int ef_cap = 32;
     while (ef_cap < need) ef_cap <<= 1;
-    const int hb = pick_hash_bits(ef_cap);
+    int hb = pick_hash_bits(ef_cap);
+    if (has_exact) {
+      // the exact layer's keys take the visited table's space
+      while (hb < 12 && (1 << (hb - 1)) < idx->layers[top_exact].size) ++hb;
+      require(idx->layers[top_exact].size <= (1 << (hb - 1)),
+              "exact_upper: the exact layer of a server must have at most 2048 points");
+    }
     SearchArgs& a = sv->args.base;
     fill_search_args(idx, a);
     a.rerank_mult = p.rerank_mult;
     a.ef_upper = p.ef_upper;
     a.descend_all = p.descend_all;
+    a.ef_l1 = p.ef_l1;
+    a.exact_upper = has_exact ? p.exact_upper : 0;
+    a.top_exact = top_exact;
+    a.exact_method = HENN_EXACT_SORT;
     a.ef_cap = ef_cap;
     a.hash_bits = hb;
     a.out_stride = p.max_k;

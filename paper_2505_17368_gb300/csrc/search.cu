@@ -45,10 +45,17 @@ namespace henn {
 #ifndef HENN_SEARCH_CHUNKS_IN_FLIGHT
 #define HENN_SEARCH_CHUNKS_IN_FLIGHT 4
 #endif
-// Beams of at most 64 entries run beam64 (1) or the general beam (0); both
-// give the same results.
-#ifndef HENN_SEARCH_BEAM64
-#define HENN_SEARCH_BEAM64 1
+// Adjacency line of the next expansion pulled towards the SM during the
+// current one: 0 = the next unexpanded entry before this step's insertion
+// (a guess), 1 = the node actually expanded next (known once the new
+// candidates are sorted: the smaller of the old next entry and the best
+// new one), into L1; 2 = the same into L2 only.
+#ifndef HENN_SEARCH_NEXT_PREFETCH
+#define HENN_SEARCH_NEXT_PREFETCH 1
+#endif
+// Lanes per row for rows of at most 32 chunks of 16 bytes.
+#ifndef HENN_SEARCH_ROW_LANES
+#define HENN_SEARCH_ROW_LANES 8
 #endif
 
 constexpr int kStageBytes = 32 * 8;     // per-warp staging of one neighbour list
@@ -299,17 +306,33 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     ++expansions;
     const int32_t c = (int32_t)key_index(e & kKeyMask);
     int32_t nb = adj[(int64_t)c * kMmax + lane];
-    // the next unexpanded entry is the likely next expansion: pull its
-    // adjacency line towards the SM while this one is processed
-    if (lane == 0 && after >= 0) {
+    // (HENN_SEARCH_NEXT_PREFETCH 0) the next unexpanded entry, a guess at
+    // the next expansion: pull its adjacency line towards the SM
+    if (HENN_SEARCH_NEXT_PREFETCH == 0 && lane == 0 && after >= 0) {
       const int32_t* nxt = adj + (int64_t)key_index(W[after] & kKeyMask) * kMmax;
       asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
     }
+    // the old next unexpanded entry (the next expansion unless a new
+    // candidate comes before it)
+    const uint64_t old_next = after >= 0 ? (W[after] & kKeyMask) : kEmpty;
     __syncwarp();
+    // the node expanded next: its adjacency line, towards the SM
+    auto pull_next = [&](uint64_t nxt) {
+      if (HENN_SEARCH_NEXT_PREFETCH != 0 && lane == 0 && nxt != kEmpty) {
+        const int32_t* p = adj + (int64_t)key_index(nxt) * kMmax;
+        if (HENN_SEARCH_NEXT_PREFETCH == 1)
+          asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
+        else
+          asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+      }
+    };
     bool fresh = nb >= 0 && mark(nb);
     unsigned fm = __ballot_sync(0xffffffffu, fresh);
     int cnt = __popc(fm);
-    if (cnt == 0) continue;
+    if (cnt == 0) {
+      pull_next(old_next);
+      continue;
+    }
     // compact fresh ids into lanes 0..cnt-1 (lane j gets the j-th fresh one)
     if (fresh) stage32[__popc(fm & below)] = nb;
     __syncwarp();
@@ -326,7 +349,10 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     }
     const unsigned cm = __ballot_sync(0xffffffffu, take);
     const int ccnt = __popc(cm);
-    if (ccnt == 0) continue;
+    if (ccnt == 0) {
+      pull_next(old_next);
+      continue;
+    }
     // candidates, compacted, then sorted into stage[0..ccnt); lane j < ccnt
     // holds the j-th smallest and its position in the new W
     __syncwarp();
@@ -339,6 +365,10 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     if (lane < ccnt) stage[rank] = cand;
     __syncwarp();
     cand = lane < ccnt ? stage[lane] : kEmpty;
+    {
+      const uint64_t best_new = __shfl_sync(0xffffffffu, cand, 0);
+      pull_next(best_new < old_next ? best_new : old_next);
+    }
     const int cpos = lane < ccnt ? lower_bound_w(W, nw, cand) + lane : 0x7fffffff;
     const int p0 = __shfl_sync(0xffffffffu, cpos, 0);
     // entries at or after p0 shift right by the number of smaller candidates
@@ -356,134 +386,6 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     __syncwarp();
     nw = min(ef, nw + ccnt);
     first = min(first, p0);
-  }
-  evals_out += evals;
-  expansions_out += expansions;
-  evictions_out = evictions;
-  return nw;
-}
-
-// The same best-first beam for widths of at most 64 (W fits two entries per
-// lane), with the same visiting order and the same W after every step, in
-// fewer dependent shared-memory round trips:
-//  - the next entry to expand is found by two ballots over W;
-//  - the node expanded next is known before this step's insertion -- the
-//    smaller of the old next unexpanded entry and the best new candidate
-//    that enters W (every other unexpanded entry is larger) -- so its
-//    adjacency row is loaded into a register then, and arrives while the
-//    insertion runs;
-//  - the insertion is a merge computed in registers: for each entering
-//    candidate, the entries of W below it (ballots) and the candidates
-//    below it; for each entry of W, the candidates below it; every key
-//    then moves to its merged position (positions >= ef fall out).
-// The warp's visited table, staging slots and query follow W in its
-// shared-memory slice (run_query's layout): they are recomputed from W
-// rather than held as pointers.
-template <typename VT, int G, int CPL>
-__device__ __noinline__ int beam64(const int32_t* __restrict__ adj, const void* vec_, const float* __restrict__ scale,
-                                   int64_t size, int64_t stride, int nchunk, int32_t entry, int ef, uint64_t* W,
-                                   int efcap, int HB, int& evals_out, int& expansions_out, int& evictions_out,
-                                   int nseed = 0) {
-  const int lane = lane_id();
-  const unsigned below = (1u << lane) - 1u;  // lanes under this one
-  int32_t* table = reinterpret_cast<int32_t*>(W + efcap);
-  int32_t* stage32 = reinterpret_cast<int32_t*>(reinterpret_cast<unsigned char*>(table) + (4 << HB));
-  const float* qs = reinterpret_cast<const float*>(reinterpret_cast<unsigned char*>(stage32) + kStageBytes);
-  const VT* vec = reinterpret_cast<const VT*>(vec_);
-  const bool bitmap = size <= ((int64_t)32 << HB);
-  int evals = 0, expansions = 0, evictions = evictions_out;
-  auto mark = [&](int32_t id) { return bitmap ? visit_bit(table, id) : visit(table, HB, id, evictions); };
-  const int words = bitmap ? (int)((size + 31) >> 5) : (1 << HB);
-  for (int s = lane; s < words; s += 32) table[s] = bitmap ? 0 : -1;
-  __syncwarp();
-  int nw;
-  if (nseed > 0) {
-    nw = min(nseed, ef);
-    if (lane == 0)
-      for (int j = 0; j < nw; ++j) mark((int32_t)key_index(W[j] & kKeyMask));
-  } else {
-    if (lane == 0) mark(entry);
-    float d0 = rows_dist<VT, G, CPL>(vec, scale, stride, entry, 1, qs, nchunk);
-    d0 = __shfl_sync(0xffffffffu, d0, 0);
-    ++evals;
-    if (lane == 0) W[0] = pack(d0, (uint32_t)entry);
-    nw = 1;
-  }
-  __syncwarp();
-  int32_t nx_node = -1, nx_row = -1;  // the node expanded next and its adjacency row (this lane's slot)
-  for (;;) {
-    uint64_t w0 = lane < nw ? W[lane] : kEmpty;
-    uint64_t w1 = 32 + lane < nw ? W[32 + lane] : kEmpty;
-    const unsigned u0 = __ballot_sync(0xffffffffu, lane < nw && !(w0 & kFlag));
-    const unsigned u1 = __ballot_sync(0xffffffffu, 32 + lane < nw && !(w1 & kFlag));
-    if ((u0 | u1) == 0u) break;
-    const int pos = u0 ? __ffs(u0) - 1 : 32 + __ffs(u1) - 1;
-    const unsigned v0 = pos < 32 ? (u0 & (u0 - 1u)) : 0u;
-    const unsigned v1 = pos < 32 ? u1 : (u1 & (u1 - 1u));
-    const int after = v0 ? __ffs(v0) - 1 : (v1 ? 32 + __ffs(v1) - 1 : -1);
-    const uint64_t e = shfl64(pos < 32 ? w0 : w1, pos & 31);
-    if (lane == 0) W[pos] = e | kFlag;
-    ++expansions;
-    const int32_t c = (int32_t)key_index(e);
-    const int32_t nb = c == nx_node ? nx_row : adj[(int64_t)c * kMmax + lane];
-    __syncwarp();
-    const bool fresh = nb >= 0 && mark(nb);
-    const unsigned fm = __ballot_sync(0xffffffffu, fresh);
-    const int cnt = __popc(fm);
-    if (cnt == 0) {
-      // nothing enters W: the next expansion is the old next entry
-      nx_node = after < 0 ? -1 : (int32_t)key_index(W[after] & kKeyMask);
-      if (nx_node >= 0) nx_row = adj[(int64_t)nx_node * kMmax + lane];
-      continue;
-    }
-    // compact fresh ids into lanes 0..cnt-1 (lane j gets the j-th fresh one)
-    if (fresh) stage32[__popc(fm & below)] = nb;
-    __syncwarp();
-    const int32_t packed_id = lane < cnt ? stage32[lane] : -1;
-    const float dn = rows_dist<VT, G, CPL>(vec, scale, stride, packed_id, cnt, qs, nchunk);
-    evals += cnt;
-    const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
-    const uint64_t kk = lane < cnt ? pack(dn, (uint32_t)packed_id) : kEmpty;
-    bool take = kk < worst;
-    // a node can reach W twice only if the visited table forgot it
-    if (__any_sync(0xffffffffu, evictions > 0) && take) {
-      const int lb = lower_bound_w(W, nw, kk);
-      if (lb < nw && (W[lb] & kKeyMask) == kk) take = false;
-    }
-    const unsigned cm = __ballot_sync(0xffffffffu, take);
-    // the next expansion and its adjacency row, before the insertion
-    {
-      const uint64_t old_next = after < 0 ? kEmpty : (W[after] & kKeyMask);
-      const uint64_t best_new = warp_min64(take ? kk : kEmpty);
-      const uint64_t nxt = best_new < old_next ? best_new : old_next;
-      nx_node = nxt == kEmpty ? -1 : (int32_t)key_index(nxt);
-      if (nx_node >= 0) nx_row = adj[(int64_t)nx_node * kMmax + lane];
-    }
-    if (cm == 0u) continue;
-    // merged positions: old entry i moves to i + (candidates below it); the
-    // candidate c goes to (entries below c) + (candidates below c)
-    w0 = lane < nw ? W[lane] : kEmpty;  // with the expanded flag just set
-    w1 = 32 + lane < nw ? W[32 + lane] : kEmpty;
-    const uint64_t k0 = w0 & kKeyMask, k1 = w1 & kKeyMask;
-    int cl0 = 0, cl1 = 0, my_rank = 0, my_wpos = 0;
-    unsigned m = cm;
-    do {
-      const int src = __ffs(m) - 1;
-      m &= m - 1u;
-      const uint64_t cj = shfl64(kk, src);
-      cl0 += cj < k0;
-      cl1 += cj < k1;
-      my_rank += cj < kk;
-      const int wb = __popc(__ballot_sync(0xffffffffu, lane < nw && k0 < cj)) +
-                     __popc(__ballot_sync(0xffffffffu, 32 + lane < nw && k1 < cj));
-      if (lane == src) my_wpos = wb;
-    } while (m);
-    __syncwarp();
-    if (lane < nw && lane + cl0 < ef) W[lane + cl0] = w0;
-    if (32 + lane < nw && 32 + lane + cl1 < ef) W[32 + lane + cl1] = w1;
-    if (take && my_wpos + my_rank < ef) W[my_wpos + my_rank] = kk;
-    __syncwarp();
-    nw = min(ef, nw + __popc(cm));
   }
   evals_out += evals;
   expansions_out += expansions;
@@ -561,7 +463,7 @@ __device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const void* ve
 template <typename VT, int DMAX>
 struct RowShape {
   static constexpr int kChunks = DMAX * (int)sizeof(VT) / 16;
-  static constexpr int G = kChunks <= 32 ? 8 : 32;
+  static constexpr int G = kChunks <= 32 ? HENN_SEARCH_ROW_LANES : 32;
   static constexpr int CPL = (kChunks + G - 1) / G;
 };
 
@@ -743,12 +645,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
       __syncwarp();
     } else if (width > 1) {
       int ex = 0;
-      const int bw = min(width, EFCAP);
-      int nw = (HENN_SEARCH_BEAM64 && bw <= 64)
-                   ? beam64<VT, G, CPL>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, bw, W, EFCAP, HB, evals,
-                                        ex, evictions, nseed)
-                   : beam<VT, G, CPL>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, bw, W, table, HB, stage,
-                                      qs, evals, ex, evictions, nseed);
+      int nw = beam<VT, G, CPL>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, min(width, EFCAP), W, table,
+                                HB, stage, qs, evals, ex, evictions, nseed);
       moves += ex;
       cur = (int32_t)key_index(W[0] & kKeyMask);
       if (a.descend_all) {
@@ -786,11 +684,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 
   // S3: layer-0 beam
   const SearchLayer B = a.layers[0];
-  int nw = (HENN_SEARCH_BEAM64 && ef <= 64)
-               ? beam64<VT, G, CPL>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, EFCAP, HB, evals,
-                                    expansions, evictions, nseed)
-               : beam<VT, G, CPL>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals,
-                                  expansions, evictions, nseed);
+  int nw = beam<VT, G, CPL>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals,
+                            expansions, evictions, nseed);
 
   // S4 + output
   finish_query<G32, CPL32>(a, W, nw, k, qs, out_ids, out_d);

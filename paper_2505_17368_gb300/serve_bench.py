@@ -94,6 +94,48 @@ def run_rate(srv, Q, rate_qps, seconds, max_batch, seed):
     }
 
 
+def batched_same_mix(idx, Q, seconds, max_batch, seed, ef_upper, descend_all, ef_l1, exact_upper, exact_method,
+                     gt=None):
+    """The batched ceiling for the same query mix: the queries of the same
+    generated request stream (batch sizes, k, ef) answered by henn_search
+    calls over batches of 10,000 queries with per-query k and ef (no
+    arrivals, no admission); (queries per second of device time, mean
+    recall@k against gt's exact neighbours, or None)."""
+    import torch
+
+    rng = np.random.default_rng(seed)
+    ks, efs = [], []
+    while len(ks) < 10000:
+        b = int(min(max_batch, max(1, round(math.exp(rng.uniform(0, math.log(max_batch)))))))
+        k = int(rng.choice([10, 100]))
+        ef = int(round(math.exp(rng.uniform(math.log(64), math.log(512)))))
+        ks += [k] * b
+        efs += [ef] * b
+    n = min(10000, len(Q))
+    kq = torch.tensor(ks[:n], dtype=torch.int32, device="cuda")
+    eq = torch.tensor(efs[:n], dtype=torch.int32, device="cuda")
+    Qd = torch.from_numpy(np.ascontiguousarray(Q[:n])).cuda()
+    kw = dict(k=kq, ef=eq, out_stride=100, ef_upper=ef_upper, descend_all=descend_all, ef_l1=ef_l1,
+              exact_upper=exact_upper, exact_method=exact_method)
+    idx.search(Qd, **kw)
+    torch.cuda.synchronize()
+    ts = []
+    for _ in range(5):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record()
+        idx.search(Qd, **kw)
+        e1.record()
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) * 1e-3)
+    rec = None
+    if gt is not None:
+        ids = idx.search(Qd, **kw)[0].cpu().numpy()
+        kk = np.array(ks[:n])
+        rec = float(np.mean([len(set(ids[q, :kk[q]].tolist()) & set(gt[q, :kk[q]].tolist())) / kk[q]
+                             for q in range(n)]))
+    return n / float(np.median(ts)), rec
+
+
 def main():
     import torch
 
@@ -107,6 +149,9 @@ def main():
     ap.add_argument("--seconds", type=float, default=3.0)
     ap.add_argument("--max-batch", type=int, default=4096)
     ap.add_argument("--ef-upper", type=int, default=64)
+    ap.add_argument("--descend-all", type=int, default=0)
+    ap.add_argument("--ef-l1", type=int, default=0)
+    ap.add_argument("--exact-upper", default="0", help="exact layer size bound, or L<i> for the size of layer i")
     ap.add_argument("--tiles", type=int, default=0)
     args = ap.parse_args()
     X, Q, info = synth.workload(args.workload, n=args.n, nq=20000)
@@ -114,11 +159,27 @@ def main():
     t = time.perf_counter()
     idx = H.Index(torch.from_numpy(X).cuda(), metric=metric, storage=H.BF16, seed=0, tiles=args.tiles)
     build_s = time.perf_counter() - t
-    srv = H.Server(idx, ring_rows=1 << 17, max_requests=4096, max_k=100, max_ef=512, ef_upper=args.ef_upper)
+    sizes = idx.info()["sizes"]
+    xu = args.exact_upper
+    xu = (sizes[int(xu[1:])] if int(xu[1:]) < len(sizes) else 0) if xu.startswith("L") else int(xu)
+    beam = dict(ef_upper=args.ef_upper, descend_all=args.descend_all, ef_l1=args.ef_l1, exact_upper=xu)
+    # exact neighbours (FP32, on the device) of the first 10,000 queries, for the recall of the mix
+    Xd = torch.from_numpy(X).cuda()
+    gt = H.exact_knn(Xd, torch.from_numpy(np.ascontiguousarray(Q[:10000])).cuda(), 100, metric=metric)[0].cpu().numpy()
+    del Xd
+    ceiling = {}
+    for m in ([H.EXACT_SORT, H.EXACT_TILES] if xu else [H.EXACT_SORT]):
+        try:
+            qps, rec = batched_same_mix(idx, Q, args.seconds, args.max_batch, 99, exact_method=m, gt=gt, **beam)
+            ceiling["tiles" if m == H.EXACT_TILES else "sort"] = {"qps": qps, "recall_at_k": rec}
+        except H.HennError as e:  # e.g. a layer too large for the in-kernel sort of a batched call
+            ceiling["tiles" if m == H.EXACT_TILES else "sort"] = str(e)
+    print(json.dumps({"workload": args.workload, "n": len(X), "layers": sizes, **beam,
+                      "batched_same_mix": ceiling}), flush=True)
+    srv = H.Server(idx, ring_rows=1 << 17, max_requests=4096, max_k=100, max_ef=512, **beam)
     for r in [float(v) for v in args.rates.split(",")]:
         res = run_rate(srv, Q, r, args.seconds, args.max_batch, seed=int(r) % 1000)
-        res.update(workload=args.workload, n=len(X), build_seconds=build_s, form="bf16 + fp32 rerank",
-                   ef_upper=args.ef_upper)
+        res.update(workload=args.workload, n=len(X), build_seconds=build_s, form="bf16 + fp32 rerank", **beam)
         print(json.dumps(res), flush=True)
     srv.close()
 

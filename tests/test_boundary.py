@@ -58,12 +58,13 @@ def test_struct_layouts_match_c():
 #include <stddef.h>
 #include "henn.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(henn_build_params), offsetof(henn_build_params, seed),
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(henn_build_params), offsetof(henn_build_params, seed),
          offsetof(henn_build_params, sampler),
          sizeof(henn_search_params), offsetof(henn_search_params, ef_upper),
          offsetof(henn_search_params, time_kernel),
          sizeof(henn_index_info), offsetof(henn_index_info, build_seconds),
-         offsetof(henn_index_info, graph_updates));
+         offsetof(henn_index_info, graph_updates), sizeof(henn_serve_params),
+         offsetof(henn_serve_params, exact_upper));
   return 0;
 }
 """
@@ -76,7 +77,8 @@ int main(void) {
     want = [C.sizeof(binding.BuildParams), binding.BuildParams.seed.offset, binding.BuildParams.sampler.offset,
             C.sizeof(binding.SearchParams),
             binding.SearchParams.ef_upper.offset, binding.SearchParams.time_kernel.offset, C.sizeof(binding.IndexInfo),
-            binding.IndexInfo.build_seconds.offset, binding.IndexInfo.graph_updates.offset]
+            binding.IndexInfo.build_seconds.offset, binding.IndexInfo.graph_updates.offset,
+            C.sizeof(binding.ServeParams), binding.ServeParams.exact_upper.offset]
     assert got == want
 
 

@@ -151,6 +151,29 @@ def test_served_results_track_oracle(index_and_queries):
     assert abs(rg - ro) <= P.RECALL_TOL + 1e-12, (rg, ro)
 
 
+def test_exact_layer_and_seeded_beams_in_serving(index_and_queries):
+    """A server may take an upper layer's exact candidate set (in-kernel
+    sort) and seed narrower beams below it (descend_all, ef_l1): each
+    request's results equal henn_search's with the same options."""
+    idx, Q = index_and_queries
+    sizes = idx.info()["sizes"]
+    xu = sizes[2]
+    kw = dict(ef_upper=16, descend_all=1, ef_l1=8, exact_upper=xu)
+    srv = H.Server(idx, ring_rows=4096, max_requests=8, max_k=100, max_ef=512, **kw)
+    for at, b, k, ef in _requests(600, 11)[:12]:
+        keys = np.arange(at, at + b, dtype=np.uint64)
+        rid = srv.submit(Q[at:at + b], k=k, ef=ef, keys=keys)
+        assert rid is not None
+        ids_s, d_s = _wait(srv, rid)
+        ids, dd, _ = idx.search(torch.from_numpy(Q[at:at + b]).cuda(), k=k, ef=ef, keys=torch.from_numpy(
+            keys.astype(np.int64)).cuda(), exact_method=H.EXACT_SORT, **kw)
+        assert np.array_equal(ids.cpu().numpy(), ids_s) and np.array_equal(dd.cpu().numpy(), d_s), at
+    srv.close()
+    with pytest.raises(H.HennError) as e:
+        H.Server(idx, ef_l1=5000)
+    assert e.value.status == 1
+
+
 def test_admission_budget_and_errors(index_and_queries):
     idx, Q = index_and_queries
     srv = H.Server(idx, ring_rows=100, max_requests=2, max_k=10, max_ef=128)
