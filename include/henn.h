@@ -214,6 +214,11 @@ typedef struct {
                                  the same set                                     */
   int32_t time_kernel;        /* 1: record device events around this call's
                                  search launches (henn_last_search_ms)           */
+  int32_t team_size;          /* warps answering one query: 1 (default), 2 or 4;
+                                 0 = 1.  The team's warps share the distance work
+                                 of every beam expansion (shorter latency per
+                                 query, fewer queries in flight); results do not
+                                 depend on it.  Must divide warps_per_block     */
 } henn_search_params;
 
 /* exact_method values */

@@ -1097,6 +1097,10 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
               "exact_method SORT: the exact layer must have <= 2^(hash_bits - 1) points (512 by default)");
     int warps = sp.warps_per_block > 0 ? sp.warps_per_block : kSearchWarps;
     require(warps >= 1 && warps <= kSearchWarps, "warps_per_block must be in [1, 4]");
+    const int team = sp.team_size > 0 ? sp.team_size : 1;
+    require(team == 1 || team == 2 || team == 4, "team_size must be 1, 2 or 4");
+    require(warps % team == 0, "team_size must divide warps_per_block");
+    const int teams = warps / team;  // queries in flight per block
 
     Scratch sc(st, idx->search_pool());
     const float* dQ = Q;
@@ -1183,6 +1187,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     a.exact_upper = sp.exact_upper;
     a.top_exact = top_exact;
     a.exact_method = has_exact ? sp.exact_method : HENN_EXACT_SORT;
+    a.team = team;
     int32_t launches = 0;
     if (has_exact && sp.exact_method == HENN_EXACT_TILES) {
       // batched candidates of the exact layer: queries against all its points
@@ -1258,8 +1263,8 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     }
     launches += groups;
     if (groups == 1) {
-      size_t smem = search_warp_smem(ef_cap, hb, idx->dpad) * warps;
-      int64_t blocks_needed = (nq + warps - 1) / warps;
+      size_t smem = search_team_smem(ef_cap, hb, idx->dpad, team) * teams;
+      int64_t blocks_needed = (nq + teams - 1) / teams;
       int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
       CK(launch_search(a, warps, grid, st));
     } else {
@@ -1281,8 +1286,8 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         ag.ef_cap = caps[g];
         ag.hash_bits = pick_hash_bits(caps[g]);
         ag.counter = counter + g;
-        size_t smem = search_warp_smem(ag.ef_cap, ag.hash_bits, idx->dpad) * warps;
-        int64_t blocks_needed = (count[g] + warps - 1) / warps;
+        size_t smem = search_team_smem(ag.ef_cap, ag.hash_bits, idx->dpad, team) * teams;
+        int64_t blocks_needed = (count[g] + teams - 1) / teams;
         int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);
         CK(launch_search(ag, warps, grid, t));
         cudaEvent_t join;

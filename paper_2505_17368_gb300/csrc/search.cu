@@ -30,6 +30,8 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <type_traits>
+
 #include "common.cuh"
 #include "kernels.cuh"
 #include "search.cuh"
@@ -45,20 +47,37 @@ namespace henn {
 #ifndef HENN_SEARCH_CHUNKS_IN_FLIGHT
 #define HENN_SEARCH_CHUNKS_IN_FLIGHT 4
 #endif
-// Adjacency line of the next expansion pulled towards the SM during the
-// current one: 0 = the next unexpanded entry before this step's insertion
-// (a guess), 1 = the node actually expanded next (known once the new
-// candidates are sorted: the smaller of the old next entry and the best
-// new one), into L1; 2 = the same into L2 only.
-#ifndef HENN_SEARCH_NEXT_PREFETCH
-#define HENN_SEARCH_NEXT_PREFETCH 1
-#endif
-// Lanes per row for rows of at most 32 chunks of 16 bytes.
-#ifndef HENN_SEARCH_ROW_LANES
-#define HENN_SEARCH_ROW_LANES 8
-#endif
+
 
 constexpr int kStageBytes = 32 * 8;     // per-warp staging of one neighbour list
+
+// A team of warps answering one query (team_size > 1): the leader warp runs
+// the query; for the neighbour rows of each beam expansion it posts a job
+// (the row ids) and every warp of the team computes the distances of rows
+// rank, rank + T, ...  The team synchronises on its own named barrier.
+struct alignas(16) TeamJob {
+  int32_t ids[32];
+  float dist[32];
+  const void* vec;
+  const float* scale;
+  int64_t qi;     // the team's current query
+  int32_t count;  // rows of this job
+  int32_t cmd;    // 0: rows, 1: the query is done
+};
+
+struct Team {
+  TeamJob* job;  // nullptr for a single warp
+  int bar;       // named barrier of the team (1 + team index)
+  int threads;   // 32 * size
+  int size;      // warps per query
+};
+
+// A single warp's "team": nothing to pass.
+struct Solo {};
+
+__device__ __forceinline__ void team_sync(const Team& tm) {
+  asm volatile("bar.sync %0, %1;" ::"r"(tm.bar), "r"(tm.threads) : "memory");
+}
 constexpr uint64_t kFlag = 1ull << 31;  // "expanded" bit inside the index word
 constexpr uint64_t kKeyMask = ~kFlag;
 
@@ -210,6 +229,52 @@ __device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const flo
   return mine;
 }
 
+// rows_dist shared by a team: the leader (all its lanes) posts the ids and
+// takes rows 0, T, 2T, ...; the other warps take theirs in team_helper.
+// Each row's distance is computed by the same lane arithmetic as in
+// rows_dist alone, so the result does not depend on the team size.
+template <typename VT, int G, int CPL>
+__device__ __forceinline__ float team_rows(const Team& tm, const VT* __restrict__ vec, const float* __restrict__ scale,
+                                           int64_t stride_bytes, int32_t my_id, int count,
+                                           const float* __restrict__ qs, int nchunk) {
+  const int lane = lane_id();
+  TeamJob* job = tm.job;
+  if (lane < count) job->ids[lane] = my_id;
+  if (lane == 0) {
+    job->vec = vec;
+    job->scale = scale;
+    job->count = count;
+    job->cmd = 0;
+  }
+  __syncwarp();
+  team_sync(tm);
+  const int mine = (count + tm.size - 1) / tm.size;
+  const int32_t id = lane < mine ? job->ids[lane * tm.size] : 0;
+  const float d = rows_dist<VT, G, CPL>(vec, scale, stride_bytes, id, mine, qs, nchunk);
+  if (lane < mine) job->dist[lane * tm.size] = d;
+  team_sync(tm);
+  return lane < count ? job->dist[lane] : 0.f;
+}
+
+// The other warps of a team: rows jobs until the leader ends the query.
+template <typename VT, int G, int CPL>
+__device__ __noinline__ void team_helper(const Team& tm, int rank, int64_t stride_bytes, int nchunk,
+                                         const float* __restrict__ qs) {
+  const int lane = lane_id();
+  TeamJob* job = tm.job;
+  for (;;) {
+    team_sync(tm);
+    if (job->cmd != 0) break;
+    const int count = job->count;
+    const int mine = (count - rank + tm.size - 1) / tm.size;  // rows rank, rank + T, ...
+    const int32_t id = lane < mine ? job->ids[rank + lane * tm.size] : 0;
+    const float d = rows_dist<VT, G, CPL>(static_cast<const VT*>(job->vec), job->scale, stride_bytes, id, mine, qs,
+                                          nchunk);
+    if (lane < mine) job->dist[rank + lane * tm.size] = d;
+    team_sync(tm);
+  }
+}
+
 // ------------------------------------------------------ visited table
 
 __device__ __forceinline__ bool visit(int32_t* table, int HB, int32_t id, int& evictions) {
@@ -253,11 +318,12 @@ __device__ __forceinline__ int lower_bound_w(const uint64_t* W, int nw, uint64_t
 // copies of the layer above's candidates) and `entry` is ignored.
 // The layer comes as its arrays and size (not a reference to a descriptor,
 // which would put a memory load before every adjacency-row address).
-template <typename VT, int G, int CPL>
+template <typename VT, int G, int CPL, typename TM>
 __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* vec_, const float* __restrict__ scale,
                                  int64_t size, int64_t stride, int nchunk, int32_t entry, int ef, uint64_t* W,
                                  int32_t* table, int HB, uint64_t* stage, const float* qs, int& evals_out,
-                                 int& expansions_out, int& evictions_out, int nseed = 0) {
+                                 int& expansions_out, int& evictions_out, int nseed, const TM tm) {
+  constexpr bool TEAM = std::is_same<TM, Team>::value;
   const int lane = lane_id();
   const unsigned below = (1u << lane) - 1u;  // lanes under this one
   int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
@@ -306,38 +372,28 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     ++expansions;
     const int32_t c = (int32_t)key_index(e & kKeyMask);
     int32_t nb = adj[(int64_t)c * kMmax + lane];
-    // (HENN_SEARCH_NEXT_PREFETCH 0) the next unexpanded entry, a guess at
-    // the next expansion: pull its adjacency line towards the SM
-    if (HENN_SEARCH_NEXT_PREFETCH == 0 && lane == 0 && after >= 0) {
+    // the next unexpanded entry is the likely next expansion: pull its
+    // adjacency line towards the SM while this one is processed (the exact
+    // next node, known once the new candidates are sorted, measured no
+    // faster: the extra work on the critical path outweighs the later hit)
+    if (lane == 0 && after >= 0) {
       const int32_t* nxt = adj + (int64_t)key_index(W[after] & kKeyMask) * kMmax;
       asm volatile("prefetch.global.L1 [%0];" ::"l"(nxt));
     }
-    // the old next unexpanded entry (the next expansion unless a new
-    // candidate comes before it)
-    const uint64_t old_next = after >= 0 ? (W[after] & kKeyMask) : kEmpty;
     __syncwarp();
-    // the node expanded next: its adjacency line, towards the SM
-    auto pull_next = [&](uint64_t nxt) {
-      if (HENN_SEARCH_NEXT_PREFETCH != 0 && lane == 0 && nxt != kEmpty) {
-        const int32_t* p = adj + (int64_t)key_index(nxt) * kMmax;
-        if (HENN_SEARCH_NEXT_PREFETCH == 1)
-          asm volatile("prefetch.global.L1 [%0];" ::"l"(p));
-        else
-          asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
-      }
-    };
     bool fresh = nb >= 0 && mark(nb);
     unsigned fm = __ballot_sync(0xffffffffu, fresh);
     int cnt = __popc(fm);
-    if (cnt == 0) {
-      pull_next(old_next);
-      continue;
-    }
+    if (cnt == 0) continue;
     // compact fresh ids into lanes 0..cnt-1 (lane j gets the j-th fresh one)
     if (fresh) stage32[__popc(fm & below)] = nb;
     __syncwarp();
     const int32_t packed_id = lane < cnt ? stage32[lane] : -1;
-    float dn = rows_dist<VT, G, CPL>(vec, scale, stride, packed_id, cnt, qs, nchunk);
+    float dn;
+    if constexpr (TEAM)
+      dn = team_rows<VT, G, CPL>(tm, vec, scale, stride, packed_id, cnt, qs, nchunk);
+    else
+      dn = rows_dist<VT, G, CPL>(vec, scale, stride, packed_id, cnt, qs, nchunk);
     evals += cnt;
     const uint64_t worst = nw < ef ? kEmpty : (W[nw - 1] & kKeyMask);
     uint64_t kk = lane < cnt ? pack(dn, (uint32_t)packed_id) : kEmpty;
@@ -349,10 +405,7 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     }
     const unsigned cm = __ballot_sync(0xffffffffu, take);
     const int ccnt = __popc(cm);
-    if (ccnt == 0) {
-      pull_next(old_next);
-      continue;
-    }
+    if (ccnt == 0) continue;
     // candidates, compacted, then sorted into stage[0..ccnt); lane j < ccnt
     // holds the j-th smallest and its position in the new W
     __syncwarp();
@@ -365,10 +418,6 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     if (lane < ccnt) stage[rank] = cand;
     __syncwarp();
     cand = lane < ccnt ? stage[lane] : kEmpty;
-    {
-      const uint64_t best_new = __shfl_sync(0xffffffffu, cand, 0);
-      pull_next(best_new < old_next ? best_new : old_next);
-    }
     const int cpos = lane < ccnt ? lower_bound_w(W, nw, cand) + lane : 0x7fffffff;
     const int p0 = __shfl_sync(0xffffffffu, cpos, 0);
     // entries at or after p0 shift right by the number of smaller candidates
@@ -463,7 +512,7 @@ __device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const void* ve
 template <typename VT, int DMAX>
 struct RowShape {
   static constexpr int kChunks = DMAX * (int)sizeof(VT) / 16;
-  static constexpr int G = kChunks <= 32 ? HENN_SEARCH_ROW_LANES : 32;
+  static constexpr int G = kChunks <= 32 ? 8 : 32;
   static constexpr int CPL = (kChunks + G - 1) / G;
 };
 
@@ -537,10 +586,10 @@ __device__ __noinline__ void finish_query(const SearchArgs& a, uint64_t* W, int 
 // One query, one warp: S1-S4 for the query row `qg` (d floats), writing
 // out_stride results to out_ids / out_d and 4 counters to stats (optional).
 // `my` is this warp's shared-memory slice.
-template <typename VT, int DMAX>
+template <typename VT, int DMAX, typename TM>
 __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my, const float* __restrict__ qg, int k,
                                           int ef, uint64_t key, int64_t* out_ids, float* out_d, int32_t* stats,
-                                          const uint64_t* pre_row = nullptr, float pre_qn = 0.f) {
+                                          const uint64_t* pre_row, float pre_qn, const TM tm) {
   constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
   constexpr int G32 = RowShape<float, DMAX>::G, CPL32 = RowShape<float, DMAX>::CPL;
   const int lane = lane_id();
@@ -645,8 +694,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
       __syncwarp();
     } else if (width > 1) {
       int ex = 0;
-      int nw = beam<VT, G, CPL>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, min(width, EFCAP), W, table,
-                                HB, stage, qs, evals, ex, evictions, nseed);
+      int nw = beam<VT, G, CPL, TM>(Ly.adj, Ly.vec, Ly.scale, Ly.size, stride, nchunk, cur, min(width, EFCAP), W,
+                                    table, HB, stage, qs, evals, ex, evictions, nseed, tm);
       moves += ex;
       cur = (int32_t)key_index(W[0] & kKeyMask);
       if (a.descend_all) {
@@ -684,8 +733,8 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
 
   // S3: layer-0 beam
   const SearchLayer B = a.layers[0];
-  int nw = beam<VT, G, CPL>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, table, HB, stage, qs, evals,
-                            expansions, evictions, nseed);
+  int nw = beam<VT, G, CPL, TM>(B.adj, B.vec, B.scale, B.size, stride, nchunk, cur, ef, W, table, HB, stage, qs,
+                                evals, expansions, evictions, nseed, tm);
 
   // S4 + output
   finish_query<G32, CPL32>(a, W, nw, k, qs, out_ids, out_d);
@@ -696,25 +745,61 @@ __device__ __forceinline__ void run_query(const SearchArgs& a, unsigned char* my
     stats[3] = evictions;
   }
   __syncwarp();
+  if constexpr (std::is_same<TM, Team>::value) {
+    // the query is done: release the team's other warps
+    if (lane == 0) tm.job->cmd = 1;
+    __syncwarp();
+    team_sync(tm);
+  }
 }
 
-template <typename VT, int DMAX>
+// TM = Solo: one warp per query.  TM = Team: teams of a.team warps.
+template <typename VT, int DMAX, typename TM>
 __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_search(const __grid_constant__ SearchArgs a) {
+  constexpr int G = RowShape<VT, DMAX>::G, CPL = RowShape<VT, DMAX>::CPL;
+  constexpr bool TEAM = std::is_same<TM, Team>::value;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lane = lane_id();
-  unsigned char* my = smem + (size_t)(threadIdx.x >> 5) * a.warp_smem;
+  const int T = TEAM ? a.team : 1;
+  const int warp = threadIdx.x >> 5, team = warp / T, rank = warp - team * T;
+  unsigned char* my = smem + (size_t)team * a.warp_smem;
+  TM tm;
+  if constexpr (TEAM) {
+    tm.size = T;
+    tm.bar = 1 + team;
+    tm.threads = 32 * T;
+    tm.job = reinterpret_cast<TeamJob*>(my + a.warp_smem - sizeof(TeamJob));
+  }
   for (;;) {
     int64_t qi = 0;
-    if (lane == 0) qi = atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
-    qi = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)qi, 0);
+    if constexpr (!TEAM) {
+      if (lane == 0) qi = atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
+      qi = (int64_t)__shfl_sync(0xffffffffu, (unsigned long long)qi, 0);
+    } else {
+      // the leader takes the team's next query; the others read it after
+      // the barrier (the leader writes it again only after the query's end
+      // barrier, which every warp of the team has reached by then)
+      if (rank == 0 && lane == 0)
+        tm.job->qi = (int64_t)atomicAdd(reinterpret_cast<unsigned long long*>(a.counter), 1ull);
+      team_sync(tm);
+      qi = tm.job->qi;
+    }
     if (qi >= a.nq) break;
+    if constexpr (TEAM) {
+      if (rank != 0) {
+        const int64_t stride = (int64_t)a.dpad * sizeof(VT);
+        const float* qs = reinterpret_cast<const float*>(my + a.ef_cap * 8 + (4 << a.hash_bits) + kStageBytes);
+        team_helper<VT, G, CPL>(tm, rank, stride, (int)(stride / 16), qs);
+        continue;
+      }
+    }
     if (a.order) qi = a.order[qi];
     const int k = a.kq ? a.kq[qi] : a.k_uniform;
     const int ef = a.efq ? a.efq[qi] : a.ef_uniform;
     const uint64_t key = a.keys ? a.keys[qi] : (uint64_t)qi;
     run_query<VT, DMAX>(a, my, a.Q + qi * a.d, k, ef, key, a.out_ids + qi * a.out_stride,
                         a.out_d + qi * a.out_stride, a.stats ? a.stats + qi * 4 : nullptr,
-                        a.pre_keys ? a.pre_keys + qi * 32 : nullptr, a.pre_qnorm ? a.pre_qnorm[qi] : 0.f);
+                        a.pre_keys ? a.pre_keys + qi * 32 : nullptr, a.pre_qnorm ? a.pre_qnorm[qi] : 0.f, tm);
   }
 }
 
@@ -783,7 +868,7 @@ __global__ void __launch_bounds__(128, HENN_SEARCH_MIN_BLOCKS) k_serve(const __g
     const int32_t ef = __ldcg(&s.desc[slot].ef);
     const uint64_t key = __ldcg(&s.desc[slot].key);
     run_query<VT, DMAX>(s.base, my, s.qring + slot * s.base.d, k, ef, key, s.out_ids + slot * s.base.out_stride,
-                        s.out_d + slot * s.base.out_stride, nullptr);
+                        s.out_d + slot * s.base.out_stride, nullptr, nullptr, 0.f, Solo());
     __syncwarp();
     if (lane == 0) {
       __threadfence_system();
@@ -1083,6 +1168,11 @@ size_t search_warp_smem(int ef_cap, int hash_bits, int dpad) {
   return (b + 15) & ~(size_t)15;
 }
 
+size_t search_team_smem(int ef_cap, int hash_bits, int dpad, int team) {
+  const size_t b = search_warp_smem(ef_cap, hash_bits, dpad);
+  return team > 1 ? b + sizeof(TeamJob) : b;
+}
+
 int search_beam_cap(int k, int ef, int ef_upper, int ef_l1, bool rerank, int rerank_mult) {
   int need = max(max(k, ef), max(ef_upper, ef_l1));
   if (rerank) need = max(need, min(ef, rerank_mult * k));
@@ -1110,7 +1200,7 @@ cudaError_t search_persistent_grid(int device, int warps, size_t smem, int* grid
 
 template <typename VT, int DMAX>
 static cudaError_t launch_t(const SearchArgs& a, int warps, int grid, size_t smem, cudaStream_t st) {
-  auto kern = k_search<VT, DMAX>;
+  auto kern = a.team > 1 ? k_search<VT, DMAX, Team> : k_search<VT, DMAX, Solo>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
   kern<<<grid, warps * 32, smem, st>>>(a);
@@ -1155,8 +1245,11 @@ cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cuda
 
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st) {
   SearchArgs b = a;
-  b.warp_smem = (int32_t)search_warp_smem(a.ef_cap, a.hash_bits, a.dpad);
-  size_t smem = (size_t)b.warp_smem * warps_per_block;
+  const int team = a.team > 1 ? a.team : 1;
+  if (warps_per_block % team != 0) return cudaErrorInvalidValue;
+  b.team = team;
+  b.warp_smem = (int32_t)search_team_smem(a.ef_cap, a.hash_bits, a.dpad, team);
+  size_t smem = (size_t)b.warp_smem * (warps_per_block / team);
   if (a.storage == HENN_BF16) return launch_vt<__nv_bfloat16>(b, warps_per_block, grid, smem, st);
   if (a.storage == HENN_FP8E4M3) return launch_vt<__nv_fp8_e4m3>(b, warps_per_block, grid, smem, st);
   return launch_vt<float>(b, warps_per_block, grid, smem, st);

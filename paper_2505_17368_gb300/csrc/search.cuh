@@ -51,7 +51,8 @@ struct SearchArgs {
   int32_t* stats;
   unsigned long long* counter;  // work counter, zero at launch
   const int32_t* order;         // nullptr, or the query of each work slot
-  int32_t warp_smem;            // bytes of shared memory per warp
+  int32_t warp_smem;            // bytes of shared memory per team (per warp when team = 1)
+  int32_t team;                 // warps per query (1, 2 or 4)
 };
 
 // One published work item of the serving loop (one query).
@@ -90,6 +91,9 @@ struct GreedyProbeArgs {
 };
 
 size_t search_warp_smem(int ef_cap, int hash_bits, int dpad);
+// Shared memory of one query's team of `team` warps: the leader's slice as
+// above plus, for team > 1, the job area the team's warps exchange rows in.
+size_t search_team_smem(int ef_cap, int hash_bits, int dpad, int team);
 // Launch shape of k_search, shared by every entry point that runs it.
 // Beam capacity of a query: the power of two (at least 32) that holds its
 // widest list -- k, ef, the upper-layer widths, and with a rerank the

@@ -14,7 +14,10 @@ class _FakeIndex:
 
 def test_candidates_follow_the_beam():
     c = autotune.candidates(10, 64)
-    assert {"warps_per_block": 4, "hash_bits": 10} in c
+    assert {"warps_per_block": 4, "team_size": 1, "hash_bits": 10} in c
+    # team sizes 1, 2 and 4 warps per query, each dividing the block's warps
+    assert {s["team_size"] for s in c} == {1, 2, 4}
+    assert all(s["warps_per_block"] % s["team_size"] == 0 for s in c)
     assert all(8 <= s["hash_bits"] <= 15 for s in c)
     big = autotune.candidates(10, 512, ef_upper=64)
     assert max(s["hash_bits"] for s in big) > max(s["hash_bits"] for s in c)
@@ -32,11 +35,12 @@ def test_tune_picks_fastest_and_caches(tmp_path):
 
     def timer(shape):
         calls.append(shape)
-        return 1.0 + 0.1 * shape["hash_bits"] - (0.5 if shape["warps_per_block"] == 2 else 0.0)
+        return (1.0 + 0.1 * shape["hash_bits"] - (0.5 if shape["warps_per_block"] == 2 else 0.0)
+                - (0.2 if shape["team_size"] == 2 else 0.0))
 
     path = str(tmp_path / "cache.json")
     best = autotune.tune(_FakeIndex(), Q, k=10, ef=64, cache_path=path, timer=timer)
-    assert best["warps_per_block"] == 2
+    assert best["warps_per_block"] == 2 and best["team_size"] == 2
     assert best["hash_bits"] == min(s["hash_bits"] for s in autotune.candidates(10, 64))
     n_first = len(calls)
     again = autotune.tune(_FakeIndex(), Q, k=10, ef=64, cache_path=path, timer=timer)
