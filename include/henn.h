@@ -219,6 +219,8 @@ typedef struct {
                                  of every beam expansion (shorter latency per
                                  query, fewer queries in flight); results do not
                                  depend on it.  Must divide warps_per_block     */
+  int32_t tile_n;             /* columns per tensor-core tile of exact_method
+                                 TILES: 128 or 256 (0 = 256); same results      */
 } henn_search_params;
 
 /* exact_method values */

@@ -3,13 +3,15 @@
 For an index, a batch size and a beam configuration, times henn_search over
 a small grid of launch shapes -- warps per block, warps per query (the team
 size: a team shares each expansion's distance work, which shortens a query
-but leaves fewer queries in flight) and the size of the per-query visited
-table -- and keeps the fastest.  Results are cached in a JSON file keyed by
+but leaves fewer queries in flight), the size of the per-query visited
+table and, for an exact layer from tensor-core tiles, the tile's width
+(128 x 128 or 128 x 256) -- and keeps the fastest.  Results are cached in a JSON file keyed by
 (n, d, storage, batch bucket, k, ef, ef_upper, ef_l1, descend_all, exact
 layer, rerank), so a process pays the sweep once per shape.  No knob
 changes results: the visited table may forget entries without changing the
 answer, a row's distance does not depend on which warp of a team computes
-it, and queries are independent of the grid.
+it nor a tile value on the tile's width, and queries are independent of the
+grid.
 
     shape = autotune.tune(index, Q_device, k=10, ef=64, ef_upper=64)
     ids, d, _ = index.search(Q_device, k=10, ef=64, ef_upper=64, **shape)
@@ -46,18 +48,24 @@ def candidates(k, ef, ef_upper=1, ef_l1=0, exact_upper=0, exact_method=0):
     table's space)."""
     hb = _default_hash_bits(_beam_cap(k, ef, ef_upper, ef_l1))
     need = exact_upper if exact_method == 0 else 0
+    # the tensor-core tile shape of the batched exact layer (exact_method 1)
+    tiles = (256, 128) if exact_method == 1 and exact_upper > 0 else (0,)
     out = []
     for w, t in ((4, 1), (2, 1), (4, 2), (2, 2), (4, 4)):
         for h in (hb - 2, hb - 1, hb, hb + 1):
             if 8 <= h <= 15 and (1 << (h - 1)) >= need:
-                out.append({"warps_per_block": w, "team_size": t, "hash_bits": h})
+                for n in tiles:
+                    shape = {"warps_per_block": w, "team_size": t, "hash_bits": h}
+                    if n:
+                        shape["tile_n"] = n
+                    out.append(shape)
     return out
 
 
 def _key(index, nq, k, ef, ef_upper, ef_l1, descend_all, exact_upper=0, exact_method=0, rerank_mult=4):
     bucket = 1 << max(0, int(math.ceil(math.log2(max(nq, 1)))))
     return (f"n={index.n},d={index.d},s={index.storage},b={bucket},k={k},ef={ef},eu={ef_upper},l1={ef_l1},"
-            f"da={descend_all},xu={exact_upper},xm={exact_method},rm={rerank_mult},v=team")
+            f"da={descend_all},xu={exact_upper},xm={exact_method},rm={rerank_mult},v=team,tile")
 
 
 def _load(path):

@@ -114,6 +114,7 @@ class SearchParams(C.Structure):
         ("exact_method", C.c_int32),
         ("time_kernel", C.c_int32),
         ("team_size", C.c_int32),
+        ("tile_n", C.c_int32),
     ]
 
 
@@ -366,7 +367,7 @@ class Index:
 
     def search(self, Q, k=10, ef=64, rerank_mult=4, keys=None, out_stride=None, stats=False,
                warps_per_block=0, hash_bits=0, ef_upper=1, descend_all=0, ef_l1=0, stream=None, out=None,
-               exact_upper=0, exact_method=EXACT_SORT, time_kernel=False, team_size=0):
+               exact_upper=0, exact_method=EXACT_SORT, time_kernel=False, team_size=0, tile_n=0):
         """Batched query.  Q on the device -> device outputs (torch); Q on the
         host -> host outputs (numpy), copies inside the call.
         k / ef: int or per-query int32 array on the same side as Q.
@@ -376,6 +377,7 @@ class Index:
         a certified rescore (EXACT_TILES) or a scan (EXACT_SCAN).
         time_kernel: record the search launches' device time (last_search_ms).
         team_size: warps per query (1, 2 or 4; same results).
+        tile_n: columns per tensor-core tile of the TILES exact layer (128 or 256; same results).
         Returns (ids int64 [nq, stride], dists float32 [nq, stride], stats or None)."""
         L = load()
         sp = SearchParams()
@@ -414,6 +416,7 @@ class Index:
         sp.exact_method = int(exact_method)
         sp.time_kernel = int(bool(time_kernel))
         sp.team_size = int(team_size)
+        sp.tile_n = int(tile_n)
         if keys is not None:
             p, _, kk = _ptr(keys)
             sp.query_keys = p

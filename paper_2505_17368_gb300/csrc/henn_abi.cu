@@ -247,7 +247,7 @@ struct henn_index {
     int32_t engine = 0;  // HENN_TILES_TCGEN05 or HENN_TILES_SIMT
     void* hi = nullptr;
     void* lo = nullptr;
-    alignas(64) unsigned char maps[256];  // tensor maps of hi / lo (tcgen05)
+    alignas(64) unsigned char maps[512];  // tensor maps of hi / lo for 256- and 128-column tiles (tcgen05)
     float* xo = nullptr;
     float* mean = nullptr;
     float* norms = nullptr;
@@ -1099,6 +1099,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     require(warps >= 1 && warps <= kSearchWarps, "warps_per_block must be in [1, 4]");
     const int team = sp.team_size > 0 ? sp.team_size : 1;
     require(team == 1 || team == 2 || team == 4, "team_size must be 1, 2 or 4");
+    require(sp.tile_n == 0 || sp.tile_n == 128 || sp.tile_n == 256, "tile_n must be 0, 128 or 256");
     require(warps % team == 0, "team_size must divide warps_per_block");
     const int teams = warps / team;  // queries in flight per block
 
@@ -1218,12 +1219,12 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
           for (int64_t q0 = 0; q0 < nq; q0 += qc) {
             const int64_t cn = std::min<int64_t>(qc, nq - q0);
             CK(launch_tile_cross_tc(static_cast<uint16_t*>(qh) + q0 * dkk, static_cast<uint16_t*>(ql) + q0 * dkk,
-                                    qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, st));
+                                    qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, sp.tile_n, st));
             launch_select_top32(dm, cn, s, ldo, pkeys + q0 * 32, true, st);
             launches += q0 > 0 ? 2 : 1;
           }
         } else {
-          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, st));
+          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, sp.tile_n, st));
         }
         a.pre_tile_u = tc_tile_unit_error(dkk);
         launches += 2;

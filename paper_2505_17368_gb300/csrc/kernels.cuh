@@ -82,12 +82,14 @@ void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void
 // columns (a layer's points), out = na x 32 keys (distance, column); with
 // out_d (mode 3) the distances themselves instead, na rows of ldo floats
 // (ldo a multiple of 32, >= nb; +inf past column nb)
-// b_maps: the two tensor maps (hi, lo) of make_column_maps, 128 bytes each
+// b_maps: the four tensor maps of make_column_maps, 128 bytes each;
+// tile_n: columns per tile, 128 or 256 (0 = 256), the same results
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, int32_t* err, cudaStream_t st);
+                                 float* out_d, int64_t ldo, int32_t* err, int32_t tile_n, cudaStream_t st);
 // Tensor maps of the column operand (hi, lo planes of nb rows, dk wide) for
-// launch_tile_cross_tc, written to maps (2 x 128 bytes); false if not encodable.
+// launch_tile_cross_tc -- hi and lo for tiles of 256 columns, then for 128 --
+// written to maps (4 x 128 bytes); false if not encodable.
 bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk, void* maps);
 // exact FP32 rerank of layer candidates -> forward lists (layer-local ids)
 void launch_rerank_fwd(const float* xw, const int32_t* ids, int64_t s, int32_t dpad, int32_t metric,

@@ -47,23 +47,24 @@ namespace henn {
 namespace tc {
 
 constexpr int BM = 128;          // rows per block (TMEM lanes)
-constexpr int BN = 256;          // columns per tile (UMMA N)
+constexpr int BN_MAX = 256;      // columns per tile, the wider choice (UMMA N = 128 or 256)
 constexpr int BK = 64;           // BF16 values per 128-byte swizzle row
 constexpr int NS = 3;            // B pipeline stages (resident A)
 constexpr int NS_STR = 5;        // pipeline stages (streamed A)
 constexpr int A_CHUNK = BM * BK * 2;  // 16 KB
-constexpr int B_CHUNK = BN * BK * 2;  // 32 KB
+constexpr int STAGE = 32768;     // bytes of one stage of the streamed pipeline
 constexpr int MAX_KC_RES = 2;    // resident A: dpad <= 128, at most 2 chunks of 64 per plane
 constexpr int MAX_KC = 16;       // streamed A: dpad <= 1024
 constexpr int KP = 32;
 constexpr int S_LD = 33;
 constexpr long long kSpinLimit = 1ll << 18;  // x 20 us hint: seconds at most
 
-// Resident A (rows of at most 128 values).
+// Resident A (rows of at most 128 values); BN columns per tile.
+template <int BN>
 struct SmemRes {
   // 1024-byte aligned operand buffers first
   uint8_t a[2 * MAX_KC_RES][A_CHUNK];  // hi chunks then lo chunks
-  uint8_t b[NS][B_CHUNK];
+  uint8_t b[NS][BN * BK * 2];
   // running top-KP of each row: a max-heap of keys, 1-based (children of
   // p at 2p and 2p + 1, so a sibling pair is one 16-byte load), root = the
   // KP-th smallest so far; slot KP + 1 holds 0 (no child), slot 0 is unused
@@ -78,8 +79,9 @@ struct SmemRes {
 // Streamed A (wider rows): a ring of 32 KB stages, each holding the A slice
 // of one 64-wide slice (hi plane, then lo plane) or one plane of a B slice;
 // the rest as above.
+template <int BN>
 struct SmemStr {
-  uint8_t ring[NS_STR][B_CHUNK];
+  uint8_t ring[NS_STR][STAGE];
   uint64_t heap[BM][KP + 2];
   alignas(16) float ncol[4][BN];
   float s[4][32][S_LD];
@@ -165,15 +167,18 @@ __device__ __forceinline__ uint64_t smem_desc(const void* p) {
 }
 
 // Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major,
-// N = 256, M = 128.
-constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) |
-                            ((uint32_t)(BM >> 4) << 24);
+// N = BN, M = 128.
+template <int BN>
+__device__ __forceinline__ constexpr uint32_t idesc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(BN >> 3) << 17) | ((uint32_t)(BM >> 4) << 24);
+}
 
+template <int BN>
 __device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
   asm volatile(
       "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
       " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem_d),
-      "l"(adesc), "l"(bdesc), "r"(kIdesc), "r"(accumulate)
+      "l"(adesc), "l"(bdesc), "r"(idesc<BN>()), "r"(accumulate)
       : "memory");
 }
 
@@ -219,7 +224,7 @@ __device__ __forceinline__ void heap_replace(uint64_t* heap, uint64_t key) {
 
 using namespace tc;
 
-template <bool kStream>
+template <bool kStream, int BN>
 __global__ void __launch_bounds__(192, 1)
     k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
@@ -227,8 +232,9 @@ __global__ void __launch_bounds__(192, 1)
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
                    int32_t nsplit, int32_t* __restrict__ err, long long spin_limit, int32_t hold) {
-  using Smem = typename std::conditional<kStream, SmemStr, SmemRes>::type;
+  using Smem = typename std::conditional<kStream, SmemStr<BN>, SmemRes<BN>>::type;
   constexpr int NST = kStream ? NS_STR : NS;
+  constexpr int B_CHUNK = BN * BK * 2;  // one plane of a B slice
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   Smem& sm = *reinterpret_cast<Smem*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~(uintptr_t)1023);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -359,9 +365,9 @@ __global__ void __launch_bounds__(192, 1)
             for (int k = 0; k < BK / 16; ++k) {
               const uint64_t bd = tc::smem_desc(sm.b[st] + k * 32);
               // B_hi pairs with A_hi and A_lo; B_lo pairs with A_hi
-              tc::mma_bf16(dt, tc::smem_desc(sm.a[slice] + k * 32), bd, acc);
+              tc::mma_bf16<BN>(dt, tc::smem_desc(sm.a[slice] + k * 32), bd, acc);
               acc = 1;
-              if (!b_is_lo) tc::mma_bf16(dt, tc::smem_desc(sm.a[MAX_KC_RES + slice] + k * 32), bd, 1);
+              if (!b_is_lo) tc::mma_bf16<BN>(dt, tc::smem_desc(sm.a[MAX_KC_RES + slice] + k * 32), bd, 1);
             }
             tc::mma_commit(&sm.empty[st]);
           }
@@ -380,9 +386,9 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k) {
               const uint64_t bd = tc::smem_desc(sm.ring[sh] + k * 32);
-              tc::mma_bf16(dt, tc::smem_desc(a_hi + k * 32), bd, acc);
+              tc::mma_bf16<BN>(dt, tc::smem_desc(a_hi + k * 32), bd, acc);
               acc = 1;
-              tc::mma_bf16(dt, tc::smem_desc(a_lo + k * 32), bd, 1);
+              tc::mma_bf16<BN>(dt, tc::smem_desc(a_lo + k * 32), bd, 1);
             }
             tc::mma_commit(&sm.empty[sh]);
             if (!tc::mbar_wait(&sm.full[sl], (uint32_t)(((it + 2) / NST) & 1), abort_flag, spin_limit)) {
@@ -393,7 +399,7 @@ __global__ void __launch_bounds__(192, 1)
             // B lo pairs with A hi
 #pragma unroll
             for (int k = 0; k < BK / 16; ++k)
-              tc::mma_bf16(dt, tc::smem_desc(a_hi + k * 32), tc::smem_desc(sm.ring[sl] + k * 32), 1);
+              tc::mma_bf16<BN>(dt, tc::smem_desc(a_hi + k * 32), tc::smem_desc(sm.ring[sl] + k * 32), 1);
             tc::mma_commit(&sm.empty[sa]);
             tc::mma_commit(&sm.empty[sl]);
           }
@@ -650,12 +656,15 @@ static bool make_map(CUtensorMap* m, const void* base, int64_t rows, int32_t dk,
 
 bool tc_tiles_supported(int32_t dpad, int32_t KPv) { return dpad <= BK * MAX_KC && KPv == KP; }
 
-static_assert(sizeof(SmemRes) + 1024 <= 227 * 1024, "shared memory of one CTA");
-static_assert(sizeof(SmemStr) + 1024 <= 227 * 1024, "shared memory of one CTA");
-static_assert(sizeof(((SmemRes*)nullptr)->heap) >= 4 * 8192, "mode 3 store boxes fit in the heap space");
-static_assert(offsetof(SmemRes, heap) % 1024 == 0, "store boxes 1024-byte aligned");
-static_assert(offsetof(SmemStr, heap) % 1024 == 0, "store boxes 1024-byte aligned");
-static_assert((2 * A_CHUNK) <= B_CHUNK && A_CHUNK % 1024 == 0, "an A slice (hi | lo) fills one stage");
+static_assert(sizeof(SmemRes<256>) + 1024 <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(SmemStr<256>) + 1024 <= 227 * 1024, "shared memory of one CTA");
+static_assert(sizeof(((SmemRes<128>*)nullptr)->heap) >= 4 * 8192, "mode 3 store boxes fit in the heap space");
+static_assert(offsetof(SmemRes<128>, heap) % 1024 == 0 && offsetof(SmemRes<256>, heap) % 1024 == 0,
+              "store boxes 1024-byte aligned");
+static_assert(offsetof(SmemStr<128>, heap) % 1024 == 0 && offsetof(SmemStr<256>, heap) % 1024 == 0,
+              "store boxes 1024-byte aligned");
+static_assert((2 * A_CHUNK) <= STAGE && BN_MAX * BK * 2 <= STAGE && A_CHUNK % 1024 == 0,
+              "an A slice (hi | lo) or a plane of a B slice fills one stage");
 
 // The kernel variant for kc slices of 64 values per plane, and its shared
 // memory; the dynamic shared-memory attribute is set once per device and
@@ -666,18 +675,25 @@ struct TileVariant {
   size_t smem;
 };
 
-static cudaError_t tile_variant(int32_t kc, TileVariant* v) {
-  static std::atomic<bool> attr_set[2][64];
+static cudaError_t tile_variant(int32_t kc, int32_t bn, TileVariant* v) {
+  static std::atomic<bool> attr_set[4][64];
   const int stream = kc > MAX_KC_RES ? 1 : 0;
-  v->fn = stream ? k_tile_topk_tc<true> : k_tile_topk_tc<false>;
-  v->smem = (stream ? sizeof(SmemStr) : sizeof(SmemRes)) + 1024;
+  const int narrow = bn == 128 ? 1 : 0;
+  const int which = 2 * stream + narrow;
+  switch (which) {
+    case 0: v->fn = k_tile_topk_tc<false, 256>; v->smem = sizeof(SmemRes<256>); break;
+    case 1: v->fn = k_tile_topk_tc<false, 128>; v->smem = sizeof(SmemRes<128>); break;
+    case 2: v->fn = k_tile_topk_tc<true, 256>; v->smem = sizeof(SmemStr<256>); break;
+    default: v->fn = k_tile_topk_tc<true, 128>; v->smem = sizeof(SmemStr<128>); break;
+  }
+  v->smem += 1024;
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
-  if (dev >= 64 || !attr_set[stream][dev].load()) {
+  if (dev >= 64 || !attr_set[which][dev].load()) {
     e = cudaFuncSetAttribute(v->fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v->smem);
     if (e != cudaSuccess) return e;
-    if (dev < 64) attr_set[stream][dev].store(true);
+    if (dev < 64) attr_set[which][dev].store(true);
   }
   return cudaSuccess;
 }
@@ -689,11 +705,11 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   __nv_bfloat16* lo = static_cast<__nv_bfloat16*>(scratch_lo);
   k_split_bf16<<<152 * 8, 256, 0, st>>>(xo, s, dpad, dk, hi, lo);
   CUtensorMap mah, mal, mbh, mbl;
-  if (!make_map(&mah, hi, s, dk, BM) || !make_map(&mal, lo, s, dk, BM) || !make_map(&mbh, hi, s, dk, BN) ||
-      !make_map(&mbl, lo, s, dk, BN))
+  if (!make_map(&mah, hi, s, dk, BM) || !make_map(&mal, lo, s, dk, BM) || !make_map(&mbh, hi, s, dk, BN_MAX) ||
+      !make_map(&mbl, lo, s, dk, BN_MAX))
     return cudaErrorInvalidValue;
   TileVariant v;
-  cudaError_t e = tile_variant(dk / BK, &v);
+  cudaError_t e = tile_variant(dk / BK, BN_MAX, &v);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (s + BM - 1) / BM;
   CUtensorMap none;  // no matrix output in modes 0 and 1
@@ -713,24 +729,25 @@ void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void
 
 bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk, void* maps) {
   CUtensorMap* m = static_cast<CUtensorMap*>(maps);
-  return dk % BK == 0 && dk / BK <= MAX_KC && nb >= 1 && make_map(&m[0], b_hi, nb, dk, BN) &&
-         make_map(&m[1], b_lo, nb, dk, BN);
+  return dk % BK == 0 && dk / BK <= MAX_KC && nb >= 1 && make_map(&m[0], b_hi, nb, dk, 256) &&
+         make_map(&m[1], b_lo, nb, dk, 256) && make_map(&m[2], b_hi, nb, dk, 128) && make_map(&m[3], b_lo, nb, dk, 128);
 }
 
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, int32_t* err, cudaStream_t st) {
+                                 float* out_d, int64_t ldo, int32_t* err, int32_t tile_n, cudaStream_t st) {
+  const int32_t BN = tile_n == 128 ? 128 : 256;
   if (dk % BK != 0 || dk / BK > MAX_KC || na < 1 || nb < 1) return cudaErrorInvalidValue;
   if (out_d && (ldo % 32 != 0 || ldo < nb)) return cudaErrorInvalidValue;
   CUtensorMap mah, mal;
   if (!make_map(&mah, a_hi, na, dk, BM) || !make_map(&mal, a_lo, na, dk, BM)) return cudaErrorInvalidValue;
-  const CUtensorMap& mbh = static_cast<const CUtensorMap*>(b_maps)[0];
-  const CUtensorMap& mbl = static_cast<const CUtensorMap*>(b_maps)[1];
+  const CUtensorMap& mbh = static_cast<const CUtensorMap*>(b_maps)[BN == 128 ? 2 : 0];
+  const CUtensorMap& mbl = static_cast<const CUtensorMap*>(b_maps)[BN == 128 ? 3 : 1];
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   TileVariant v;
-  e = tile_variant(dk / BK, &v);
+  e = tile_variant(dk / BK, BN, &v);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (na + BM - 1) / BM;
   // mode 3: split each row block's tiles over nsplit CTAs (one CTA per SM

@@ -25,7 +25,9 @@ def test_candidates_follow_the_beam():
     # per exact-layer point; tiles and scans use none of them
     sort = autotune.candidates(10, 64, exact_upper=1000, exact_method=0)
     assert sort and all((1 << (s["hash_bits"] - 1)) >= 1000 for s in sort)
-    assert autotune.candidates(10, 64, exact_upper=4000, exact_method=1) == c
+    tiles = autotune.candidates(10, 64, exact_upper=4000, exact_method=1)
+    assert [dict(t) for t in tiles if t.pop("tile_n") == 256] == c  # each shape with 256- and 128-column tiles
+    assert {t["tile_n"] for t in autotune.candidates(10, 64, exact_upper=4000, exact_method=1)} == {128, 256}
     assert autotune.candidates(10, 64, exact_upper=100000, exact_method=0) == []
 
 

@@ -1,7 +1,8 @@
 """The exact upper layer (the nearest points of the lowest layer with at most
 exact_upper points, then the walk below it) found three ways through the C
 ABI: sorted in the visited table (EXACT_SORT), from batched distance tiles
-with a certified rescore (EXACT_TILES: tcgen05 for d <= 128, SIMT above),
+with a certified rescore (EXACT_TILES: tcgen05 tiles of 128 x 256 or
+128 x 128, the row block streamed for rows wider than 128 values),
 and by a scan of the layer (EXACT_SCAN).  The three give the same set, so
 the same answers bit for bit; the answers track the FP64 oracle's exact
 layer.  Tolerances: tests/parity.py.
@@ -186,3 +187,25 @@ def test_full_size_tiles_equal_scan():
     out = _run(gidx, Q[:2000], methods=(H.EXACT_TILES, H.EXACT_SCAN), k=10, ef=48, exact_upper=sizes[1])
     _same(out)
     assert out[H.EXACT_TILES][2][:, 0].sum() < out[H.EXACT_SCAN][2][:, 0].sum()
+
+
+@pytest.mark.parametrize("d", [32, 200])
+def test_tile_widths_give_identical_results(d):
+    """The tile's width (128 or 256 columns) changes how columns are grouped,
+    not how any tile value is summed: the candidates, the certificate and the
+    answers (and the per-query counters) are the same bit for bit."""
+    if d == 32:
+        X, Q, _ = synth.workload("uniform-10k-d32")
+        Q = Q[:600]
+    else:
+        X, r = synth.gaussian_mixture(20000, d, 100, seed=6, rescale_to_255=True)
+        Q, _ = synth.gaussian_mixture(600, d, 100, seed=106, rescale_from=r, rescale_to_255=True)
+    gidx = _gpu_index(X, seed=2, storage=H.BF16)
+    sizes = gidx.info()["sizes"]
+    Qd = torch.from_numpy(np.ascontiguousarray(Q)).to(DEV)
+    for xu, efu, da in [(sizes[1], 16, 1), (sizes[2], 8, 1)]:
+        res = [[t.cpu().numpy() for t in gidx.search(Qd, k=10, ef=48, ef_upper=efu, descend_all=da, exact_upper=xu,
+                                                     exact_method=H.EXACT_TILES, stats=True, tile_n=n)]
+               for n in (256, 128)]
+        for a, b in zip(*res):
+            assert np.array_equal(a, b), (d, xu)
