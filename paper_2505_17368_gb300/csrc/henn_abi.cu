@@ -1008,11 +1008,7 @@ const henn_index::EntryOps& entry_ops(const henn_index* idx, int32_t li, cudaStr
 // whose matrix takes at most a third of L2 (written by the tile launch, read
 // by the selection from L2 and dropped there, so it never reaches DRAM)
 constexpr int64_t kDenseExactMax = 16384;
-// Batched exact layer: queries run in the order of their nearest exact-layer
-// point (1) or in batch order (0); results are the same.
-#ifndef HENN_SEARCH_ORDER_QUERIES
-#define HENN_SEARCH_ORDER_QUERIES 1
-#endif
+
 #ifndef HENN_EXACT_L2_SHARE
 #define HENN_EXACT_L2_SHARE 0  // a chunk's matrix takes at most L2 / this (0: up to 1 GiB, one chunk here)
 #endif
@@ -1246,13 +1242,6 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         launches += splits > 1 ? 3 : 2;
       }
       CKL("exact-layer tiles");
-      if (HENN_SEARCH_ORDER_QUERIES && !d_order && s <= kDenseExactMax) {
-        // one launch: run the queries in the order of their nearest exact-layer point
-        int32_t* o = sc.get<int32_t>(nq);
-        CK(launch_order_by_seed(pkeys, nq, (int32_t)s, o, st));
-        d_order = o;
-        launches += 1;
-      }
       a.pre_keys = pkeys;
       a.pre_qnorm = qn;
       a.pre_nmax = eo.nmax;
@@ -1276,7 +1265,7 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     }
     launches += groups;
     if (groups == 1) {
-      a.order = d_order;  // the order of the nearest exact-layer point, or batch order
+      a.order = d_order;
       size_t smem = search_team_smem(ef_cap, hb, idx->dpad, team) * teams;
       int64_t blocks_needed = (nq + teams - 1) / teams;
       int grid = (int)std::min<int64_t>(persistent_grid(idx->device, warps, smem), blocks_needed);

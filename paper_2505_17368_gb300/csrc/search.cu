@@ -1151,44 +1151,6 @@ __global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t 
   }
 }
 
-// The queries of a batch ordered by their nearest point of the exact layer
-// (the first of their tile candidates): a counting sort in one block, the
-// counters in shared memory.  Queries near each other then run at the same
-// time and share the rows and adjacency lines they read in L2; the order
-// does not change any query's result.
-__global__ void __launch_bounds__(1024) k_order_by_seed(const uint64_t* __restrict__ keys, int64_t nq, int32_t s,
-                                                        int32_t* __restrict__ order) {
-  extern __shared__ int32_t cnt[];  // s + 1 counters
-  const int tid = threadIdx.x;
-  for (int b = tid; b <= s; b += blockDim.x) cnt[b] = 0;
-  __syncthreads();
-  auto bin_of = [&](int64_t q) {
-    const uint32_t i = key_index(keys[q * 32]);
-    return i < (uint32_t)s ? (int32_t)i : s;  // an empty key goes last
-  };
-  for (int64_t q = tid; q < nq; q += blockDim.x) atomicAdd(&cnt[bin_of(q)], 1);
-  __syncthreads();
-  // exclusive prefix sum over the s + 1 counters, one thread's run at a time
-  if (tid == 0) {
-    int32_t run = 0;
-    for (int b = 0; b <= s; ++b) {
-      const int32_t c = cnt[b];
-      cnt[b] = run;
-      run += c;
-    }
-  }
-  __syncthreads();
-  for (int64_t q = tid; q < nq; q += blockDim.x) order[atomicAdd(&cnt[bin_of(q)], 1)] = (int32_t)q;
-}
-
-cudaError_t launch_order_by_seed(const uint64_t* keys, int64_t nq, int32_t s, int32_t* order, cudaStream_t st) {
-  const size_t smem = sizeof(int32_t) * ((size_t)s + 1);
-  cudaError_t e = cudaFuncSetAttribute(k_order_by_seed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  k_order_by_seed<<<1, 1024, smem, st>>>(keys, nq, s, order);
-  return cudaGetLastError();
-}
-
 void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, bool discard,
                          cudaStream_t st) {
   int64_t blocks = (nq + 7) / 8;

@@ -121,9 +121,6 @@ void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, i
 // contents are undefined afterwards).
 void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, bool discard,
                          cudaStream_t st);
-// The batch's queries ordered by the first of their 32 tile keys (a point
-// of a layer of s <= 16384 points): order[j] = the query run j-th.
-cudaError_t launch_order_by_seed(const uint64_t* keys, int64_t nq, int32_t s, int32_t* order, cudaStream_t st);
 cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStream_t st);
 cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st);
 cudaError_t launch_search(const SearchArgs& a, int warps_per_block, int grid, cudaStream_t st);
