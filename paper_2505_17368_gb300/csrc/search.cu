@@ -47,9 +47,29 @@ namespace henn {
 #ifndef HENN_SEARCH_CHUNKS_IN_FLIGHT
 #define HENN_SEARCH_CHUNKS_IN_FLIGHT 4
 #endif
+// The beam's shared-memory pointers re-derived from the dynamic shared
+// memory base (1) or used as passed (0).
+#ifndef HENN_SEARCH_SMEM32
+#define HENN_SEARCH_SMEM32 1
+#endif
 
 
 constexpr int kStageBytes = 32 * 8;     // per-warp staging of one neighbour list
+
+// The kernels' dynamic shared memory (every extern __shared__ array names
+// its start).  Pointers a non-inlined function re-derives from it (base +
+// offset) are known to be shared-memory addresses: 32-bit, read and written
+// without the generic-address translation.
+extern __shared__ __align__(16) unsigned char dyn_smem[];
+template <typename T>
+__device__ __forceinline__ T* as_shared(T* p) {
+#if HENN_SEARCH_SMEM32
+  const size_t off = reinterpret_cast<const unsigned char*>(p) - dyn_smem;
+  return reinterpret_cast<T*>(dyn_smem + off);
+#else
+  return p;
+#endif
+}
 
 // A team of warps answering one query (team_size > 1): the leader warp runs
 // the query; for the neighbour rows of each beam expansion it posts a job
@@ -324,6 +344,10 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
                                  int32_t* table, int HB, uint64_t* stage, const float* qs, int& evals_out,
                                  int& expansions_out, int& evictions_out, int nseed, const TM tm) {
   constexpr bool TEAM = std::is_same<TM, Team>::value;
+  W = as_shared(W);
+  table = as_shared(table);
+  stage = as_shared(stage);
+  qs = as_shared(qs);
   const int lane = lane_id();
   const unsigned below = (1u << lane) - 1u;  // lanes under this one
   int32_t* stage32 = reinterpret_cast<int32_t*>(stage);
@@ -456,6 +480,7 @@ template <typename VT, int G, int CPL>
 __device__ __noinline__ uint64_t exact_top32(const SearchArgs& a, const void* vec_, const float* __restrict__ scale,
                                              int64_t size, int64_t stride, int nchunk, const float* qs,
                                              const uint64_t* pre_row, float pre_qn, int need, int& evals) {
+  qs = as_shared(qs);
   const int lane = lane_id();
   const VT* vec = reinterpret_cast<const VT*>(vec_);
   const int s = (int)size;
@@ -521,6 +546,8 @@ struct RowShape {
 template <int G32, int CPL32>
 __device__ __noinline__ void finish_query(const SearchArgs& a, uint64_t* W, int nw, int k, const float* qs,
                                           int64_t* out_ids, float* out_d) {
+  W = as_shared(W);
+  qs = as_shared(qs);
   const int lane = lane_id();
   const int dpad = a.dpad;
   const int out_k = min(k, a.out_stride);

@@ -3,13 +3,15 @@
     python -m paper_2505_17368_gb300.profile_driver search [--n 1000000] [--nq 10000] [--ef 64] [--ef-upper 64]
                                                           [--descend-all 0] [--ef-l1 0] [--exact-upper 0]
                                                           [--exact-method 0] [--rerank-mult 4]
-    python -m paper_2505_17368_gb300.profile_driver tiles  [--n 200000]
+    python -m paper_2505_17368_gb300.profile_driver tiles  [--n 200000] [--d 128|960]
 
 `search` builds a BF16 index of the n-point prefix of the 1M x 128 mixture
 workload and runs three batched searches (profile the third launch of
 k_search; with --exact-method 1 each search is a query-preparation launch,
 a k_tile_topk_tc launch (after the five of the build) and k_search); `tiles` builds an index with the tcgen05 tile engine (the first
-k_tile_topk_tc launch is layer 0).  Both print a one-line summary.
+k_tile_topk_tc launch is layer 0) on the n-point prefix of the 1M x 128
+mixture, or with --d 960 of the 1M x 960 one (rows streamed through the
+tile pipeline).  Both print a one-line summary.
 """
 from __future__ import annotations
 
@@ -39,9 +41,10 @@ def main():
     ap.add_argument("--exact-upper", type=int, default=0)
     ap.add_argument("--exact-method", type=int, default=0)
     ap.add_argument("--rerank-mult", type=int, default=4)
+    ap.add_argument("--d", type=int, default=128, choices=[128, 960])
     a = ap.parse_args()
     n = a.n or (1_000_000 if a.what == "search" else 200_000)
-    X, Q, _ = synth.workload("mixture-1m-d128", n=n, nq=a.nq)
+    X, Q, _ = synth.workload("mixture-1m-d128" if a.d == 128 else "mixture-1m-d960", n=n, nq=a.nq)
     Xd = torch.from_numpy(X).cuda()
     if a.what == "tiles":
         idx = H.Index(Xd, storage=H.BF16, seed=0, tiles=H.TILES_TCGEN05)
