@@ -1217,15 +1217,20 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
           int64_t qc = (int64_t)(chunk_bytes / (4.0 * (double)ldo)) / 128 * 128;
           qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
           float* dm = sc.get<float>((size_t)qc * ldo);
+          // each row's 32-column chunk minima: whole 256-column tiles, 8 per tile
+          const int64_t ldc = (s + 255) / 256 * 8;
+          float* cmn = sc.get<float>((size_t)qc * ldc);
           for (int64_t q0 = 0; q0 < nq; q0 += qc) {
             const int64_t cn = std::min<int64_t>(qc, nq - q0);
             CK(launch_tile_cross_tc(static_cast<uint16_t*>(qh) + q0 * dkk, static_cast<uint16_t*>(ql) + q0 * dkk,
-                                    qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, perr, sp.tile_n, st));
-            launch_select_top32(dm, cn, s, ldo, pkeys + q0 * 32, true, st);
+                                    qn + q0, cn, eo.maps, eo.norms, s, dkk, nullptr, dm, ldo, cmn, ldc, perr,
+                                    sp.tile_n, st));
+            launch_select_top32(dm, cmn, cn, s, ldo, ldc, pkeys + q0 * 32, true, st);
             launches += q0 > 0 ? 2 : 1;
           }
         } else {
-          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, perr, sp.tile_n, st));
+          CK(launch_tile_cross_tc(qh, ql, qn, nq, eo.maps, eo.norms, s, dkk, pkeys, nullptr, 0, nullptr, 0, perr,
+                                  sp.tile_n, st));
         }
         a.pre_tile_u = tc_tile_unit_error(dkk);
         launches += 2;

@@ -84,9 +84,12 @@ void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void
 // (ldo a multiple of 32, >= nb; +inf past column nb)
 // b_maps: the four tensor maps of make_column_maps, 128 bytes each;
 // tile_n: columns per tile, 128 or 256 (0 = 256), the same results
+// out_cmin (mode 3, nullable): each row's minimum over every 32-column chunk,
+// rows of ldc floats (ldc a multiple of 8 covering every tile, 16-byte aligned)
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, int32_t* err, int32_t tile_n, cudaStream_t st);
+                                 float* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err, int32_t tile_n,
+                                 cudaStream_t st);
 // Tensor maps of the column operand (hi, lo planes of nb rows, dk wide) for
 // launch_tile_cross_tc -- hi and lo for tiles of 256 columns, then for 128 --
 // written to maps (4 x 128 bytes); false if not encodable.

@@ -231,6 +231,7 @@ __global__ void __launch_bounds__(192, 1)
                    const __grid_constant__ CUtensorMap to_d,
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
                    int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
+                   float* __restrict__ out_cmin, int64_t ldc,
                    int32_t nsplit, int32_t* __restrict__ err, long long spin_limit, int32_t hold) {
   using Smem = typename std::conditional<kStream, SmemStr<BN>, SmemRes<BN>>::type;
   constexpr int NST = kStream ? NS_STR : NS;
@@ -458,6 +459,8 @@ __global__ void __launch_bounds__(192, 1)
         const int64_t c = (int64_t)(t + 1) * BN + q * 32 + lane;
         pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
       }
+      if (mode == 3 && out_cmin)
+        for (int q = 0; q < BN / 32; ++q) sm.s[ew][lane][q] = kInf;
       __syncwarp();
 #pragma unroll 1
       for (int q = 0; q < BN / 32; ++q) {
@@ -476,14 +479,17 @@ __global__ void __launch_bounds__(192, 1)
           __syncwarp();
           const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
           float4* brow = reinterpret_cast<float4*>(buf + lane * 32);
+          float cmin = kInf;  // the chunk's minimum for this row (fminf passes over a NaN)
           if (c0 + 32 <= sc) {  // warp-uniform: every column of the chunk valid
 #pragma unroll
             for (int j4 = 0; j4 < 8; ++j4) {
               const float4 nn = n4[j4];
-              brow[j4 ^ (lane & 7)] = make_float4(max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 0], nn.x)),
-                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 1], nn.y)),
-                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 2], nn.z)),
-                                                  max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 3], nn.w)));
+              const float4 o4 = make_float4(max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 0], nn.x)),
+                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 1], nn.y)),
+                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 2], nn.z)),
+                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 3], nn.w)));
+              brow[j4 ^ (lane & 7)] = o4;
+              cmin = fminf(cmin, fminf(fminf(o4.x, o4.y), fminf(o4.z, o4.w)));
             }
           } else {
 #pragma unroll
@@ -492,11 +498,14 @@ __global__ void __launch_bounds__(192, 1)
               const float nc[4] = {nn.x, nn.y, nn.z, nn.w};
               float o[4];
 #pragma unroll
-              for (int e = 0; e < 4; ++e)
+              for (int e = 0; e < 4; ++e) {
                 o[e] = c0 + 4 * j4 + e < sc ? max_nan0(nrow + fmaf(-2.f, v[4 * j4 + e], nc[e])) : kInf;
+                cmin = fminf(cmin, o[e]);
+              }
               brow[j4 ^ (lane & 7)] = make_float4(o[0], o[1], o[2], o[3]);
             }
           }
+          if (out_cmin) sm.s[ew][lane][q] = cmin;
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           __syncwarp();
           if (lane == 0) tc::tma_store_2d(&to_d, buf, (int)c0, (int)(r0 + 32 * sub));
@@ -552,6 +561,13 @@ __global__ void __launch_bounds__(192, 1)
           } while (keep);
         }
         __syncwarp();
+      }
+      if (mode == 3 && out_cmin && grow < s) {
+        // this row's chunk minima of the tile, BN / 32 floats, as 16-byte stores
+        float4* dst = reinterpret_cast<float4*>(out_cmin + grow * ldc + (int64_t)t * (BN / 32));
+        const float* src = sm.s[ew][lane];
+#pragma unroll
+        for (int j = 0; j < BN / 128; ++j) dst[j] = make_float4(src[4 * j], src[4 * j + 1], src[4 * j + 2], src[4 * j + 3]);
       }
       tc::fence_before();
       __syncwarp();
@@ -671,7 +687,8 @@ static_assert((2 * A_CHUNK) <= STAGE && BN_MAX * BK * 2 <= STAGE && A_CHUNK % 10
 // variant.
 struct TileVariant {
   void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const float*, const float*, int64_t,
-             int64_t, int32_t, int32_t, uint64_t*, float*, int64_t, int32_t, int32_t*, long long, int32_t);
+             int64_t, int32_t, int32_t, uint64_t*, float*, int64_t, float*, int64_t, int32_t, int32_t*, long long,
+             int32_t);
   size_t smem;
 };
 
@@ -718,7 +735,7 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
   int32_t hold;
   wait_policy(&spin_limit, &hold);
   v.fn<<<(unsigned)nrb, 192, v.smem, st>>>(mah, mal, mbh, mbl, none, norms, norms, s, s, dk / BK, mode, out, nullptr,
-                                           0, 1, err, spin_limit, hold);
+                                           0, nullptr, 0, 1, err, spin_limit, hold);
   return cudaGetLastError();
 }
 
@@ -735,10 +752,15 @@ bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk
 
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, int32_t* err, int32_t tile_n, cudaStream_t st) {
+                                 float* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err, int32_t tile_n,
+                                 cudaStream_t st) {
   const int32_t BN = tile_n == 128 ? 128 : 256;
   if (dk % BK != 0 || dk / BK > MAX_KC || na < 1 || nb < 1) return cudaErrorInvalidValue;
   if (out_d && (ldo % 32 != 0 || ldo < nb)) return cudaErrorInvalidValue;
+  // chunk minima: rows of ldc floats covering every tile's BN / 32 chunks, 16-byte aligned
+  if (out_cmin && (!out_d || ldc % 8 != 0 || ldc * 32 < (nb + 255) / 256 * 256 ||
+                   (reinterpret_cast<uintptr_t>(out_cmin) & 15) != 0))
+    return cudaErrorInvalidValue;
   CUtensorMap mah, mal;
   if (!make_map(&mah, a_hi, na, dk, BM) || !make_map(&mal, a_lo, na, dk, BM)) return cudaErrorInvalidValue;
   const CUtensorMap& mbh = static_cast<const CUtensorMap*>(b_maps)[BN == 128 ? 2 : 0];
@@ -774,7 +796,8 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   int32_t hold;
   wait_policy(&spin_limit, &hold);
   v.fn<<<(unsigned)(nrb * nsplit), 192, v.smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
-                                                     out_d ? 3 : 2, out, out_d, ldo, nsplit, err, spin_limit, hold);
+                                                     out_d ? 3 : 2, out, out_d, ldo, out_cmin, ldc, nsplit, err,
+                                                     spin_limit, hold);
   return cudaGetLastError();
 }
 

@@ -1096,96 +1096,104 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 
 // One warp per query: the 32 smallest (distance, column) keys of its row of
 // a tile distance matrix (+inf entries never enter), ascending, one per
-// lane.  Pass 1: each lane's minimum over the even and over the odd columns
-// of its 4 per 128-column step (64 disjoint column groups); the 32nd
-// smallest of those 64 minima, T, is >= the row's 32nd smallest value (32
-// distinct columns lie at or below it).  Pass 2 (the
-// row again, now mostly from L2) merges only entries <= T into the running
-// list: a few passing keys by shuffle insertion, many by sorting the batch
-// and a bitonic merge.
-__global__ void k_select_top32(const float* __restrict__ D, int64_t nq, int64_t s, int64_t ldo,
-                               uint64_t* __restrict__ out, int32_t discard) {
+// lane.  The tile launch also wrote each row's minimum over every 32-column
+// chunk (cmin, rows of ldc floats).  T = the 32nd smallest of those chunk
+// minima bounds the row's 32nd smallest value (32 distinct columns lie at
+// or below it), and a column at or below T lies in a chunk whose minimum is
+// at or below T: only those chunks (32 of them, plus ties) are read, four
+// 128-byte chunks at a time, and their entries <= T merged into the running
+// list -- a few by shuffle insertion, many by sorting the batch and a
+// bitonic merge.  The result is the row's 32 smallest keys, as a full scan
+// would give; with `discard` each line read is dropped from L2 afterwards.
+__global__ void k_select_top32(const float* __restrict__ D, const float* __restrict__ cmin, int64_t nq, int64_t s,
+                               int64_t ldo, int64_t ldc, uint64_t* __restrict__ out, int32_t discard) {
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
-  const float4 kInf4 = make_float4(kInf, kInf, kInf, kInf);
+  const int nch = (int)(ldo / 32);
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
-    const float4* row = reinterpret_cast<const float4*>(D + q * ldo);
-    const int64_t n4 = ldo / 4;  // float4 per row
-    float m1 = kInf, m2 = kInf;  // minima of this lane's two groups (fminf skips NaN)
-    for (int64_t i = lane; i < n4; i += 32) {
-      const float4 v = __ldg(row + i);
-      m1 = fminf(m1, fminf(v.x, v.z));
-      m2 = fminf(m2, fminf(v.y, v.w));
+    const float* cm = cmin + q * ldc;
+    // the 32 smallest chunk minima, kept sorted across the warp
+    float best = kInf;
+    for (int g = 0; g < nch; g += 32) {
+      float v = g + lane < nch ? __ldg(cm + g + lane) : kInf;
+      v = __shfl_sync(0xffffffffu, warp_sort_asc_f32(v), 31 - lane);
+      float r = fminf(best, v);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) {
+        const float x = __shfl_xor_sync(0xffffffffu, r, o);
+        r = (lane & o) == 0 ? fminf(x, r) : fmaxf(x, r);
+      }
+      best = r;
     }
-    // the 32 smallest of the 64 minima: sort both sets across the warp;
-    // the element-wise minimum of one and the other reversed holds them,
-    // and T is their largest
-    const float s1 = warp_sort_asc_f32(m1);
-    const float s2 = __shfl_sync(0xffffffffu, warp_sort_asc_f32(m2), 31 - lane);
-    float T = fminf(s1, s2);
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) T = fmaxf(T, __shfl_xor_sync(0xffffffffu, T, o));
+    const float T = __shfl_sync(0xffffffffu, best, 31);
     uint64_t mine = kEmpty, worst = kEmpty;
-    float4 nxt = lane < n4 ? __ldcs(row + lane) : kInf4;
-    for (int64_t i0 = 0; i0 < n4; i0 += 32) {
-      const float4 cur = nxt;
-      nxt = i0 + 32 + lane < n4 ? __ldcs(row + i0 + 32 + lane) : kInf4;
-      const bool any4 = cur.x <= T || cur.y <= T || cur.z <= T || cur.w <= T;
-      if (!__any_sync(0xffffffffu, any4)) continue;
-      const float dvs[4] = {cur.x, cur.y, cur.z, cur.w};
-      const int64_t cbase = 4 * (i0 + lane);
+    const float* row = D + q * ldo;
+    for (int g = 0; g < nch; g += 32) {
+      const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
+      unsigned m = __ballot_sync(0xffffffffu, in);
+      while (m) {
+        // up to four of the chunks at a time: their loads in flight together
+        int ch[4];
+        float dv[4];
 #pragma unroll
-      for (int e = 0; e < 4; ++e) {
-        const float dv = dvs[e];
-        uint64_t kk = (dv <= T && !isinf(dv)) ? pack(dv, (uint32_t)(cbase + e)) : kEmpty;
-        unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
-        if (!bm) continue;
-        if (__popc(bm) > 6) {
-          kk = shfl64(warp_sort_asc(kk), 31 - lane);
-          uint64_t r = mine < kk ? mine : kk;
-#pragma unroll
-          for (int j = 16; j > 0; j >>= 1) {
-            const uint64_t o = shfl_xor64(r, j);
-            r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
-          }
-          mine = r;
-        } else {
-          do {
-            const int src = __ffs(bm) - 1;
-            bm &= bm - 1;
-            const uint64_t x = shfl64(kk, src);
-            if (x < worst) {
-              const int pos = __popc(__ballot_sync(0xffffffffu, mine < x));
-              const uint64_t up = shfl64(mine, lane > 0 ? lane - 1 : 0);
-              mine = lane < pos ? mine : (lane == pos ? x : up);
-              worst = shfl64(mine, 31);
-            }
-          } while (bm);
+        for (int b = 0; b < 4; ++b) {
+          ch[b] = m ? g + __ffs(m) - 1 : -1;
+          if (m) m &= m - 1;
+          dv[b] = ch[b] >= 0 ? __ldcs(row + (int64_t)ch[b] * 32 + lane) : kInf;
         }
-        worst = shfl64(mine, 31);
+#pragma unroll
+        for (int b = 0; b < 4; ++b) {
+          if (ch[b] < 0) continue;  // warp-uniform
+          const float x = dv[b];
+          uint64_t kk = (x <= T && !isinf(x)) ? pack(x, (uint32_t)(ch[b] * 32 + lane)) : kEmpty;
+          unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
+          if (!bm) continue;
+          if (__popc(bm) > 6) {
+            kk = shfl64(warp_sort_asc(kk), 31 - lane);
+            uint64_t r = mine < kk ? mine : kk;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+              const uint64_t o = shfl_xor64(r, j);
+              r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+            }
+            mine = r;
+          } else {
+            do {
+              const int src = __ffs(bm) - 1;
+              bm &= bm - 1;
+              const uint64_t x64 = shfl64(kk, src);
+              if (x64 < worst) {
+                const int pos = __popc(__ballot_sync(0xffffffffu, mine < x64));
+                const uint64_t up = shfl64(mine, lane > 0 ? lane - 1 : 0);
+                mine = lane < pos ? mine : (lane == pos ? x64 : up);
+                worst = shfl64(mine, 31);
+              }
+            } while (bm);
+          }
+          worst = shfl64(mine, 31);
+        }
       }
     }
     out[q * 32 + lane] = mine;
     // the row is not read again: drop its lines from L2 without writing
-    // them back (the buffer is rewritten or freed next), so a matrix that
-    // fit in L2 never reaches DRAM
+    // them back (the buffer is rewritten or freed next)
     __syncwarp();
     if (discard) {
-      const char* rb = reinterpret_cast<const char*>(D + q * ldo);
+      const char* rb = reinterpret_cast<const char*>(row);
       for (int64_t l = lane; l < ldo / 32; l += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(rb + l * 128) : "memory");
     }
   }
 }
 
-void launch_select_top32(const float* D, int64_t nq, int64_t s, int64_t ldo, uint64_t* out, bool discard,
-                         cudaStream_t st) {
+void launch_select_top32(const float* D, const float* cmin, int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
+                         uint64_t* out, bool discard, cudaStream_t st) {
   int64_t blocks = (nq + 7) / 8;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
   // discard works on whole 128-byte lines: rows must start on one
   const bool lines = (reinterpret_cast<uintptr_t>(D) & 127) == 0 && ldo % 32 == 0;
-  k_select_top32<<<(int)blocks, 256, 0, st>>>(D, nq, s, ldo, out, discard && lines ? 1 : 0);
+  k_select_top32<<<(int)blocks, 256, 0, st>>>(D, cmin, nq, s, ldo, ldc, out, discard && lines ? 1 : 0);
 }
 
 // ------------------------------------------------------------ dispatch
