@@ -1105,37 +1105,6 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 // list -- a few by shuffle insertion, many by sorting the batch and a
 // bitonic merge.  The result is the row's 32 smallest keys, as a full scan
 // would give; with `discard` each line read is dropped from L2 afterwards.
-__device__ __forceinline__ void merge_key(uint64_t kk, uint64_t& mine, uint64_t& worst) {
-  const int lane = threadIdx.x & 31;
-  unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
-  if (!bm) return;
-  if (__popc(bm) > 6) {
-    kk = shfl64(warp_sort_asc(kk), 31 - lane);
-    uint64_t r = mine < kk ? mine : kk;
-#pragma unroll
-    for (int j = 16; j > 0; j >>= 1) {
-      const uint64_t o = shfl_xor64(r, j);
-      r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
-    }
-    mine = r;
-  } else {
-    do {
-      const int src = __ffs(bm) - 1;
-      bm &= bm - 1;
-      const uint64_t x64 = shfl64(kk, src);
-      if (x64 < worst) {
-        const int pos = __popc(__ballot_sync(0xffffffffu, mine < x64));
-        const uint64_t up = shfl64(mine, lane > 0 ? lane - 1 : 0);
-        mine = lane < pos ? mine : (lane == pos ? x64 : up);
-        worst = shfl64(mine, 31);
-      }
-    } while (bm);
-  }
-  worst = shfl64(mine, 31);
-}
-
-constexpr int kSelectBatch = 16;  // chunks whose loads are in flight together
-
 __global__ void k_select_top32(const float* __restrict__ D, const float* __restrict__ cmin, int64_t nq, int64_t s,
                                int64_t ldo, int64_t ldc, uint64_t* __restrict__ out, int32_t discard) {
   const int lane = threadIdx.x & 31;
@@ -1144,54 +1113,65 @@ __global__ void k_select_top32(const float* __restrict__ D, const float* __restr
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float* cm = cmin + q * ldc;
-    // the 32 smallest chunk minima, kept sorted across the warp (the loads
-    // of 128 chunks at a time in flight together)
+    // the 32 smallest chunk minima, kept sorted across the warp
     float best = kInf;
-    for (int g0 = 0; g0 < nch; g0 += 128) {
-      float v[4];
+    for (int g = 0; g < nch; g += 32) {
+      float v = g + lane < nch ? __ldg(cm + g + lane) : kInf;
+      v = __shfl_sync(0xffffffffu, warp_sort_asc_f32(v), 31 - lane);
+      float r = fminf(best, v);
 #pragma unroll
-      for (int b = 0; b < 4; ++b) v[b] = g0 + 32 * b + lane < nch ? __ldg(cm + g0 + 32 * b + lane) : kInf;
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const float w = __shfl_sync(0xffffffffu, warp_sort_asc_f32(v[b]), 31 - lane);
-        float r = fminf(best, w);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) {
-          const float x = __shfl_xor_sync(0xffffffffu, r, o);
-          r = (lane & o) == 0 ? fminf(x, r) : fmaxf(x, r);
-        }
-        best = r;
+      for (int o = 16; o > 0; o >>= 1) {
+        const float x = __shfl_xor_sync(0xffffffffu, r, o);
+        r = (lane & o) == 0 ? fminf(x, r) : fmaxf(x, r);
       }
+      best = r;
     }
     const float T = __shfl_sync(0xffffffffu, best, 31);
     uint64_t mine = kEmpty, worst = kEmpty;
     const float* row = D + q * ldo;
-    for (int g0 = 0; g0 < nch; g0 += 128) {
-      // the chunks of these 128 whose minimum is at or below T
-      unsigned mk[4];
+    for (int g = 0; g < nch; g += 32) {
+      const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
+      unsigned m = __ballot_sync(0xffffffffu, in);
+      while (m) {
+        // up to four of the chunks at a time: their loads in flight together
+        int ch[4];
+        float dv[4];
 #pragma unroll
-      for (int b = 0; b < 4; ++b)
-        mk[b] = __ballot_sync(0xffffffffu, g0 + 32 * b + lane < nch && __ldg(cm + g0 + 32 * b + lane) <= T);
-      while (mk[0] | mk[1] | mk[2] | mk[3]) {
-        int ch[kSelectBatch];
-        float dv[kSelectBatch];
-#pragma unroll
-        for (int b = 0; b < kSelectBatch; ++b) {
-          int c = -1;
-#pragma unroll
-          for (int w = 0; w < 4; ++w)
-            if (c < 0 && mk[w]) {
-              c = g0 + 32 * w + __ffs(mk[w]) - 1;
-              mk[w] &= mk[w] - 1;
-            }
-          ch[b] = c;
-          dv[b] = c >= 0 ? __ldcs(row + (int64_t)c * 32 + lane) : kInf;
+        for (int b = 0; b < 4; ++b) {
+          ch[b] = m ? g + __ffs(m) - 1 : -1;
+          if (m) m &= m - 1;
+          dv[b] = ch[b] >= 0 ? __ldcs(row + (int64_t)ch[b] * 32 + lane) : kInf;
         }
 #pragma unroll
-        for (int b = 0; b < kSelectBatch; ++b) {
-          if (ch[b] < 0) break;  // warp-uniform: the batch's remaining slots are empty
+        for (int b = 0; b < 4; ++b) {
+          if (ch[b] < 0) continue;  // warp-uniform
           const float x = dv[b];
-          merge_key((x <= T && !isinf(x)) ? pack(x, (uint32_t)(ch[b] * 32 + lane)) : kEmpty, mine, worst);
+          uint64_t kk = (x <= T && !isinf(x)) ? pack(x, (uint32_t)(ch[b] * 32 + lane)) : kEmpty;
+          unsigned bm = __ballot_sync(0xffffffffu, kk < worst);
+          if (!bm) continue;
+          if (__popc(bm) > 6) {
+            kk = shfl64(warp_sort_asc(kk), 31 - lane);
+            uint64_t r = mine < kk ? mine : kk;
+#pragma unroll
+            for (int j = 16; j > 0; j >>= 1) {
+              const uint64_t o = shfl_xor64(r, j);
+              r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+            }
+            mine = r;
+          } else {
+            do {
+              const int src = __ffs(bm) - 1;
+              bm &= bm - 1;
+              const uint64_t x64 = shfl64(kk, src);
+              if (x64 < worst) {
+                const int pos = __popc(__ballot_sync(0xffffffffu, mine < x64));
+                const uint64_t up = shfl64(mine, lane > 0 ? lane - 1 : 0);
+                mine = lane < pos ? mine : (lane == pos ? x64 : up);
+                worst = shfl64(mine, 31);
+              }
+            } while (bm);
+          }
+          worst = shfl64(mine, 31);
         }
       }
     }
