@@ -74,6 +74,11 @@ def lib():
             L.ho_verify.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.POINTER(C.c_int64),
                                     C.c_int64, C.POINTER(C.c_int64), C.c_int64, C.c_uint64, C.c_int32,
                                     C.c_int32, C.c_int32, C.c_int64, C.c_int32, C.POINTER(C.c_uint8)]
+            L.ho_build_layers_from.restype = C.c_int32
+            L.ho_build_layers_from.argtypes = [C.POINTER(C.c_float), C.c_int32, C.c_int32, C.c_int32, C.c_int32,
+                                               C.c_double, C.c_int32, C.c_int32, C.c_uint64, C.c_int32, C.c_int32,
+                                               C.POINTER(C.c_int64), C.c_int64, C.POINTER(C.c_int64),
+                                               C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int32)]
             L.ho_build_layers_halving.restype = C.c_int32
             L.ho_build_layers_halving.argtypes = [C.c_int64, C.c_int32, C.c_int32, C.c_uint64,
                                                   C.POINTER(C.c_int64), C.POINTER(C.c_int64), C.POINTER(C.c_int64)]
@@ -335,6 +340,72 @@ def insert(idx, X, new_ids, m=4):
             idx["adj"][i] = edge_rule(idx["fwd"][i], idx["fwd_d"][i], Mmax, idx["graph"])
         idx["sizes"] = np.array([len(a) for a in idx["ids"]], dtype=np.int64)
     return idx
+
+
+def build_layers_from(X, prev_ids, first_layer, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, seed=0,
+                      metric=L2):
+    """Layers first_layer, first_layer + 1, ... (Alg. 1 + Alg. 2) built on
+    top of a layer whose points are prev_ids (ascending global ids).
+    Returns (ids per new layer, down per new layer -- positions in
+    prev_ids for the first --, attempts per new layer); raises if no
+    epsilon-net is found."""
+    X = _f32(X)
+    prev = np.ascontiguousarray(prev_ids, dtype=np.int64)
+    s0 = len(prev)
+    sizes = np.zeros(64, dtype=np.int64)
+    ids = np.zeros(max(s0, 1), dtype=np.int64)
+    down = np.zeros(max(s0, 1), dtype=np.int64)
+    attempts = np.zeros(64, dtype=np.int32)
+    top = lib().ho_build_layers_from(_p(X, C.c_float), X.shape[1], metric, m, max_layers, c0, r, max_attempts, seed,
+                                     0, first_layer, _p(prev, C.c_int64), s0, _p(sizes, C.c_int64),
+                                     _p(ids, C.c_int64), _p(down, C.c_int64), _p(attempts, C.c_int32))
+    if top < 0:
+        raise RuntimeError("no epsilon-net found within max_attempts")
+    out_ids, out_down, out_att, off = [], [], [], 0
+    for layer in range(first_layer, top + 1):
+        c = int(sizes[layer])
+        out_ids.append(ids[off:off + c].copy())
+        out_down.append(down[off:off + c].copy())
+        out_att.append(int(attempts[layer]))
+        off += c
+    return out_ids, out_down, out_att
+
+
+def delete(idx, X, dead, m=4, max_layers=0, c0=1.0, r=100, max_attempts=64, share=0.5):
+    """Delete of App. C on top of tombstones: `dead` (a boolean mask over
+    global ids) holds every deleted point; deleted points stay in the
+    layers as walk-only nodes and never come back (search(deleted=)).  The
+    lowest upper layer i whose live points fall below `share` times the
+    size a fresh sample of the live points of layer i - 1 would draw,
+    ceil(live(L_{i-1}) / 2^m), is resampled from those live points (Alg. 2
+    with the build's seed and layer numbers) and the hierarchy is rebuilt
+    from it up to the root: membership, down pointers (positions in layer
+    i - 1, whose arrays keep their dead entries) and graphs.  Layer 0 keeps
+    every point.  Modifies idx; returns the first rebuilt layer or None."""
+    X = _f32(X)
+    dead = np.asarray(dead, dtype=bool)
+    seed, M, Mmax, graph, metric = idx["seed"], idx["M"], idx["Mmax"], idx["graph"], idx["metric"]
+    for i in range(1, idx["L"] + 1):
+        below = idx["ids"][i - 1]
+        livep = np.nonzero(~dead[below])[0]
+        need = -(-len(livep) // (1 << m))
+        if (~dead[idx["ids"][i]]).sum() >= share * need:
+            continue
+        new_ids, new_down, new_att = build_layers_from(X, below[livep], i, m, max_layers, c0, r, max_attempts, seed,
+                                                       metric)
+        idx["ids"] = idx["ids"][:i] + new_ids
+        idx["down"] = idx["down"][:i] + ([livep[new_down[0]]] + new_down[1:] if new_ids else [])
+        idx["attempts"] = np.concatenate([np.asarray(idx["attempts"][:i]), np.asarray(new_att, np.int32)])
+        idx["fwd"], idx["fwd_d"], idx["adj"] = idx["fwd"][:i], idx["fwd_d"][:i], idx["adj"][:i]
+        for j, lids in enumerate(new_ids):
+            f, fd = forward_lists(X, lids, seed, i + j, M, graph, metric)
+            idx["fwd"].append(f)
+            idx["fwd_d"].append(fd)
+            idx["adj"].append(edge_rule(f, fd, Mmax, graph))
+        idx["L"] = i - 1 + len(new_ids)
+        idx["sizes"] = np.array([len(a) for a in idx["ids"]], dtype=np.int64)
+        return i
+    return None
 
 
 def search(idx, X, Q, k=10, ef=64, keys=None, out_stride=None, seed=None, ef_upper=1, ef_l1=0,

@@ -289,20 +289,18 @@ int32_t ho_verify(const float* X, int32_t d, int32_t metric, const int64_t* prev
  * layer i-1 found by the Las-Vegas loop of Alg. 2, with |L_i| drawn as
  * ceil(|L_{i-1}| / 2^m) samples (Cor. 2).  Layers are built while i <=
  * max_layers (0: no limit) and |L_{i-1}| >= 2^m. */
-int32_t ho_build_layers(const float* X, int64_t n, int32_t d, int32_t metric, int32_t m,
-                        int32_t max_layers, double c0, int32_t r, int32_t max_attempts,
-                        uint64_t seed, int32_t exhaustive, int64_t* sizes, int64_t* ids,
-                        int64_t* down, int32_t* attempts) {
-  int64_t* prev = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
-  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)n);
-  for (int64_t i = 0; i < n; ++i) prev[i] = i;
-  int64_t s = n;
-  sizes[0] = n;
-  attempts[0] = 0;
+int32_t ho_build_layers_from(const float* X, int32_t d, int32_t metric, int32_t m, int32_t max_layers,
+                             double c0, int32_t r, int32_t max_attempts, uint64_t seed, int32_t exhaustive,
+                             int32_t first_layer, const int64_t* prev_ids, int64_t s0, int64_t* sizes,
+                             int64_t* ids, int64_t* down, int32_t* attempts) {
+  int64_t* prev = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s0 > 0 ? s0 : 1));
+  int64_t* pos = (int64_t*)malloc(sizeof(int64_t) * (size_t)(s0 > 0 ? s0 : 1));
+  for (int64_t i = 0; i < s0; ++i) prev[i] = prev_ids[i];
+  int64_t s = s0;
   int64_t off = 0;
-  int32_t L = 0;
+  int32_t L = first_layer - 1;
   const int64_t decay = 1LL << m;
-  for (int32_t layer = 1; layer < 64; ++layer) {
+  for (int32_t layer = first_layer; layer < 64; ++layer) {
     if (max_layers > 0 && layer > max_layers) break;
     if (s < decay) break;
     int64_t t = (s + decay - 1) / decay;
@@ -334,6 +332,20 @@ int32_t ho_build_layers(const float* X, int64_t n, int32_t d, int32_t metric, in
   }
   free(prev);
   free(pos);
+  return L;
+}
+
+int32_t ho_build_layers(const float* X, int64_t n, int32_t d, int32_t metric, int32_t m,
+                        int32_t max_layers, double c0, int32_t r, int32_t max_attempts,
+                        uint64_t seed, int32_t exhaustive, int64_t* sizes, int64_t* ids,
+                        int64_t* down, int32_t* attempts) {
+  int64_t* all = (int64_t*)malloc(sizeof(int64_t) * (size_t)(n > 0 ? n : 1));
+  for (int64_t i = 0; i < n; ++i) all[i] = i;
+  sizes[0] = n;
+  attempts[0] = 0;
+  const int32_t L = ho_build_layers_from(X, d, metric, m, max_layers, c0, r, max_attempts, seed, exhaustive, 1,
+                                         all, n, sizes, ids, down, attempts);
+  free(all);
   return L;
 }
 

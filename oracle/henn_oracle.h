@@ -89,6 +89,19 @@ int32_t ho_build_layers(const float* X, int64_t n, int32_t d, int32_t metric, in
                         uint64_t seed, int32_t exhaustive, int64_t* sizes, int64_t* ids,
                         int64_t* down, int32_t* attempts);
 
+/* The same layers built from layer `first_layer` on, the layer below being
+ * the s0 global ids prev_ids (ascending): layer first_layer is sampled from
+ * them, the next from it, and so on.  sizes / attempts are indexed by layer
+ * number (entries first_layer.. written); ids / down are concatenated from
+ * first_layer on, down holding positions in prev_ids for first_layer.
+ * Returns the highest layer built (first_layer - 1 if none), or -1 if some
+ * layer found no epsilon-net.  Used by the delete path of App. C to
+ * resample a layer from the live points of the layer below. */
+int32_t ho_build_layers_from(const float* X, int32_t d, int32_t metric, int32_t m, int32_t max_layers,
+                             double c0, int32_t r, int32_t max_attempts, uint64_t seed, int32_t exhaustive,
+                             int32_t first_layer, const int64_t* prev_ids, int64_t s0, int64_t* sizes,
+                             int64_t* ids, int64_t* down, int32_t* attempts);
+
 /* Alg. 3 BuildEpsNetDiscV2: m halving steps of the positions 0..s-1 of the
  * previous layer.  Each step matches the current list in consecutive pairs
  * (positions 2j, 2j+1 of the list: one arbitrary matching), keeps one

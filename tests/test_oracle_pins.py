@@ -783,3 +783,62 @@ def test_greedy_upper_layers_chain_alg4(hier3k):
     _, _, st = O.search(idx, X, many, k=1, ef=1)
     counts = np.bincount(st[:, 3], minlength=len(idx["ids"][L]))
     assert counts.min() > 0
+
+
+# --------------------------------- delete with resampling (App. C, Delete)
+
+def test_rebuild_from_a_layer_reproduces_the_build():
+    """Building from layer i on top of the unchanged layer i - 1 draws the
+    same random streams as the full build (Alg. 1 + Alg. 2): the same layers."""
+    X = synth.uniform_cube(5000, 8, seed=62)
+    idx = O.build_index(X, seed=4)
+    for i in range(1, idx["L"] + 1):
+        ids, down, att = O.build_layers_from(X, idx["ids"][i - 1], i, seed=4)
+        assert len(ids) == idx["L"] - i + 1
+        for j, (a, b) in enumerate(zip(ids, down)):
+            assert np.array_equal(a, idx["ids"][i + j]) and np.array_equal(b, idx["down"][i + j])
+            assert att[j] == idx["attempts"][i + j]
+
+
+def test_delete_resamples_a_shrunken_layer_and_rebuilds_above():
+    """App. C, Delete: a few deletions leave the layers as they are; once
+    the live part of layer 1 falls below half of a fresh sample of the live
+    points below, layer 1 is resampled from the live points of layer 0 and
+    everything above is rebuilt: nested layers of live points, down pointers
+    into the layer below, sizes within Lemma 1's bound."""
+    X = synth.uniform_cube(6000, 8, seed=63)
+    idx = O.build_index(X, seed=5)
+    before = [a.copy() for a in idx["ids"]]
+    dead = np.zeros(len(X), bool)
+    dead[before[1][:5]] = True
+    assert O.delete(idx, X, dead) is None
+    assert all(np.array_equal(a, b) for a, b in zip(idx["ids"], before))
+    dead[before[1][: (2 * len(before[1])) // 3]] = True
+    assert O.delete(idx, X, dead) == 1
+    assert np.array_equal(idx["ids"][0], np.arange(len(X)))
+    for i in range(1, idx["L"] + 1):
+        ids, below = idx["ids"][i], idx["ids"][i - 1]
+        assert not dead[ids].any()
+        assert np.array_equal(below[idx["down"][i]], ids) and np.all(np.diff(ids) > 0)
+        live_below = (~dead[below]).sum()
+        assert len(ids) <= -(-live_below // 16)
+        assert idx["adj"][i].shape == (len(ids), idx["Mmax"])
+    # the rebuilt layer 1 is what a fresh build on the live points draws for layer 1
+    fresh, _, _ = O.build_layers_from(X, np.nonzero(~dead)[0], 1, seed=5)
+    assert np.array_equal(fresh[0], idx["ids"][1])
+
+
+def test_search_after_resampling_is_exact_with_a_covering_beam():
+    """After a resampling delete, a beam covering the base layer returns the
+    exact k nearest live points (scipy), deleted ones never."""
+    X = synth.uniform_cube(600, 5, seed=64)
+    Q = synth.uniform_cube(30, 5, seed=65)
+    idx = O.build_index(X, seed=6)
+    dead = np.zeros(len(X), bool)
+    dead[idx["ids"][1][: (2 * len(idx["ids"][1])) // 3]] = True
+    dead[::7] = True
+    assert O.delete(idx, X, dead) == 1
+    got, _, _ = O.search(idx, X, Q, k=10, ef=600, deleted=dead)
+    D = cdist(Q.astype(np.float64), X.astype(np.float64), "sqeuclidean")
+    D[:, dead] = np.inf
+    assert np.array_equal(got, np.argsort(D, axis=1, kind="stable")[:, :10])
