@@ -106,6 +106,11 @@ typedef struct {
   int32_t tiles;         /* henn_tiles                                          */
   uint64_t seed;         /* index seed                                          */
   int32_t sampler;       /* henn_sampler; default SAMPLING                      */
+  double resample_share; /* App. C, Delete: an upper layer whose live points
+                            fall below this share of a fresh sample of the
+                            live layer below, ceil(live / 2^m), is resampled
+                            and the hierarchy rebuilt above it; default 0.5,
+                            <= 0: never (tombstones only)                    */
 } henn_build_params;
 
 /* Fills *p with the defaults above (struct_size included). */
@@ -156,14 +161,20 @@ henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t x_on_device
 henn_status henn_insert(henn_index* idx, const float* X, int64_t n_new, int32_t x_on_device, void* stream);
 
 /*
- * henn_delete -- Delete (App. C) as tombstones: the points with these
- * global ids (HOST array of n int64, each in [0, number of points)) no
- * longer appear in search results; they stay in their layers and graphs as
- * waypoints, and a result is the first k live entries of the final
- * candidate list.  The paper's resampling of a layer that shrinks below its
- * threshold is not done here: rebuild with henn_build when many points are
- * gone.  Servers made from idx before the first delete do not see it.
- * Synchronises `stream`.  Errors: HENN_ERR_INVALID_ARG for an id out of range.
+ * henn_delete -- Delete (App. C).  The points with these global ids (HOST
+ * array of n int64, each in [0, number of points)) no longer appear in
+ * search results: they stay in their layers and graphs as waypoints
+ * (tombstones), and a result is the first k live entries of the final
+ * candidate list.  Then, as App. C prescribes when a layer has shrunk too
+ * far: the lowest upper layer i whose live points number fewer than
+ * resample_share (of the build parameters) times ceil(live(L_{i-1}) / 2^m)
+ * is resampled from the live points of layer i - 1 (Alg. 2, or Alg. 3, with
+ * the build's seed and layer numbers) and the hierarchy is rebuilt from it
+ * to the root (membership, down pointers, graphs, traversal copies); layer
+ * 0 keeps every point.  Servers made from idx before the call do not see
+ * it and must be destroyed first.  Not safe concurrently with searches on
+ * idx.  Synchronises `stream`.  Errors: HENN_ERR_INVALID_ARG for an id out
+ * of range; a failed resampling as henn_build (HENN_ERR_EPSNET_NOT_FOUND).
  */
 henn_status henn_delete(henn_index* idx, const int64_t* ids, int64_t n, void* stream);
 

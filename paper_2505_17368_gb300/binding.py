@@ -92,6 +92,7 @@ class BuildParams(C.Structure):
         ("tiles", C.c_int32),
         ("seed", C.c_uint64),
         ("sampler", C.c_int32),
+        ("resample_share", C.c_double),
     ]
 
 
@@ -263,7 +264,7 @@ class Index:
 
     def __init__(self, X, metric=L2, storage=F32, graph=GRAPH_NSW, m=4, max_layers=0, eps_c0=1.0,
                  num_ranges=100, max_attempts=64, M=16, Mmax=32, tiles=TILES_AUTO, seed=0, stream=None,
-                 sampler=SAMPLER_SAMPLING):
+                 sampler=SAMPLER_SAMPLING, resample_share=0.5):
         L = load()
         p = BuildParams()
         L.henn_build_params_default(C.byref(p))
@@ -272,6 +273,7 @@ class Index:
         p.num_ranges, p.max_attempts, p.M, p.Mmax, p.tiles = num_ranges, max_attempts, M, Mmax, tiles
         p.seed = seed & 0xFFFFFFFFFFFFFFFF
         p.sampler = int(sampler)
+        p.resample_share = float(resample_share)
         if _is_torch(X):
             import torch
 
@@ -304,7 +306,9 @@ class Index:
         return first
 
     def delete(self, ids, stream=None):
-        """henn_delete: tombstone the points with these global ids."""
+        """henn_delete: tombstone the points with these global ids, and
+        resample and rebuild the upper layers when one has shrunk too far
+        (App. C)."""
         ids = np.ascontiguousarray(np.asarray(ids, dtype=np.int64).reshape(-1))
         _check(load().henn_delete(self._h, C.c_void_p(ids.ctypes.data), ids.size, _stream(stream)))
 

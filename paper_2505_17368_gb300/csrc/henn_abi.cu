@@ -212,6 +212,7 @@ struct henn_index {
   double tile_seconds = 0.0, tile_flops = 0.0;
   int32_t tile_engine = 0;
   int32_t graph_instantiations = 0, graph_updates = 0;
+  henn_build_params params;  // as the build validated them (delete's resampling reuses them)
   int device = 0;
 
   template <typename T>
@@ -317,6 +318,7 @@ extern "C" void henn_build_params_default(henn_build_params* p) {
   p->tiles = HENN_TILES_AUTO;
   p->seed = 0;
   p->sampler = HENN_SAMPLER_SAMPLING;
+  p->resample_share = 0.5;
 }
 
 extern "C" void henn_search_params_default(henn_search_params* sp) {
@@ -423,6 +425,55 @@ int32_t build_layer_membership(henn_index* ix, const henn_build_params& p, int32
     }
   }
   return -1;
+}
+
+// Membership of layers first_layer, first_layer + 1, ... (Alg. 1 with Alg. 2
+// or Alg. 3) on top of a layer of s0 points whose global ids are prev_ids
+// (device, ascending; nullptr: the points 0..s0-1), appended to ix->layers
+// with their down pointers (positions in prev_ids for the first); stops as
+// the build does (|L| < 2^m or max_layers).
+void build_membership(henn_index* ix, const henn_build_params& p, int32_t first_layer, const int32_t* prev_ids,
+                      int64_t s0, CapturedGraph& attempt_graph, BuildTrace& tr, cudaStream_t st) {
+  Scratch sc(st);
+  uint8_t* flags = sc.get<uint8_t>(s0);
+  int64_t* tile_buf = sc.get<int64_t>((size_t)scan_tiles(s0) + 1);
+  int64_t* d_total = sc.get<int64_t>(1);
+  int32_t* pos = sc.get<int32_t>(s0);
+  int32_t* ids = sc.get<int32_t>(s0);
+  const int64_t decay = 1LL << p.m;
+  const int32_t* prev = prev_ids;
+  int64_t s = s0;
+  for (int32_t layer = first_layer; layer < HENN_MAX_LAYERS; ++layer) {
+    if (p.max_layers > 0 && layer > p.max_layers) break;
+    if (s < decay) break;
+    int64_t count = 0;
+    int32_t amb = 0;
+    int32_t a = 0;
+    if (p.sampler == HENN_SAMPLER_HALVING) {
+      // Alg. 3 (BuildEpsNetDiscV2): m halving steps, no verification;
+      // `ids` doubles as the ping-pong buffer until the ids are written
+      count = launch_halving(ix->seed, layer, s, p.m, prev, ids, pos, ids, st);
+      CKL("halving");
+    } else {
+      a = build_layer_membership(ix, p, layer, s, prev, sc, flags, tile_buf, d_total, pos, ids, &count, &amb,
+                                 attempt_graph, st);
+    }
+    if (a < 0)
+      throw Failure(HENN_ERR_EPSNET_NOT_FOUND, "no eps-net for layer " + std::to_string(layer) + " within max_attempts");
+    LayerDev Ly;
+    Ly.size = count;
+    Ly.ids = ix->alloc<int32_t>(count);
+    Ly.down = ix->alloc<int32_t>(count);
+    CK(cudaMemcpyAsync(Ly.ids, ids, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
+    CK(cudaMemcpyAsync(Ly.down, pos, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
+    ix->layers.push_back(Ly);
+    ix->attempts.push_back(a);
+    ix->ambiguous.push_back(amb);
+    tr.mark("membership", layer);
+    prev = Ly.ids;
+    s = count;
+  }
+  CK(cudaStreamSynchronize(st));
 }
 
 void build_layer_graph(henn_index* ix, const henn_build_params& p, int32_t li, CapturedGraph& graph, cudaStream_t st,
@@ -569,6 +620,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     require(p.num_ranges >= 1 && p.num_ranges <= 4096, "num_ranges must be in [1, 4096]");
     require(p.max_attempts >= 1 && p.max_attempts <= 100000, "max_attempts");
     require(p.M >= 1 && p.M <= 32, "M must be in [1, 32]");
+    require(std::isfinite(p.resample_share), "resample_share must be finite");
     require(p.Mmax == 32, "Mmax must be 32");
     // The build runs on its own non-blocking stream (the legacy default
     // stream cannot be captured into graphs), after the caller's stream
@@ -589,6 +641,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     BuildTrace tr(st);
 
     ix = new henn_index();
+    ix->params = p;
     CK(cudaGetDevice(&ix->device));
     ix->n = n;
     ix->d = d;
@@ -624,46 +677,7 @@ extern "C" henn_status henn_build(const float* X, int64_t n, int32_t d, int32_t 
     ix->attempts.push_back(0);
     ix->ambiguous.push_back(0);
     CapturedGraph attempt_graph, layer_graph;
-    {
-      Scratch sc(st);
-      uint8_t* flags = sc.get<uint8_t>(n);
-      int64_t* tile_buf = sc.get<int64_t>((size_t)scan_tiles(n) + 1);
-      int64_t* d_total = sc.get<int64_t>(1);
-      int32_t* pos = sc.get<int32_t>(n);
-      int32_t* ids = sc.get<int32_t>(n);
-      const int64_t decay = 1LL << p.m;
-      for (int32_t layer = 1; layer < HENN_MAX_LAYERS; ++layer) {
-        if (p.max_layers > 0 && layer > p.max_layers) break;
-        const int64_t s = ix->layers[layer - 1].size;
-        if (s < decay) break;
-        int64_t count = 0;
-        int32_t amb = 0;
-        int32_t a = 0;
-        if (p.sampler == HENN_SAMPLER_HALVING) {
-          // Alg. 3 (BuildEpsNetDiscV2): m halving steps, no verification;
-          // `ids` doubles as the ping-pong buffer until the ids are written
-          count = launch_halving(ix->seed, layer, s, p.m, ix->layers[layer - 1].ids, ids, pos, ids, st);
-          CKL("halving");
-        } else {
-          a = build_layer_membership(ix, p, layer, s, ix->layers[layer - 1].ids, sc, flags, tile_buf, d_total, pos,
-                                     ids, &count, &amb, attempt_graph, st);
-        }
-        if (a < 0)
-          throw Failure(HENN_ERR_EPSNET_NOT_FOUND,
-                        "no eps-net for layer " + std::to_string(layer) + " within max_attempts");
-        LayerDev Ly;
-        Ly.size = count;
-        Ly.ids = ix->alloc<int32_t>(count);
-        Ly.down = ix->alloc<int32_t>(count);
-        CK(cudaMemcpyAsync(Ly.ids, ids, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
-        CK(cudaMemcpyAsync(Ly.down, pos, sizeof(int32_t) * count, cudaMemcpyDeviceToDevice, st));
-        ix->layers.push_back(Ly);
-        ix->attempts.push_back(a);
-        ix->ambiguous.push_back(amb);
-        tr.mark("membership", layer);
-      }
-      CK(cudaStreamSynchronize(st));
-    }
+    build_membership(ix, p, 1, nullptr, n, attempt_graph, tr, st);
     ix->L = (int32_t)ix->layers.size() - 1;
 
     // ---- navigable graph + traversal copy per layer
@@ -710,6 +724,114 @@ extern "C" void henn_free(henn_index* idx) { delete idx; }
 // ---------------------------------------------------------------- delete
 
 namespace {
+
+// The search-side layer table of ix (device), rewritten from ix->layers;
+// reallocated when the number of layers changed.
+void upload_layer_table(henn_index* ix, cudaStream_t st) {
+  std::vector<SearchLayer> h(ix->L + 1);
+  for (int32_t li = 0; li <= ix->L; ++li) {
+    h[li].adj = ix->layers[li].adj;
+    h[li].vec = ix->layers[li].vec;
+    h[li].scale = ix->layers[li].vscale;
+    h[li].down = ix->layers[li].down;
+    h[li].size = ix->layers[li].size;
+  }
+  ix->release(ix->d_layers);
+  ix->d_layers = ix->alloc<SearchLayer>(h.size());
+  CK(cudaMemcpyAsync(ix->d_layers, h.data(), sizeof(SearchLayer) * h.size(), cudaMemcpyHostToDevice, st));
+  CK(cudaStreamSynchronize(st));
+}
+
+// Layer i resampled from the live points of layer i - 1 (global ids
+// liveids, at positions livepos of layer i - 1) and every layer above it
+// rebuilt: membership (Alg. 1 + Alg. 2 or Alg. 3, the build's seed and
+// layer numbers), down pointers into layer i - 1's arrays (which keep
+// their dead entries), graphs and traversal copies.
+void rebuild_from(henn_index* ix, int32_t i, const std::vector<int32_t>& liveids, const std::vector<int32_t>& livepos) {
+  const henn_build_params& p = ix->params;
+  struct OwnStream {
+    cudaStream_t s = nullptr;
+    ~OwnStream() {
+      if (s) {
+        cudaStreamSynchronize(s);
+        cudaStreamDestroy(s);
+      }
+    }
+  } own;
+  CK(cudaStreamCreateWithFlags(&own.s, cudaStreamNonBlocking));
+  cudaStream_t st = own.s;
+  BuildTrace tr(st);
+  ix->drop_entry_ops();
+  for (int32_t li = ix->L; li >= i; --li) {
+    LayerDev& Ly = ix->layers[li];
+    for (void* q : {(void*)Ly.ids, (void*)Ly.down, (void*)Ly.adj, (void*)Ly.fwd, (void*)Ly.fwd_d, Ly.vec,
+                    (void*)Ly.vscale})
+      ix->release(q);
+  }
+  ix->layers.resize(i);
+  ix->attempts.resize(i);
+  ix->ambiguous.resize(i);
+  {
+    Scratch sc(st);
+    int32_t* prev = sc.get<int32_t>(liveids.size());
+    CK(cudaMemcpyAsync(prev, liveids.data(), sizeof(int32_t) * liveids.size(), cudaMemcpyHostToDevice, st));
+    CapturedGraph attempt_graph;
+    build_membership(ix, p, i, prev, (int64_t)liveids.size(), attempt_graph, tr, st);
+  }
+  if ((int32_t)ix->layers.size() > i) {
+    // the first new layer's down pointers: positions in the live list -> in layer i - 1
+    LayerDev& F = ix->layers[i];
+    std::vector<int32_t> dn((size_t)F.size);
+    CK(cudaMemcpyAsync(dn.data(), F.down, sizeof(int32_t) * dn.size(), cudaMemcpyDeviceToHost, st));
+    CK(cudaStreamSynchronize(st));
+    for (int32_t& v : dn) v = livepos[(size_t)v];
+    CK(cudaMemcpyAsync(F.down, dn.data(), sizeof(int32_t) * dn.size(), cudaMemcpyHostToDevice, st));
+    CK(cudaStreamSynchronize(st));
+  }
+  ix->L = (int32_t)ix->layers.size() - 1;
+  CapturedGraph layer_graph;
+  for (int32_t li = i; li <= ix->L; ++li) {
+    LayerDev& Ly = ix->layers[li];
+    Ly.cap = Ly.size;
+    Ly.adj = ix->alloc<int32_t>((size_t)Ly.size * kMmax);
+    Ly.fwd = ix->alloc<int32_t>((size_t)Ly.size * ix->M);
+    Ly.fwd_d = ix->alloc<float>((size_t)Ly.size * ix->M);
+    build_layer_graph(ix, p, li, layer_graph, st, tr);
+  }
+  upload_layer_table(ix, st);
+}
+
+// Delete of App. C after the tombstones are set: the lowest upper layer i
+// whose live points number fewer than resample_share * ceil(live(L_{i-1}) /
+// 2^m) is resampled from the live points of layer i - 1 and the hierarchy
+// rebuilt above it.  Reads the tombstones and the layers' ids to the host.
+void resample_after_delete(henn_index* ix) {
+  const henn_build_params& p = ix->params;
+  if (!(p.resample_share > 0.0) || ix->L < 1 || !ix->dead) return;
+  std::vector<uint8_t> dead((size_t)ix->n);
+  CK(cudaMemcpy(dead.data(), ix->dead, (size_t)ix->n, cudaMemcpyDeviceToHost));
+  std::vector<int32_t> below((size_t)ix->n), cur;
+  for (int64_t j = 0; j < ix->n; ++j) below[(size_t)j] = (int32_t)j;
+  for (int32_t i = 1; i <= ix->L; ++i) {
+    cur.resize((size_t)ix->layers[i].size);
+    CK(cudaMemcpy(cur.data(), ix->layers[i].ids, sizeof(int32_t) * cur.size(), cudaMemcpyDeviceToHost));
+    std::vector<int32_t> livepos, liveids;
+    for (size_t j = 0; j < below.size(); ++j)
+      if (!dead[(size_t)below[j]]) {
+        livepos.push_back((int32_t)j);
+        liveids.push_back(below[j]);
+      }
+    int64_t live_i = 0;
+    for (int32_t v : cur) live_i += dead[(size_t)v] ? 0 : 1;
+    const int64_t need = ((int64_t)liveids.size() + (1LL << p.m) - 1) >> p.m;
+    if ((double)live_i < p.resample_share * (double)need) {
+      rebuild_from(ix, i, liveids, livepos);
+      return;
+    }
+    below.swap(cur);
+  }
+}
+
 __global__ void k_mark_dead(const int64_t* __restrict__ ids, int64_t n, uint8_t* __restrict__ dead) {
   for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
     dead[ids[i]] = 1;
@@ -737,6 +859,7 @@ extern "C" henn_status henn_delete(henn_index* ix, const int64_t* ids, int64_t n
     CKL("delete");
     CK(cudaStreamSynchronize(st));
     ix->n_dead += n;  // an upper bound: a point deleted twice counts twice
+    resample_after_delete(ix);
     return HENN_OK;
   } catch (const Failure& f) {
     g_error = f.msg;

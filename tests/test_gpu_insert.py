@@ -71,3 +71,43 @@ def test_delete_parity(storage):
     print(f"delete {storage}: gpu {rec(ids):.4f} oracle {rec(oi):.4f}")
     assert abs(rec(ids) - rec(oi)) <= P.RECALL_TOL + 1e-12, (rec(ids), rec(oi))
     assert np.all(np.diff(dd.cpu().numpy(), axis=1) >= 0)
+
+
+@pytest.mark.parametrize("storage", ["f32", "bf16"])
+def test_delete_resampling_parity(storage):
+    """Delete of App. C with resampling: the GPU and the oracle apply the
+    same deletions (two calls, the first too small to trigger anything);
+    when layer 1's live part falls below half of a fresh sample of the live
+    base, both resample it from the live points and rebuild above it.  The
+    layers are bit-exact, the graphs match up to near ties, deleted points
+    never come back, and recall on the live points tracks the oracle's."""
+    X = synth.uniform_cube(8000, 16, seed=71)
+    Q = synth.uniform_cube(1500, 16, seed=72)
+    st = H.F32 if storage == "f32" else H.BF16
+    oidx = O.build_index(X, seed=12)
+    gidx = _gpu_index(X, seed=12, storage=st)
+    l1 = oidx["ids"][1].copy()
+    dead = np.zeros(len(X), bool)
+    first = np.concatenate([l1[:4], np.arange(0, len(X), 97)])
+    dead[first] = True
+    gidx.delete(first)
+    assert O.delete(oidx, X, dead) is None
+    _layers_equal(gidx, oidx)
+    second = np.concatenate([l1[: (2 * len(l1)) // 3], np.arange(5, len(X), 11)])
+    dead[second] = True
+    gidx.delete(second)
+    assert O.delete(oidx, X, dead) == 1
+    _layers_equal(gidx, oidx)
+    _graph_parity(gidx, oidx, X)
+    for i in range(1, gidx.info()["L"] + 1):
+        assert not dead[gidx.layer(i)["ids"]].any()
+    ids, dd, _ = gidx.search(torch.from_numpy(Q).to(DEV), k=10, ef=64)
+    ids = ids.cpu().numpy()
+    assert np.all(ids >= 0) and not dead[ids].any()
+    oi, _, _ = O.search(oidx, X, Q, k=10, ef=64, deleted=dead)
+    live = np.nonzero(~dead)[0]
+    li, _ = O.bruteforce(X[live], Q, 10)
+    gt = live[li]
+    rec = lambda found: np.mean([len(set(found[q]) & set(gt[q])) / 10 for q in range(len(Q))])  # noqa: E731
+    print(f"delete+resample {storage}: gpu {rec(ids):.4f} oracle {rec(oi):.4f}")
+    assert abs(rec(ids) - rec(oi)) <= P.RECALL_TOL + 1e-12, (rec(ids), rec(oi))
