@@ -194,6 +194,17 @@ struct Chunk<__nv_fp8_e4m3> {
   }
 };
 
+// One 16-byte chunk of a row.  Rows are read once per query: they skip L1
+// (no allocation there), which keeps the adjacency lines that the beam
+// prefetches, and the lines of rows still in flight, resident.
+__device__ __forceinline__ uint4 load_row_chunk(const uint4* p) {
+  uint4 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v4.u32 {%0, %1, %2, %3}, [%4];"
+               : "=r"(v.x), "=r"(v.y), "=r"(v.z), "=r"(v.w)
+               : "l"(p));
+  return v;
+}
+
 // Distances from the query (in shared memory) to up to 32 rows whose ids
 // are held one per lane in lanes 0..count-1.  G lanes cooperate on a row
 // (16-byte chunks lane, lane+G, ...), 32/G rows per pass.  The loads of PB
@@ -224,7 +235,7 @@ __device__ __forceinline__ float rows_dist(const VT* __restrict__ vec, const flo
 #pragma unroll
         for (int t = 0; t < CPL; ++t) {
           const int c = g + t * G;
-          if (c < nchunk) raw[pb][t] = __ldg(row + c);
+          if (c < nchunk) raw[pb][t] = load_row_chunk(row + c);
         }
       }
     }
@@ -430,6 +441,41 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
     const unsigned cm = __ballot_sync(0xffffffffu, take);
     const int ccnt = __popc(cm);
     if (ccnt == 0) continue;
+    if (nw <= 64) {
+      // W in two chunks: one pass over the candidates (compacted, unsorted)
+      // counts, for each entry of W, the candidates below it (its shift),
+      // and for each candidate the candidates and the entries of W below it
+      // (its position); then every moved entry and every candidate is
+      // written once
+      __syncwarp();
+      if (take) stage[__popc(cm & below)] = kk;
+      __syncwarp();
+      const bool v0 = lane < nw, v1 = lane + 32 < nw;
+      const uint64_t w0 = v0 ? W[lane] : kEmpty, w1 = v1 ? W[lane + 32] : kEmpty;
+      const uint64_t m0 = w0 & kKeyMask, m1 = w1 & kKeyMask;
+      const uint64_t cand = lane < ccnt ? stage[lane] : kEmpty;
+      int cl0 = 0, cl1 = 0, rk = 0, lb = 0;
+      for (int j = 0; j < ccnt; ++j) {
+        const uint64_t cj = stage[j];
+        const bool below0 = cj < m0, below1 = cj < m1;  // keys are distinct
+        cl0 += below0;
+        cl1 += below1;
+        rk += cj < cand;
+        const int nb = __popc(__ballot_sync(0xffffffffu, v0 && !below0)) +
+                       __popc(__ballot_sync(0xffffffffu, v1 && !below1));
+        if (lane == j) lb = nb;
+      }
+      const int cpos = lane < ccnt ? lb + rk : 0x7fffffff;
+      const int p0 = __reduce_min_sync(0xffffffffu, cpos);
+      __syncwarp();
+      if (v0 && cl0 > 0 && lane + cl0 < ef) W[lane + cl0] = w0;
+      if (v1 && cl1 > 0 && lane + 32 + cl1 < ef) W[lane + 32 + cl1] = w1;
+      if (lane < ccnt && cpos < ef) W[cpos] = cand;
+      __syncwarp();
+      nw = min(ef, nw + ccnt);
+      first = min(first, p0);
+      continue;
+    }
     // candidates, compacted, then sorted into stage[0..ccnt); lane j < ccnt
     // holds the j-th smallest and its position in the new W
     __syncwarp();
@@ -1105,8 +1151,19 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 // list -- a few by shuffle insertion, many by sorting the batch and a
 // bitonic merge.  The result is the row's 32 smallest keys, as a full scan
 // would give; with `discard` each line read is dropped from L2 afterwards.
-__global__ void k_select_top32(const float* __restrict__ D, const float* __restrict__ cmin, int64_t nq, int64_t s,
-                               int64_t ldo, int64_t ldc, uint64_t* __restrict__ out, int32_t discard) {
+#ifndef HENN_SELECT_ONE_TRIP
+#define HENN_SELECT_ONE_TRIP 1
+#endif
+constexpr int kSelChunks = 128;  // candidate chunks listed per row
+constexpr int kSelKeys = 256;    // entries <= T staged per row
+
+__global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ D, const float* __restrict__ cmin,
+                                                      int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
+                                                      uint64_t* __restrict__ out, int32_t discard) {
+#if HENN_SELECT_ONE_TRIP
+  __shared__ int sel_chunks[8][kSelChunks];
+  __shared__ uint64_t sel_keys[8][kSelKeys];
+#endif
   const int lane = threadIdx.x & 31;
   const float kInf = __int_as_float(0x7f800000);
   const int nch = (int)(ldo / 32);
@@ -1129,7 +1186,86 @@ __global__ void k_select_top32(const float* __restrict__ D, const float* __restr
     const float T = __shfl_sync(0xffffffffu, best, 31);
     uint64_t mine = kEmpty, worst = kEmpty;
     const float* row = D + q * ldo;
+#if HENN_SELECT_ONE_TRIP
+    // the chunks that can hold an entry <= T (usually exactly 32): their ids
+    // listed, then each lane loads one whole chunk, so that every chunk of
+    // the row is in flight at once; the entries <= T are staged as keys and
+    // merged 32 at a time.  Longer lists take the loop below.
+    // whole chunks as 16-byte loads: rows 16-byte aligned
+    bool fast = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ldo % 4 == 0);
+    if (fast) {
+      int* chl = sel_chunks[threadIdx.x >> 5];
+      uint64_t* stg = sel_keys[threadIdx.x >> 5];
+      int nc = 0;
+      for (int g = 0; g < nch; g += 32) {
+        const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
+        const unsigned bm = __ballot_sync(0xffffffffu, in);
+        const int pos = nc + __popc(bm & ((1u << lane) - 1u));
+        if (in && pos < kSelChunks) chl[pos] = g + lane;
+        nc += __popc(bm);
+      }
+      fast = nc <= kSelChunks;
+      __syncwarp();
+      int n = 0;
+      for (int r0 = 0; fast && r0 < nc; r0 += 32) {
+        const int ch = r0 + lane < nc ? chl[r0 + lane] : -1;
+        float v[32];
+        if (ch >= 0) {
+          const float4* src = reinterpret_cast<const float4*>(row + (int64_t)ch * 32);
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const float4 f = __ldcs(src + i);
+            v[4 * i] = f.x;
+            v[4 * i + 1] = f.y;
+            v[4 * i + 2] = f.z;
+            v[4 * i + 3] = f.w;
+          }
+        }
+        unsigned keep = 0;
+#pragma unroll
+        for (int e = 0; e < 32; ++e) keep |= (ch >= 0 && v[e] <= T && !isinf(v[e])) ? (1u << e) : 0u;
+        const int c = __popc(keep);
+        int incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+          const int t = __shfl_up_sync(0xffffffffu, incl, o);
+          if (lane >= o) incl += t;
+        }
+        const int tot = __shfl_sync(0xffffffffu, incl, 31);
+        if (n + tot > kSelKeys) {
+          fast = false;
+          break;
+        }
+        int at = n + incl - c;
+#pragma unroll
+        for (int e = 0; e < 32; ++e)
+          if (keep & (1u << e)) stg[at++] = pack(v[e], (uint32_t)(ch * 32 + e));
+        n += tot;
+      }
+      if (fast) {
+        __syncwarp();
+        for (int b = 0; b < n; b += 32) {
+          uint64_t kk = b + lane < n ? stg[b + lane] : kEmpty;
+          if (!__any_sync(0xffffffffu, kk < worst)) continue;
+          // the running list and the reversed sorted batch: their
+          // element-wise minimum holds the 32 smallest as a bitonic sequence
+          kk = shfl64(warp_sort_asc(kk), 31 - lane);
+          uint64_t r = mine < kk ? mine : kk;
+#pragma unroll
+          for (int j = 16; j > 0; j >>= 1) {
+            const uint64_t o = shfl_xor64(r, j);
+            r = (lane & j) == 0 ? (o < r ? o : r) : (o > r ? o : r);
+          }
+          mine = r;
+          worst = shfl64(mine, 31);
+        }
+      }
+      __syncwarp();
+    }
+    for (int g = 0; !fast && g < nch; g += 32) {
+#else
     for (int g = 0; g < nch; g += 32) {
+#endif
       const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
       unsigned m = __ballot_sync(0xffffffffu, in);
       while (m) {
