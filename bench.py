@@ -3,6 +3,7 @@ Gaussian-mixture workload rescaled to [0, 255], 10,000 queries, k = 10),
 batched BF16 traversal + exact FP32 rerank vs plain FP32; build seconds.
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference] [--sweep]
+                    [--shape warps,team,hash_bits,tile_n]
 
 One step = one henn_search call over the whole 10,000-query batch with the
 index resident in HBM: one persistent search launch, preceded, when the
@@ -17,7 +18,9 @@ FP64 brute force on a sample), with ties at the 10th distance counted; if
 it falls under 0.95, ef steps up the EF_SWEEP list until it does not.  The
 same beam is also scored on a held-out query batch.  Beside it the line
 reports the best beam that only walks the upper layers (no exact layer) and
-the paper's plain greedy descent (Alg. 4 on every upper layer).
+the paper's plain greedy descent (Alg. 4 on every upper layer).  The launch
+shape comes from the autotuner, or from --shape (for runs under a profiler,
+where the autotuner's timings mean nothing).
 
 Under torchrun every rank holds its own index replica and its own query
 batch (weak scaling, no collective on the data path); rank 0 prints one
@@ -457,8 +460,14 @@ def run_ours(args):
     # ---- launch shape (warps per block, visited-table size) by the autotuner
     from paper_2505_17368_gb300 import autotune
 
-    shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
-                          exact_method=xm, rerank_mult=rm, use_cache=False)
+    if args.shape:
+        # a fixed launch shape (profiling: the autotuner's timings are not
+        # meaningful under a profiler)
+        w, t, hb, tn = (int(x) for x in args.shape.split(","))
+        shape = {"warps_per_block": w, "team_size": t, "hash_bits": hb, "tile_n": tn}
+    else:
+        shape = autotune.tune(idx_bf16, Qd, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu,
+                              exact_method=xm, rerank_mult=rm, use_cache=False)
     # ---- algorithmic bytes per launch from the kernel's own counters
     _, _, st = idx_bf16.search(Qd, stats=True, **_kw(beam, shape))
     st = st.cpu().numpy().astype(np.int64)
@@ -530,6 +539,7 @@ def run_ours(args):
             "descend_all": da, "ef_l1": l1, "exact_upper": xu, "exact_method": xm, "rerank_mult": rm,
             "beam_source": "sweep" if args.sweep else ("--beam" if args.beam else "default"),
             "launch_shape": shape,
+            "launch_shape_source": "--shape" if args.shape else "autotuner",
             "form": f"bf16 traversal + fp32 rerank of top {rm}k", "recall_at_10": rec,
             "recall_at_10_held_out": rec_out, "recall_scoring": (
                 f"FP64 ground truth (FP64 order of each query's {GT_POOL} FP32-nearest candidates from "
@@ -643,6 +653,8 @@ def main():
     ap.add_argument("--beam", default=None,
                     help="ef,ef_upper,descend_all,ef_l1,exact_upper,exact_method[,rerank_mult] instead of "
                          "DEFAULT_BEAM (exact_upper may be L<i>, the size of layer i)")
+    ap.add_argument("--shape", default=None,
+                    help="warps_per_block,team_size,hash_bits,tile_n: a fixed launch shape instead of the autotuner's")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
