@@ -209,3 +209,29 @@ def test_tile_widths_give_identical_results(d):
                for n in (256, 128)]
         for a, b in zip(*res):
             assert np.array_equal(a, b), (d, xu)
+
+
+def test_tied_distances_equal_scan():
+    """Binary rows of 8 values (squared distances are the integers 0..8, and
+    every vector recurs about 500 times): on the 7,578-point layer 1 most
+    queries have more than 256 entries at or below the 32nd smallest chunk
+    minimum, or more than 128 chunks under it, so the top-32 selection takes
+    its long-list path for them and the one-round-trip path for the rest;
+    the exact sets, ties ordered by index, still equal the scan's.  With one
+    seed (ef_upper 1) the certificate holds for most queries (30 or so copies
+    at distance 0, the 32nd candidate at 1), so the selected candidates are
+    the ones the walk uses."""
+    rng = np.random.default_rng(21)
+    X = rng.integers(0, 2, size=(125000, 8)).astype(np.float32)
+    Q = rng.integers(0, 2, size=(1000, 8)).astype(np.float32)
+    for storage in (H.F32, H.BF16):
+        gidx = _gpu_index(X, seed=4, storage=storage)
+        sizes = gidx.info()["sizes"]
+        assert len(sizes) >= 3 and sizes[1] > 4096, sizes
+        for xu, efu, da in [(sizes[1], 1, 0), (sizes[1], 8, 1), (sizes[2], 16, 1)]:
+            out = _run(gidx, Q, methods=(H.EXACT_TILES, H.EXACT_SCAN), k=10, ef=48, ef_upper=efu, descend_all=da,
+                       exact_upper=xu)
+            _same(out)
+            if efu == 1:
+                # most queries kept the certified candidates (fewer evaluations than a scan)
+                assert out[H.EXACT_TILES][2][:, 0].sum() < out[H.EXACT_SCAN][2][:, 0].sum()
