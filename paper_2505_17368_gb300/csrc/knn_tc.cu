@@ -138,6 +138,30 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
 __device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
+// (a, b) <- (c - 2a, d - 2b) as one paired FMA, each element rounded as
+// fmaf(-2, a, c) would round it
+__device__ __forceinline__ void fma2_m2(float& a, float& b, float c, float d) {
+  asm("{\n\t.reg .b64 va, m2, cc;\n\t"
+      "mov.b64 va, {%0, %1};\n\t"
+      "mov.b64 m2, {%4, %4};\n\t"
+      "mov.b64 cc, {%2, %3};\n\t"
+      "fma.rn.f32x2 va, va, m2, cc;\n\t"
+      "mov.b64 {%0, %1}, va;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "f"(c), "f"(d), "f"(-2.f));
+}
+
+// (a, b) <- (a + x, b + x) as one paired add
+__device__ __forceinline__ void add2_s(float& a, float& b, float x) {
+  asm("{\n\t.reg .b64 va, xx;\n\t"
+      "mov.b64 va, {%0, %1};\n\t"
+      "mov.b64 xx, {%2, %2};\n\t"
+      "add.rn.f32x2 va, va, xx;\n\t"
+      "mov.b64 {%0, %1}, va;\n\t}"
+      : "+f"(a), "+f"(b)
+      : "f"(x));
+}
+
 // max(x, 0) that keeps a NaN (max.NaN)
 __device__ __forceinline__ float max_nan0(float x) {
   float r;
@@ -484,10 +508,12 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
             for (int j4 = 0; j4 < 8; ++j4) {
               const float4 nn = n4[j4];
-              const float4 o4 = make_float4(max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 0], nn.x)),
-                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 1], nn.y)),
-                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 2], nn.z)),
-                                            max_nan0(nrow + fmaf(-2.f, v[4 * j4 + 3], nn.w)));
+              float t0 = v[4 * j4 + 0], t1 = v[4 * j4 + 1], t2 = v[4 * j4 + 2], t3 = v[4 * j4 + 3];
+              tc::fma2_m2(t0, t1, nn.x, nn.y);
+              tc::fma2_m2(t2, t3, nn.z, nn.w);
+              tc::add2_s(t0, t1, nrow);
+              tc::add2_s(t2, t3, nrow);
+              const float4 o4 = make_float4(max_nan0(t0), max_nan0(t1), max_nan0(t2), max_nan0(t3));
               brow[j4 ^ (lane & 7)] = o4;
               cmin = fminf(cmin, fminf(fminf(o4.x, o4.y), fminf(o4.z, o4.w)));
             }
@@ -520,10 +546,8 @@ __global__ void __launch_bounds__(192, 1)
 #pragma unroll
         for (int j4 = 0; j4 < 8; ++j4) {
           const float4 nn = n4[j4];
-          v[4 * j4 + 0] = fmaf(-2.f, v[4 * j4 + 0], nn.x);
-          v[4 * j4 + 1] = fmaf(-2.f, v[4 * j4 + 1], nn.y);
-          v[4 * j4 + 2] = fmaf(-2.f, v[4 * j4 + 2], nn.z);
-          v[4 * j4 + 3] = fmaf(-2.f, v[4 * j4 + 3], nn.w);
+          tc::fma2_m2(v[4 * j4 + 0], v[4 * j4 + 1], nn.x, nn.y);
+          tc::fma2_m2(v[4 * j4 + 2], v[4 * j4 + 3], nn.z, nn.w);
           vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
         }
         const bool maybe = vmin <= thr_adj;
