@@ -226,6 +226,37 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+// The load split in two, for two chunks behind one wait: the issue, whose
+// registers are not read before tmem_ld_wait (which waits for every earlier
+// load of the thread) and, for the other chunk's registers, tmem_regs_after.
+__device__ __forceinline__ void tmem_ld32_issue(uint32_t taddr, uint32_t (&r)[32]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr)
+      : "memory");
+}
+
+#define HENN_R32_INOUT(r)                                                                                     \
+  "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]), "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), \
+      "+r"(r[9]), "+r"(r[10]), "+r"(r[11]), "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]),  \
+      "+r"(r[17]), "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]), "+r"(r[24]), \
+      "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]), "+r"(r[30]), "+r"(r[31])
+
+__device__ __forceinline__ void tmem_ld_wait(uint32_t (&r)[32]) {
+  asm volatile("tcgen05.wait::ld.sync.aligned;" : HENN_R32_INOUT(r) : : "memory");
+}
+
+// no instruction: r is read only after this point (placed after a wait)
+__device__ __forceinline__ void tmem_regs_after(uint32_t (&r)[32]) {
+  asm volatile("" : HENN_R32_INOUT(r) : : "memory");
+}
+#undef HENN_R32_INOUT
+
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
@@ -486,13 +517,92 @@ __global__ void __launch_bounds__(192, 1)
       if (mode == 3 && out_cmin)
         for (int q = 0; q < BN / 32; ++q) sm.s[ew][lane][q] = kInf;
       __syncwarp();
+      const uint32_t tacc = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN);
+      // n_col - 2<a,b> for the 32 columns of chunk q, in place, and their
+      // minimum
+      auto prep = [&](const int q, float (&v)[32]) {
+        const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
+        float vmin = kInf;
+#pragma unroll
+        for (int j4 = 0; j4 < 8; ++j4) {
+          const float4 nn = n4[j4];
+          tc::fma2_m2(v[4 * j4 + 0], v[4 * j4 + 1], nn.x, nn.y);
+          tc::fma2_m2(v[4 * j4 + 2], v[4 * j4 + 3], nn.z, nn.w);
+          vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
+        }
+        return vmin;
+      };
+      // the row lists: the columns of chunk c0 under the row's threshold
+      // offered to its heap (rows in parallel, one per lane)
+      auto lists = [&](const int64_t c0, float (&v)[32], const float vmin) {
+        const bool maybe = vmin <= thr_adj;
+        if (!__any_sync(0xffffffffu, maybe)) return;
+        unsigned keep = 0;
+        if (maybe) {
+          // columns c0 + j valid for this row, as a bit mask
+          const int32_t rem = lim - (int32_t)c0;
+          unsigned vmask = rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
+          const int32_t so = self - (int32_t)c0;
+          if (so >= 0 && so < 32) vmask &= ~(1u << so);
+#pragma unroll
+          for (int j = 0; j < 32; ++j) keep |= (v[j] <= thr_adj) ? (1u << j) : 0u;
+          keep &= vmask;
+        }
+        if (keep) {
+          // this lane's row: stage the passing values, then offer them to
+          // the row's heap one by one
+          float* srow = sm.s[ew][lane];
+#pragma unroll
+          for (int j = 0; j < 32; ++j) srow[j] = v[j];
+          do {
+            const int j = __ffs(keep) - 1;
+            keep &= keep - 1;
+            const float dv = fmaxf(nrow + srow[j], 0.f);
+            const uint64_t key = pack(dv, (uint32_t)(c0 + j));
+            if (!isinf(dv) && key < root) {
+              tc::heap_replace(heap, key);
+              root = heap[1];
+              const float nthr = root == kEmpty ? kInf : key_dist(root);
+              // slightly permissive: rounding of the folded threshold must
+              // not drop a column the certified pool counts on
+              thr_adj = nthr - nrow + 1e-6f * (fabsf(nthr) + fabsf(nrow));
+            }
+          } while (keep);
+        }
+        __syncwarp();
+      };
+      if (mode != 3) {
+        // two chunks at a time: both TMEM loads behind one wait, the two
+        // chunks' distance terms interleaved, then their inserts in chunk
+        // order (the same lists as one chunk at a time)
 #pragma unroll 1
-      for (int q = 0; q < BN / 32; ++q) {
+        for (int q = 0; q < BN / 32; q += 2) {
+          const int64_t ca = (int64_t)t * BN + q * 32, cb = ca + 32;
+          uint32_t ra[32], rb[32];
+          tc::tmem_ld32_issue(tacc + (uint32_t)q * 32, ra);
+          tc::tmem_ld32_issue(tacc + (uint32_t)(q + 1) * 32, rb);
+          tc::tmem_ld_wait(ra);
+          tc::tmem_regs_after(rb);
+          if (ca >= cend) continue;  // warp-uniform
+          float va[32], vb[32];
+#pragma unroll
+          for (int i = 0; i < 32; ++i) {
+            va[i] = __uint_as_float(ra[i]);
+            vb[i] = __uint_as_float(rb[i]);
+          }
+          const float ma = prep(q, va);
+          const float mb = prep(q + 1, vb);
+          lists(ca, va, ma);
+          if (cb < cend) lists(cb, vb, mb);  // warp-uniform
+        }
+      }
+#pragma unroll 1
+      for (int q = 0; q < BN / 32 && mode == 3; ++q) {
         const int64_t c0 = (int64_t)t * BN + q * 32;
         float v[32];
-        tc::tmem_ld32(tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN + q * 32), v);
+        tc::tmem_ld32(tacc + (uint32_t)q * 32, v);
         if (c0 >= cend) continue;  // warp-uniform
-        if (mode == 3) {
+        {
           // the row's 32 distances, each formed as in the lists below
           // (+inf past the last column; NaN kept, which no selection
           // takes, as no list would), staged as this warp's 32 x 32 box in shared memory
@@ -539,52 +649,6 @@ __global__ void __launch_bounds__(192, 1)
           __syncwarp();
           continue;
         }
-        // n_col - 2<a,b> for the 32 columns and their minimum: most chunks
-        // end here, with no column under the row's threshold
-        const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
-        float vmin = kInf;
-#pragma unroll
-        for (int j4 = 0; j4 < 8; ++j4) {
-          const float4 nn = n4[j4];
-          tc::fma2_m2(v[4 * j4 + 0], v[4 * j4 + 1], nn.x, nn.y);
-          tc::fma2_m2(v[4 * j4 + 2], v[4 * j4 + 3], nn.z, nn.w);
-          vmin = fminf(vmin, fminf(fminf(v[4 * j4 + 0], v[4 * j4 + 1]), fminf(v[4 * j4 + 2], v[4 * j4 + 3])));
-        }
-        const bool maybe = vmin <= thr_adj;
-        if (!__any_sync(0xffffffffu, maybe)) continue;
-        unsigned keep = 0;
-        if (maybe) {
-          // columns c0 + j valid for this row, as a bit mask
-          const int32_t rem = lim - (int32_t)c0;
-          unsigned vmask = rem >= 32 ? 0xffffffffu : (rem <= 0 ? 0u : ((1u << rem) - 1u));
-          const int32_t so = self - (int32_t)c0;
-          if (so >= 0 && so < 32) vmask &= ~(1u << so);
-#pragma unroll
-          for (int j = 0; j < 32; ++j) keep |= (v[j] <= thr_adj) ? (1u << j) : 0u;
-          keep &= vmask;
-        }
-        if (keep) {
-          // this lane's row: stage the passing values, then offer them to
-          // the row's heap one by one (rows in parallel, one per lane)
-          float* srow = sm.s[ew][lane];
-#pragma unroll
-          for (int j = 0; j < 32; ++j) srow[j] = v[j];
-          do {
-            const int j = __ffs(keep) - 1;
-            keep &= keep - 1;
-            const float dv = fmaxf(nrow + srow[j], 0.f);
-            const uint64_t key = pack(dv, (uint32_t)(c0 + j));
-            if (!isinf(dv) && key < root) {
-              tc::heap_replace(heap, key);
-              root = heap[1];
-              const float nthr = root == kEmpty ? kInf : key_dist(root);
-              // slightly permissive: rounding of the folded threshold must
-              // not drop a column the certified pool counts on
-              thr_adj = nthr - nrow + 1e-6f * (fabsf(nthr) + fabsf(nrow));
-            }
-          } while (keep);
-        }
-        __syncwarp();
       }
       if (mode == 3 && out_cmin && grow < s) {
         // this row's chunk minima of the tile, BN / 32 floats, as 16-byte stores
