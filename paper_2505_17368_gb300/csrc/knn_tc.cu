@@ -261,16 +261,22 @@ __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::be
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
 // Replaces the root of a row's max-heap (heap[1..KP], heap[KP + 1] = 0) by
-// a smaller key and sifts it down.
+// a smaller key and sifts it down.  The heap is 4-ary: the children of node
+// p are 4p - 2 .. 4p + 1 (node 8's last child is the sentinel), read as two
+// 16-byte loads, three levels below the root where a binary heap has five.
+static_assert(KP == 32, "node 8's children end at the sentinel KP + 1");
 __device__ __forceinline__ void heap_replace(uint64_t* heap, uint64_t key) {
   int p = 1;
-  for (int c = 2; c <= KP; c = 2 * p) {
-    const ulonglong2 ch = *reinterpret_cast<const ulonglong2*>(heap + c);
-    const bool right = ch.y > ch.x;
-    const uint64_t mv = right ? ch.y : ch.x;
+  for (int c = 2; c <= KP; c = 4 * p - 2) {
+    const ulonglong2 a = *reinterpret_cast<const ulonglong2*>(heap + c);
+    const ulonglong2 b = *reinterpret_cast<const ulonglong2*>(heap + c + 2);
+    const bool ra = a.y > a.x, rb = b.y > b.x;
+    const uint64_t ma = ra ? a.y : a.x, mb = rb ? b.y : b.x;
+    const bool second = mb > ma;
+    const uint64_t mv = second ? mb : ma;
     if (mv < key) break;  // keys are distinct
     heap[p] = mv;
-    p = c + (right ? 1 : 0);
+    p = c + (second ? 2 + (rb ? 1 : 0) : (ra ? 1 : 0));
   }
   heap[p] = key;
 }
