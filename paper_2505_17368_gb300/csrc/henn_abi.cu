@@ -1331,15 +1331,15 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         // a small layer: the distance matrix itself (written and read once,
         // coalesced) and a selection pass at full occupancy; else the
         // running lists inside the tile epilogue
-        const int64_t ldo = (s + 31) / 32 * 32;
+        const int64_t ldo = (s + 63) / 64 * 64;  // 16-bit keys: rows of whole 128-byte lines
         if (s <= kDenseExactMax) {
           int l2 = 0;
           CK(cudaDeviceGetAttribute(&l2, cudaDevAttrL2CacheSize, idx->device));
           const double chunk_bytes =
               HENN_EXACT_L2_SHARE > 0 ? std::max(8.0 * (1 << 20), (double)l2 / HENN_EXACT_L2_SHARE) : 1.0 * (1 << 30);
-          int64_t qc = (int64_t)(chunk_bytes / (4.0 * (double)ldo)) / 128 * 128;
+          int64_t qc = (int64_t)(chunk_bytes / (2.0 * (double)ldo)) / 128 * 128;
           qc = std::max<int64_t>(128, std::min<int64_t>(qc, nq));
-          float* dm = sc.get<float>((size_t)qc * ldo);
+          uint16_t* dm = sc.get<uint16_t>((size_t)qc * ldo);
           // each row's 32-column chunk minima: whole 256-column tiles, 8 per tile
           const int64_t ldc = (s + 255) / 256 * 8;
           float* cmn = sc.get<float>((size_t)qc * ldc);

@@ -80,16 +80,19 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
 void launch_split_bf16(const float* x, int64_t s, int32_t dpad, int32_t dk, void* hi, void* lo, cudaStream_t st);
 // mode 2 on tensor cores from pre-split planes: na rows (queries) against nb
 // columns (a layer's points), out = na x 32 keys (distance, column); with
-// out_d (mode 3) the distances themselves instead, na rows of ldo floats
-// (ldo a multiple of 32, >= nb; +inf past column nb)
+// out_d (mode 3) every distance instead, as a 16-bit order-preserving key
+// (the distance's float bits 30..15: rounded down to 8 mantissa bits), na
+// rows of ldo keys (ldo a multiple of 64, >= nb, out_d 128-byte aligned;
+// the key of +inf past column nb)
 // b_maps: the four tensor maps of make_column_maps, 128 bytes each;
 // tile_n: columns per tile, 128 or 256 (0 = 256), the same results
 // out_cmin (mode 3, nullable): each row's minimum over every 32-column chunk,
-// rows of ldc floats (ldc a multiple of 8 covering every tile, 16-byte aligned)
+// as the lower end of its key's bucket, rows of ldc floats (ldc a multiple
+// of 8 covering every tile, 16-byte aligned)
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err, int32_t tile_n,
-                                 cudaStream_t st);
+                                 uint16_t* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err,
+                                 int32_t tile_n, cudaStream_t st);
 // Tensor maps of the column operand (hi, lo planes of nb rows, dk wide) for
 // launch_tile_cross_tc -- hi and lo for tiles of 256 columns, then for 128 --
 // written to maps (4 x 128 bytes); false if not encodable.

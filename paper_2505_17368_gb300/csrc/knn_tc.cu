@@ -6,7 +6,8 @@
 // from one layer in insertion order, column c valid for row r iff c < r
 // (causal, NSW) or c != r (kNN graph); mode 2 takes the rows from one set
 // (queries) and every column from another (a layer's points); mode 3 is
-// mode 2 writing every tile value (the distance matrix) instead of lists.
+// mode 2 writing every tile value (the distance matrix, as 16-bit keys that
+// keep the order of the distances) instead of lists.
 //
 // Precision: each FP32 operand is split into x = hi + lo with hi =
 // bf16(x), lo = bf16(x - hi); the tile accumulates hi.hi + lo.hi + hi.lo in
@@ -169,6 +170,18 @@ __device__ __forceinline__ float max_nan0(float x) {
   return r;
 }
 
+// Distance keys of the mode-3 matrix: bits 30..15 of a distance that is
+// >= 0 (or -0, +inf, NaN), an order-preserving 16-bit code (8 exponent and 8
+// mantissa bits; -0 maps to the code of +0, +inf to 0xFF00, NaN above it).
+// A key k stands for every distance in [k << 15, (k + 1) << 15) read as
+// float bits: the distance rounded down to 8 mantissa bits.  Two keys per
+// word, the first column in the low half (the lower address).
+__device__ __forceinline__ uint32_t key16x2(float a, float b) {
+  return ((__float_as_uint(a) >> 15) & 0xFFFFu) | ((__float_as_uint(b) << 1) & 0xFFFF0000u);
+}
+// the lower end of a distance's key bucket, as a float
+__device__ __forceinline__ float key16_floor(float x) { return __uint_as_float((__float_as_uint(x) >> 15) << 15); }
+
 __device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
   asm volatile(
       "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];" ::"r"(
@@ -291,7 +304,7 @@ __global__ void __launch_bounds__(192, 1)
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                    const __grid_constant__ CUtensorMap to_d,
                    const float* __restrict__ norms, const float* __restrict__ norms_c, int64_t s, int64_t sc,
-                   int32_t kc, int32_t mode, uint64_t* __restrict__ out, float* __restrict__ out_d, int64_t ldo,
+                   int32_t kc, int32_t mode, uint64_t* __restrict__ out, uint16_t* __restrict__ out_d, int64_t ldo,
                    float* __restrict__ out_cmin, int64_t ldc,
                    int32_t nsplit, int32_t* __restrict__ err, long long spin_limit, int32_t hold) {
   using Smem = typename std::conditional<kStream, SmemStr<BN>, SmemRes<BN>>::type;
@@ -492,7 +505,7 @@ __global__ void __launch_bounds__(192, 1)
     uint64_t root = kEmpty;
     // mode 3 keeps no lists: the heap space holds each warp's two 4 KB
     // store boxes (1024-byte aligned)
-    float* m3_stage = reinterpret_cast<float*>(&sm.heap[0][0]) + ew * 2048;
+    uint32_t* m3_stage = reinterpret_cast<uint32_t*>(&sm.heap[0][0]) + ew * 2048;
     int m3_buf = 0;
     bool ok = true;
     float pn[BN / 32];  // column norms of the next tile, one per lane and chunk
@@ -602,59 +615,82 @@ __global__ void __launch_bounds__(192, 1)
           if (cb < cend) lists(cb, vb, mb);  // warp-uniform
         }
       }
+      // mode 3: the distances as 16-bit keys, two 32-column chunks (64
+      // columns, one 128-byte row of the box) at a time behind one TMEM wait
 #pragma unroll 1
-      for (int q = 0; q < BN / 32 && mode == 3; ++q) {
+      for (int q = 0; q < BN / 32 && mode == 3; q += 2) {
         const int64_t c0 = (int64_t)t * BN + q * 32;
-        float v[32];
-        tc::tmem_ld32(tacc + (uint32_t)q * 32, v);
+        uint32_t ra[32], rb[32];
+        tc::tmem_ld32_issue(tacc + (uint32_t)q * 32, ra);
+        tc::tmem_ld32_issue(tacc + (uint32_t)(q + 1) * 32, rb);
+        tc::tmem_ld_wait(ra);
+        tc::tmem_regs_after(rb);
         if (c0 >= cend) continue;  // warp-uniform
-        {
-          // the row's 32 distances, each formed as in the lists below
-          // (+inf past the last column; NaN kept, which no selection
-          // takes, as no list would), staged as this warp's 32 x 32 box in shared memory
-          // (128-byte rows, 16-byte chunks swizzled by row, as the tensor
-          // map's 128B swizzle expects) and written by one bulk tensor store
-          float* buf = m3_stage + m3_buf * 1024;
-          if (lane == 0) tc::bulk_wait_read_le1();  // the store that read buf two chunks ago
-          __syncwarp();
-          const float4* n4 = reinterpret_cast<const float4*>(ncs + q * 32);
-          float4* brow = reinterpret_cast<float4*>(buf + lane * 32);
-          float cmin = kInf;  // the chunk's minimum for this row (fminf passes over a NaN)
-          if (c0 + 32 <= sc) {  // warp-uniform: every column of the chunk valid
+        // the row's 64 distances, each formed as in the lists above (+inf
+        // past the last column; NaN kept, which no selection takes), as
+        // keys staged in this warp's 32 x 64 box in shared memory (128-byte
+        // rows, 16-byte pieces swizzled by row, as the tensor map's 128B
+        // swizzle expects) and written by one bulk tensor store
+        uint32_t* buf = m3_stage + m3_buf * 1024;
+        if (lane == 0) tc::bulk_wait_read_le1();  // the store that read buf two pairs ago
+        __syncwarp();
+        uint4* brow = reinterpret_cast<uint4*>(buf + lane * 32);
+        float cm[2] = {kInf, kInf};  // each chunk's minimum for this row (fminf passes over a NaN)
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-              const float4 nn = n4[j4];
-              float t0 = v[4 * j4 + 0], t1 = v[4 * j4 + 1], t2 = v[4 * j4 + 2], t3 = v[4 * j4 + 3];
-              tc::fma2_m2(t0, t1, nn.x, nn.y);
-              tc::fma2_m2(t2, t3, nn.z, nn.w);
-              tc::add2_s(t0, t1, nrow);
-              tc::add2_s(t2, t3, nrow);
-              const float4 o4 = make_float4(max_nan0(t0), max_nan0(t1), max_nan0(t2), max_nan0(t3));
-              brow[j4 ^ (lane & 7)] = o4;
-              cmin = fminf(cmin, fminf(fminf(o4.x, o4.y), fminf(o4.z, o4.w)));
+        for (int h = 0; h < 2; ++h) {
+          uint32_t(&r)[32] = h == 0 ? ra : rb;
+          const float4* n4 = reinterpret_cast<const float4*>(ncs + (q + h) * 32);
+          const int64_t ch0 = c0 + 32 * h;
+          if (ch0 + 32 <= sc) {  // warp-uniform: every column of the chunk valid
+#pragma unroll
+            for (int j4 = 0; j4 < 8; j4 += 2) {
+              float o[8];
+#pragma unroll
+              for (int u = 0; u < 2; ++u) {
+                const float4 nn = n4[j4 + u];
+                float t0 = __uint_as_float(r[4 * (j4 + u) + 0]), t1 = __uint_as_float(r[4 * (j4 + u) + 1]);
+                float t2 = __uint_as_float(r[4 * (j4 + u) + 2]), t3 = __uint_as_float(r[4 * (j4 + u) + 3]);
+                tc::fma2_m2(t0, t1, nn.x, nn.y);
+                tc::fma2_m2(t2, t3, nn.z, nn.w);
+                tc::add2_s(t0, t1, nrow);
+                tc::add2_s(t2, t3, nrow);
+                o[4 * u + 0] = max_nan0(t0);
+                o[4 * u + 1] = max_nan0(t1);
+                o[4 * u + 2] = max_nan0(t2);
+                o[4 * u + 3] = max_nan0(t3);
+              }
+#pragma unroll
+              for (int e = 0; e < 8; ++e) cm[h] = fminf(cm[h], o[e]);
+              brow[(4 * h + j4 / 2) ^ (lane & 7)] =
+                  make_uint4(key16x2(o[0], o[1]), key16x2(o[2], o[3]), key16x2(o[4], o[5]), key16x2(o[6], o[7]));
             }
           } else {
 #pragma unroll
-            for (int j4 = 0; j4 < 8; ++j4) {
-              const float4 nn = n4[j4];
-              const float nc[4] = {nn.x, nn.y, nn.z, nn.w};
-              float o[4];
+            for (int j4 = 0; j4 < 8; j4 += 2) {
+              float o[8];
 #pragma unroll
-              for (int e = 0; e < 4; ++e) {
-                o[e] = c0 + 4 * j4 + e < sc ? max_nan0(nrow + fmaf(-2.f, v[4 * j4 + e], nc[e])) : kInf;
-                cmin = fminf(cmin, o[e]);
+              for (int e = 0; e < 8; ++e) {
+                const int j = 4 * j4 + e;
+                const float nc = ncs[(q + h) * 32 + j];
+                o[e] = ch0 + j < sc ? max_nan0(nrow + fmaf(-2.f, __uint_as_float(r[j]), nc)) : kInf;
+                cm[h] = fminf(cm[h], o[e]);
               }
-              brow[j4 ^ (lane & 7)] = make_float4(o[0], o[1], o[2], o[3]);
+              brow[(4 * h + j4 / 2) ^ (lane & 7)] =
+                  make_uint4(key16x2(o[0], o[1]), key16x2(o[2], o[3]), key16x2(o[4], o[5]), key16x2(o[6], o[7]));
             }
           }
-          if (out_cmin) sm.s[ew][lane][q] = cmin;
-          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-          __syncwarp();
-          if (lane == 0) tc::tma_store_2d(&to_d, buf, (int)c0, (int)(r0 + 32 * sub));
-          m3_buf ^= 1;
-          __syncwarp();
-          continue;
         }
+        if (out_cmin) {
+          // the lower ends of the minima's key buckets: the minimum of a
+          // chunk's key lower ends
+          sm.s[ew][lane][q] = key16_floor(cm[0]);
+          sm.s[ew][lane][q + 1] = key16_floor(cm[1]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncwarp();
+        if (lane == 0) tc::tma_store_2d(&to_d, buf, (int)c0, (int)(r0 + 32 * sub));
+        m3_buf ^= 1;
+        __syncwarp();
       }
       if (mode == 3 && out_cmin && grow < s) {
         // this row's chunk minima of the tile, BN / 32 floats, as 16-byte stores
@@ -737,15 +773,16 @@ static PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// FP32 matrix of `rows` x ld, stored by 32 x 32 boxes (128B swizzle)
+// 16-bit key matrix of `rows` x ld, stored by boxes of 32 rows x 64 keys
+// (128-byte box rows, 128B swizzle)
 static bool make_store_map(CUtensorMap* m, const void* base, int64_t rows, int64_t ld) {
   auto fn = encode_fn();
   if (!fn) return false;
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
-  cuuint64_t strides[1] = {(cuuint64_t)ld * 4};
-  cuuint32_t box[2] = {32, 32};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * 2};
+  cuuint32_t box[2] = {64, 32};
   cuuint32_t estr[2] = {1, 1};
-  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<void*>(base), dims, strides, box, estr,
+  CUresult r = fn(m, CU_TENSOR_MAP_DATA_TYPE_UINT16, 2, const_cast<void*>(base), dims, strides, box, estr,
                   CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                   CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS;
@@ -781,7 +818,7 @@ static_assert((2 * A_CHUNK) <= STAGE && BN_MAX * BK * 2 <= STAGE && A_CHUNK % 10
 // variant.
 struct TileVariant {
   void (*fn)(CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, CUtensorMap, const float*, const float*, int64_t,
-             int64_t, int32_t, int32_t, uint64_t*, float*, int64_t, float*, int64_t, int32_t, int32_t*, long long,
+             int64_t, int32_t, int32_t, uint64_t*, uint16_t*, int64_t, float*, int64_t, int32_t, int32_t*, long long,
              int32_t);
   size_t smem;
 };
@@ -846,11 +883,13 @@ bool make_column_maps(const void* b_hi, const void* b_lo, int64_t nb, int32_t dk
 
 cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float* a_norms, int64_t na,
                                  const void* b_maps, const float* b_norms, int64_t nb, int32_t dk, uint64_t* out,
-                                 float* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err, int32_t tile_n,
-                                 cudaStream_t st) {
+                                 uint16_t* out_d, int64_t ldo, float* out_cmin, int64_t ldc, int32_t* err,
+                                 int32_t tile_n, cudaStream_t st) {
   const int32_t BN = tile_n == 128 ? 128 : 256;
   if (dk % BK != 0 || dk / BK > MAX_KC || na < 1 || nb < 1) return cudaErrorInvalidValue;
-  if (out_d && (ldo % 32 != 0 || ldo < nb)) return cudaErrorInvalidValue;
+  // key rows of whole 128-byte lines, 128-byte aligned (the selection drops them from L2 by line)
+  if (out_d && (ldo % 64 != 0 || ldo < nb || (reinterpret_cast<uintptr_t>(out_d) & 127) != 0))
+    return cudaErrorInvalidValue;
   // chunk minima: rows of ldc floats covering every tile's BN / 32 chunks, 16-byte aligned
   if (out_cmin && (!out_d || ldc % 8 != 0 || ldc * 32 < (nb + 255) / 256 * 256 ||
                    (reinterpret_cast<uintptr_t>(out_cmin) & 15) != 0))

@@ -516,7 +516,8 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
 // keys (traversal distance, layer position) of its 32 nearest points,
 // ascending, one per lane (kEmpty past the layer's size).  Method 1 starts
 // from the query's 32 tile candidates, rescored here: a point outside them
-// has a tile distance >= thr (the 32nd candidate's), so a true distance >=
+// has a tile distance >= thr (the 32nd candidate's, rounded down to its
+// 16-bit key's bucket by the selection), so a true distance >=
 // thr - beta, beta bounding the tile error for this query; if that exceeds
 // the need-th rescored distance (widened for its own rounding), no outside
 // point belongs to the first `need` keys.  Otherwise, and for method 2,
@@ -1142,12 +1143,16 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 
 // One warp per query: the 32 smallest (distance, column) keys of its row of
 // a tile distance matrix (+inf entries never enter), ascending, one per
-// lane.  The tile launch also wrote each row's minimum over every 32-column
-// chunk (cmin, rows of ldc floats).  T = the 32nd smallest of those chunk
-// minima bounds the row's 32nd smallest value (32 distinct columns lie at
-// or below it), and a column at or below T lies in a chunk whose minimum is
-// at or below T: only those chunks (32 of them, plus ties) are read, four
-// 128-byte chunks at a time, and their entries <= T merged into the running
+// lane.  The matrix holds 16-bit keys, each the distance rounded down to 8
+// mantissa bits (its float bits 30..15); an entry's distance here is the
+// lower end of its key's bucket (the key shifted back), so every column
+// outside the 32 has a tile distance at or above the 32nd's.  The tile
+// launch also wrote each row's minimum over every 32-column chunk (cmin,
+// rows of ldc floats, the same rounding).  T = the 32nd smallest of those
+// chunk minima bounds the row's 32nd smallest value (32 distinct columns lie
+// at or below it), and a column at or below T lies in a chunk whose minimum
+// is at or below T: only those chunks (32 of them, plus ties) are read, four
+// 64-byte chunks at a time, and their entries <= T merged into the running
 // list -- a few by shuffle insertion, many by sorting the batch and a
 // bitonic merge.  The result is the row's 32 smallest keys, as a full scan
 // would give; with `discard` each line read is dropped from L2 afterwards.
@@ -1157,7 +1162,10 @@ __device__ __forceinline__ float warp_sort_asc_f32(float v) {
 constexpr int kSelChunks = 128;  // candidate chunks listed per row
 constexpr int kSelKeys = 256;    // entries <= T staged per row
 
-__global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ D, const float* __restrict__ cmin,
+// the lower end of a 16-bit distance key's bucket
+__device__ __forceinline__ float key16_dist(uint32_t k) { return __uint_as_float(k << 15); }
+
+__global__ void __launch_bounds__(256) k_select_top32(const uint16_t* __restrict__ D, const float* __restrict__ cmin,
                                                       int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
                                                       uint64_t* __restrict__ out, int32_t discard) {
 #if HENN_SELECT_ONE_TRIP
@@ -1170,60 +1178,103 @@ __global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ 
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float* cm = cmin + q * ldc;
-    // the 32 smallest chunk minima, kept sorted across the warp
-    float best = kInf;
-    for (int g = 0; g < nch; g += 32) {
-      float v = g + lane < nch ? __ldg(cm + g + lane) : kInf;
-      v = __shfl_sync(0xffffffffu, warp_sort_asc_f32(v), 31 - lane);
-      float r = fminf(best, v);
+    // T = the 32nd smallest chunk minimum.  Rows of up to 128 chunks hold
+    // the minima as keys (each minimum is the lower end of its key's
+    // bucket, so the key is exact) and find T's key bit by bit from the top:
+    // the largest key t with at most 31 minima below it.  Longer rows keep
+    // the 32 smallest minima sorted across the warp.
+    const bool few = nch <= 128;
+    uint32_t mk[4];
+    uint32_t pk = 0;  // T's key (few rows)
+    float T;
+    if (few) {
 #pragma unroll
-      for (int o = 16; o > 0; o >>= 1) {
-        const float x = __shfl_xor_sync(0xffffffffu, r, o);
-        r = (lane & o) == 0 ? fminf(x, r) : fmaxf(x, r);
+      for (int j = 0; j < 4; ++j) {
+        const int c = 32 * j + lane;
+        mk[j] = c < nch ? (__float_as_uint(__ldg(cm + c)) >> 15) & 0xFFFFu : 0xFFFFu;
       }
-      best = r;
+      uint32_t p = 0;
+#pragma unroll 1
+      for (int b = 15; b >= 0; --b) {
+        const uint32_t t = p | (1u << b);
+        int cnt = 0;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cnt += __popc(__ballot_sync(0xffffffffu, mk[j] < t));
+        if (cnt <= 31) p = t;
+      }
+      // fewer than 32 finite minima: T = +inf (key 0xFF00; no minimum is NaN)
+      pk = min(p, 0xFF00u);
+      T = pk == 0xFF00u ? kInf : __uint_as_float(pk << 15);
+    } else {
+      float best = kInf;
+      for (int g = 0; g < nch; g += 32) {
+        float v = g + lane < nch ? __ldg(cm + g + lane) : kInf;
+        v = __shfl_sync(0xffffffffu, warp_sort_asc_f32(v), 31 - lane);
+        float r = fminf(best, v);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          const float x = __shfl_xor_sync(0xffffffffu, r, o);
+          r = (lane & o) == 0 ? fminf(x, r) : fmaxf(x, r);
+        }
+        best = r;
+      }
+      T = __shfl_sync(0xffffffffu, best, 31);
     }
-    const float T = __shfl_sync(0xffffffffu, best, 31);
     uint64_t mine = kEmpty, worst = kEmpty;
-    const float* row = D + q * ldo;
+    const uint16_t* row = D + q * ldo;
 #if HENN_SELECT_ONE_TRIP
     // the chunks that can hold an entry <= T (usually exactly 32): their ids
     // listed, then each lane loads one whole chunk, so that every chunk of
     // the row is in flight at once; the entries <= T are staged as keys and
     // merged 32 at a time.  Longer lists take the loop below.
     // whole chunks as 16-byte loads: rows 16-byte aligned
-    bool fast = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ldo % 4 == 0);
+    bool fast = ((reinterpret_cast<uintptr_t>(D) & 15) == 0) && (ldo % 8 == 0);
     if (fast) {
       int* chl = sel_chunks[threadIdx.x >> 5];
       uint64_t* stg = sel_keys[threadIdx.x >> 5];
       int nc = 0;
-      for (int g = 0; g < nch; g += 32) {
-        const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
-        const unsigned bm = __ballot_sync(0xffffffffu, in);
-        const int pos = nc + __popc(bm & ((1u << lane) - 1u));
-        if (in && pos < kSelChunks) chl[pos] = g + lane;
-        nc += __popc(bm);
+      if (few) {
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const bool in = 32 * j + lane < nch && mk[j] <= pk;
+          const unsigned bm = __ballot_sync(0xffffffffu, in);
+          const int pos = nc + __popc(bm & ((1u << lane) - 1u));
+          if (in) chl[pos] = 32 * j + lane;
+          nc += __popc(bm);
+        }
+      } else {
+        for (int g = 0; g < nch; g += 32) {
+          const bool in = g + lane < nch && __ldg(cm + g + lane) <= T;
+          const unsigned bm = __ballot_sync(0xffffffffu, in);
+          const int pos = nc + __popc(bm & ((1u << lane) - 1u));
+          if (in && pos < kSelChunks) chl[pos] = g + lane;
+          nc += __popc(bm);
+        }
       }
       fast = nc <= kSelChunks;
       __syncwarp();
       int n = 0;
+      // the keys <= T as integers: T is the lower end of a key's bucket,
+      // and keys of +inf or NaN (0xFF00 and above) never enter
+      const uint32_t Tk = min((__float_as_uint(T) >> 15) & 0xFFFFu, 0xFEFFu);
       for (int r0 = 0; fast && r0 < nc; r0 += 32) {
         const int ch = r0 + lane < nc ? chl[r0 + lane] : -1;
-        float v[32];
-        if (ch >= 0) {
-          const float4* src = reinterpret_cast<const float4*>(row + (int64_t)ch * 32);
-#pragma unroll
-          for (int i = 0; i < 8; ++i) {
-            const float4 f = __ldcs(src + i);
-            v[4 * i] = f.x;
-            v[4 * i + 1] = f.y;
-            v[4 * i + 2] = f.z;
-            v[4 * i + 3] = f.w;
-          }
-        }
+        uint32_t w[16];  // the chunk's 32 keys, two per word (the lower column in the low half)
         unsigned keep = 0;
+        if (ch >= 0) {
+          const uint4* src = reinterpret_cast<const uint4*>(row + (int64_t)ch * 32);
 #pragma unroll
-        for (int e = 0; e < 32; ++e) keep |= (ch >= 0 && v[e] <= T && !isinf(v[e])) ? (1u << e) : 0u;
+          for (int i = 0; i < 4; ++i) {
+            const uint4 x = __ldcs(src + i);
+            w[4 * i] = x.x;
+            w[4 * i + 1] = x.y;
+            w[4 * i + 2] = x.z;
+            w[4 * i + 3] = x.w;
+          }
+#pragma unroll
+          for (int i = 0; i < 16; ++i)
+            keep |= ((w[i] & 0xFFFFu) <= Tk ? 1u : 0u) << (2 * i) | ((w[i] >> 16) <= Tk ? 2u : 0u) << (2 * i);
+        }
         const int c = __popc(keep);
         int incl = c;
 #pragma unroll
@@ -1238,8 +1289,11 @@ __global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ 
         }
         int at = n + incl - c;
 #pragma unroll
-        for (int e = 0; e < 32; ++e)
-          if (keep & (1u << e)) stg[at++] = pack(v[e], (uint32_t)(ch * 32 + e));
+        for (int i = 0; i < 16; ++i) {
+          if (!(keep & (3u << (2 * i)))) continue;
+          if (keep & (1u << (2 * i))) stg[at++] = pack(key16_dist(w[i] & 0xFFFFu), (uint32_t)(ch * 32 + 2 * i));
+          if (keep & (2u << (2 * i))) stg[at++] = pack(key16_dist(w[i] >> 16), (uint32_t)(ch * 32 + 2 * i + 1));
+        }
         n += tot;
       }
       if (fast) {
@@ -1276,7 +1330,7 @@ __global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ 
         for (int b = 0; b < 4; ++b) {
           ch[b] = m ? g + __ffs(m) - 1 : -1;
           if (m) m &= m - 1;
-          dv[b] = ch[b] >= 0 ? __ldcs(row + (int64_t)ch[b] * 32 + lane) : kInf;
+          dv[b] = ch[b] >= 0 ? key16_dist(__ldcs(row + (int64_t)ch[b] * 32 + lane)) : kInf;
         }
 #pragma unroll
         for (int b = 0; b < 4; ++b) {
@@ -1317,18 +1371,18 @@ __global__ void __launch_bounds__(256) k_select_top32(const float* __restrict__ 
     __syncwarp();
     if (discard) {
       const char* rb = reinterpret_cast<const char*>(row);
-      for (int64_t l = lane; l < ldo / 32; l += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(rb + l * 128) : "memory");
+      for (int64_t l = lane; l < ldo / 64; l += 32) asm volatile("discard.global.L2 [%0], 128;" ::"l"(rb + l * 128) : "memory");
     }
   }
 }
 
-void launch_select_top32(const float* D, const float* cmin, int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
+void launch_select_top32(const uint16_t* D, const float* cmin, int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
                          uint64_t* out, bool discard, cudaStream_t st) {
   int64_t blocks = (nq + 7) / 8;
   if (blocks > 152 * 64) blocks = 152 * 64;
   if (blocks < 1) blocks = 1;
   // discard works on whole 128-byte lines: rows must start on one
-  const bool lines = (reinterpret_cast<uintptr_t>(D) & 127) == 0 && ldo % 32 == 0;
+  const bool lines = (reinterpret_cast<uintptr_t>(D) & 127) == 0 && ldo % 64 == 0;
   k_select_top32<<<(int)blocks, 256, 0, st>>>(D, cmin, nq, s, ldo, ldc, out, discard && lines ? 1 : 0);
 }
 

@@ -115,12 +115,13 @@ cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s
 // split BF16 planes (hi, lo, dk wide), each output nullable.
 void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric, const float* mean,
                           float* xo, void* hi, void* lo, int32_t dk, float* norms, cudaStream_t st);
-// Per query, the 32 smallest keys of its row of a distance matrix (nq rows
-// of ldo floats, s columns), guided by the rows' 32-column chunk minima
-// (cmin, rows of ldc floats, as the tile launch writes them): the tile
-// candidates of exact_method 1.  With discard, each row's cache lines are
+// Per query, the 32 smallest keys of its row of a distance-key matrix (nq
+// rows of ldo 16-bit keys as the tile launch's mode 3 writes them, s
+// columns), guided by the rows' 32-column chunk minima (cmin, rows of ldc
+// floats): the tile candidates of exact_method 1, each as (the lower end of
+// its key's bucket, column).  With discard, each row's cache lines are
 // dropped from L2 after it is read (its contents are undefined afterwards).
-void launch_select_top32(const float* D, const float* cmin, int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
+void launch_select_top32(const uint16_t* D, const float* cmin, int64_t nq, int64_t s, int64_t ldo, int64_t ldc,
                          uint64_t* out, bool discard, cudaStream_t st);
 cudaError_t launch_greedy_probe(const GreedyProbeArgs& a, int storage, cudaStream_t st);
 cudaError_t launch_serve(const ServeArgs& a, int warps_per_block, int grid, cudaStream_t st);
