@@ -253,7 +253,12 @@ void henn_search_params_default(henn_search_params* sp);
  * row q holds k[q] results in ascending distance (l2: Euclidean distance,
  * angular: 1 - cos), padded with -1 / +inf.  All arrays (Q, k, ef,
  * query_keys, stats, outputs) are device pointers if q_on_device, else host
- * pointers (the call then copies, runs and synchronises).
+ * pointers (the call then copies, runs and synchronises).  Host queries and
+ * host outputs in page-locked memory that the device can address
+ * (cudaHostAlloc, cudaMallocHost, cudaHostRegister with mapping) are read
+ * and written in place by the kernels over the host link instead of being
+ * staged through device memory (the outputs only when both are); the
+ * caller must not touch them until the call returns.
  * Errors: HENN_ERR_INVALID_ARG (k < 1, k > 1024, ef > 4096, stride < k,
  * NULL pointers), HENN_ERR_OOM, HENN_ERR_CUDA.
  */

@@ -379,6 +379,11 @@ class Index:
         exact_upper points gives its exact candidate set, found by a sort in
         the visited table (EXACT_SORT), one batched distance-tile launch with
         a certified rescore (EXACT_TILES) or a scan (EXACT_SCAN).
+        out: (ids, dists) to write into instead of new arrays -- CUDA tensors
+        for device queries; for host queries numpy arrays (int64 and float32,
+        C-contiguous, shape (nq, stride)), for instance views of page-locked
+        tensors, into which the results are copied directly (into pageable
+        memory the driver stages the copy through a buffer of its own).
         time_kernel: record the search launches' device time (last_search_ms).
         team_size: warps per query (1, 2 or 4; same results).
         tile_n: columns per tensor-core tile of the TILES exact layer (128 or 256; same results).
@@ -436,8 +441,16 @@ class Index:
                 dists = torch.empty((nq, stride), dtype=torch.float32, device=dev)
             st = torch.empty((nq, 4), dtype=torch.int32, device=dev) if stats else None
         else:
-            ids = np.empty((nq, stride), np.int64)
-            dists = np.empty((nq, stride), np.float32)
+            if out is not None:
+                ids, dists = out[0], out[1]
+                for a_, dt in ((ids, np.int64), (dists, np.float32)):
+                    if (not isinstance(a_, np.ndarray) or a_.dtype != dt or a_.shape != (nq, stride)
+                            or not a_.flags.c_contiguous or not a_.flags.writeable):
+                        raise HennError(1, f"out: host queries need writable C-contiguous numpy arrays of shape "
+                                           f"({nq}, {stride}), int64 ids and float32 distances")
+            else:
+                ids = np.empty((nq, stride), np.int64)
+                dists = np.empty((nq, stride), np.float32)
             st = np.empty((nq, 4), np.int32) if stats else None
         if st is not None:
             sp.stats = _ptr(st)[0]

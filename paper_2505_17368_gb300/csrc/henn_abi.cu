@@ -51,6 +51,18 @@ void require(bool ok, const std::string& msg) {
 
 // Stream-ordered scratch allocation, released when the owner goes out of
 // scope (also on failure).
+// The device address of a host buffer in page-locked memory the device can
+// address (cudaHostAlloc / cudaMallocHost, or registered with mapping), else
+// nullptr (pageable memory, which has to be staged).
+static void* mapped_host(const void* p) {
+  cudaPointerAttributes at;
+  if (p == nullptr || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();  // clear a sticky query error
+    return nullptr;
+  }
+  return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+}
+
 struct Scratch {
   cudaStream_t st;
   cudaMemPool_t pool;
@@ -1235,10 +1247,17 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     int64_t* dids = out_ids;
     float* dd = out_dists;
     int32_t* dstats = sp.stats;
+    bool out_in_place = q_on_device != 0;
     if (!q_on_device) {
-      float* q = sc.get<float>((size_t)nq * idx->d);
-      CK(cudaMemcpyAsync(q, Q, sizeof(float) * nq * idx->d, cudaMemcpyHostToDevice, st));
-      dQ = q;
+      // page-locked queries and outputs are used in place (the kernels read
+      // and write them over the host link); other host buffers are staged
+      if (const void* qm = mapped_host(Q)) {
+        dQ = static_cast<const float*>(qm);
+      } else {
+        float* q = sc.get<float>((size_t)nq * idx->d);
+        CK(cudaMemcpyAsync(q, Q, sizeof(float) * nq * idx->d, cudaMemcpyHostToDevice, st));
+        dQ = q;
+      }
       if (sp.k) {
         int32_t* t = sc.get<int32_t>(nq);
         CK(cudaMemcpyAsync(t, hk.data(), sizeof(int32_t) * nq, cudaMemcpyHostToDevice, st));
@@ -1254,8 +1273,11 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         CK(cudaMemcpyAsync(t, sp.query_keys, sizeof(uint64_t) * nq, cudaMemcpyHostToDevice, st));
         dkeys = t;
       }
-      dids = sc.get<int64_t>((size_t)nq * out_stride);
-      dd = sc.get<float>((size_t)nq * out_stride);
+      void* im = mapped_host(out_ids);
+      void* dm = mapped_host(out_dists);
+      out_in_place = im != nullptr && dm != nullptr;
+      dids = out_in_place ? static_cast<int64_t*>(im) : sc.get<int64_t>((size_t)nq * out_stride);
+      dd = out_in_place ? static_cast<float*>(dm) : sc.get<float>((size_t)nq * out_stride);
       if (sp.stats) dstats = sc.get<int32_t>((size_t)nq * 4);
     }
     // Per-query k / ef: queries are grouped by beam capacity and each group
@@ -1436,8 +1458,10 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
       tlk.unlock();
     }
     if (!q_on_device) {
-      CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
-      CK(cudaMemcpyAsync(out_dists, dd, sizeof(float) * nq * out_stride, cudaMemcpyDeviceToHost, st));
+      if (!out_in_place) {
+        CK(cudaMemcpyAsync(out_ids, dids, sizeof(int64_t) * nq * out_stride, cudaMemcpyDeviceToHost, st));
+        CK(cudaMemcpyAsync(out_dists, dd, sizeof(float) * nq * out_stride, cudaMemcpyDeviceToHost, st));
+      }
       if (sp.stats) CK(cudaMemcpyAsync(sp.stats, dstats, sizeof(int32_t) * nq * 4, cudaMemcpyDeviceToHost, st));
       CK(cudaStreamSynchronize(st));
     }

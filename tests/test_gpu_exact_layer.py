@@ -151,6 +151,21 @@ def test_host_buffers_and_small_batches(uniform10k):
     for nq in (1, 7, 129):
         c, cd, _ = gidx.search(Q[:nq], k=10, ef=32, exact_upper=1000, exact_method=H.EXACT_TILES)
         assert np.array_equal(c, b[:nq]) and np.array_equal(cd, bd[:nq])
+    # page-locked queries and results are used in place by the kernels;
+    # page-locked queries with pageable results: the results are staged
+    Qh = torch.from_numpy(Q).pin_memory()
+    f, fd, _ = gidx.search(Qh.numpy(), k=10, ef=32, exact_upper=1000, exact_method=H.EXACT_TILES)
+    assert np.array_equal(f, b) and np.array_equal(fd, bd)
+    # results written into the caller's page-locked buffers, twice in a row
+    ids_h = torch.full((Q.shape[0], 10), -7, dtype=torch.int64).pin_memory()
+    d_h = torch.full((Q.shape[0], 10), -7.0, dtype=torch.float32).pin_memory()
+    for _ in range(2):
+        e, ed, _ = gidx.search(Qh.numpy(), k=10, ef=32, exact_upper=1000, exact_method=H.EXACT_TILES,
+                               out=(ids_h.numpy(), d_h.numpy()))
+        assert np.array_equal(ids_h.numpy(), b) and np.array_equal(d_h.numpy(), bd)
+        assert np.shares_memory(e, ids_h.numpy()) and np.shares_memory(ed, d_h.numpy())
+    with pytest.raises(H.HennError):
+        gidx.search(Q, k=10, ef=32, out=(np.empty((Q.shape[0], 9), np.int64), np.empty((Q.shape[0], 9), np.float32)))
 
 
 def test_after_insert(uniform10k):
