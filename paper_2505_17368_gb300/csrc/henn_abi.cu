@@ -1248,11 +1248,13 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
     float* dd = out_dists;
     int32_t* dstats = sp.stats;
     bool out_in_place = q_on_device != 0;
+    bool q_in_host = false;  // the kernels read the queries from page-locked host memory
     if (!q_on_device) {
       // page-locked queries and outputs are used in place (the kernels read
       // and write them over the host link); other host buffers are staged
       if (const void* qm = mapped_host(Q)) {
         dQ = static_cast<const float*>(qm);
+        q_in_host = true;
       } else {
         float* q = sc.get<float>((size_t)nq * idx->d);
         CK(cudaMemcpyAsync(q, Q, sizeof(float) * nq * idx->d, cudaMemcpyHostToDevice, st));
@@ -1349,7 +1351,11 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         const int32_t dkk = round_up(dpad, 64);
         void* qh = sc.get<uint16_t>((size_t)nq * dkk);
         void* ql = sc.get<uint16_t>((size_t)nq * dkk);
-        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, nullptr, qh, ql, dkk, qn, st);
+        // queries read over the host link once: the query preparation also
+        // leaves a device copy for the search kernel
+        float* qraw = q_in_host ? sc.get<float>((size_t)nq * idx->d) : nullptr;
+        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, nullptr, qh, ql, dkk, qn, qraw, st);
+        if (qraw) a.Q = qraw;
         // a small layer: the distance matrix itself (written and read once,
         // coalesced) and a selection pass at full occupancy; else the
         // running lists inside the tile epilogue
@@ -1381,7 +1387,9 @@ extern "C" henn_status henn_search(const henn_index* idx, const float* Q, int64_
         launches += 2;
       } else {
         float* qo = sc.get<float>((size_t)nq * dpad);
-        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, qo, nullptr, nullptr, 0, qn, st);
+        float* qraw = q_in_host ? sc.get<float>((size_t)nq * idx->d) : nullptr;
+        launch_entry_queries(dQ, nq, idx->d, dpad, idx->metric, eo.mean, qo, nullptr, nullptr, 0, qn, qraw, st);
+        if (qraw) a.Q = qraw;
         const int64_t rb = (nq + 63) / 64;
         const int32_t splits =
             (int32_t)std::max<int64_t>(1, std::min<int64_t>((2 * 152 + rb - 1) / rb, (s + 4095) / 4096));

@@ -1076,19 +1076,45 @@ cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s
 }
 
 // One warp per query: the row exactly as run_query stages it (the angular
-// normalisation in the same order), minus the layer's centre.
-__global__ void k_entry_queries(const float* __restrict__ Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric,
-                                const float* __restrict__ mean, float* __restrict__ xo, __nv_bfloat16* __restrict__ hi,
-                                __nv_bfloat16* __restrict__ lo, int32_t dk, float* __restrict__ norms) {
+// normalisation in the same order), minus the layer's centre.  The row is
+// read once into shared memory (16-byte loads where the rows allow: the
+// rows may sit in page-locked host memory, read over the host link) and,
+// with qraw, also written there as read (a device copy for the search
+// kernel).
+constexpr int kEntryMaxD = 1024;
+
+__global__ void __launch_bounds__(256) k_entry_queries(const float* __restrict__ Q, int64_t nq, int32_t d,
+                                                       int32_t dpad, int32_t metric, const float* __restrict__ mean,
+                                                       float* __restrict__ xo, __nv_bfloat16* __restrict__ hi,
+                                                       __nv_bfloat16* __restrict__ lo, int32_t dk,
+                                                       float* __restrict__ norms, float* __restrict__ qraw) {
+  __shared__ __align__(16) float rows[8][kEntryMaxD];
   const int lane = threadIdx.x & 31;
+  float* r = rows[threadIdx.x >> 5];
+  const bool vec = (d % 4 == 0) && ((reinterpret_cast<uintptr_t>(Q) & 15) == 0) &&
+                   (!qraw || (reinterpret_cast<uintptr_t>(qraw) & 15) == 0);
   for (int64_t q = (blockIdx.x * (int64_t)blockDim.x + threadIdx.x) >> 5; q < nq;
        q += ((int64_t)gridDim.x * blockDim.x) >> 5) {
     const float* qg = Q + q * d;
+    if (vec) {
+      for (int c4 = lane; c4 < d / 4; c4 += 32) {
+        const float4 v = __ldcs(reinterpret_cast<const float4*>(qg) + c4);
+        reinterpret_cast<float4*>(r)[c4] = v;
+        if (qraw) reinterpret_cast<float4*>(qraw + q * d)[c4] = v;
+      }
+    } else {
+      for (int c = lane; c < d; c += 32) {
+        const float v = __ldcs(qg + c);
+        r[c] = v;
+        if (qraw) qraw[q * d + c] = v;
+      }
+    }
+    __syncwarp();
     float inv = 1.f;
     if (metric == HENN_ANGULAR) {
       float ss = 0.f;
       for (int c = lane; c < dpad; c += 32) {
-        const float v = c < d ? qg[c] : 0.f;
+        const float v = c < d ? r[c] : 0.f;
         ss = fmaf(v, v, ss);
       }
 #pragma unroll
@@ -1099,7 +1125,7 @@ __global__ void k_entry_queries(const float* __restrict__ Q, int64_t nq, int32_t
     for (int c = lane; c < dk; c += 32) {
       float v = 0.f;
       if (c < dpad) {
-        float x = c < d ? qg[c] : 0.f;
+        float x = c < d ? r[c] : 0.f;
         if (metric == HENN_ANGULAR) x *= inv;
         v = x - mean[c];
         acc = fmaf(v, v, acc);
@@ -1114,16 +1140,17 @@ __global__ void k_entry_queries(const float* __restrict__ Q, int64_t nq, int32_t
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
     if (lane == 0) norms[q] = acc;
+    __syncwarp();  // r is rewritten by the next query of this warp
   }
 }
 
 void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric, const float* mean,
-                          float* xo, void* hi, void* lo, int32_t dk, float* norms, cudaStream_t st) {
+                          float* xo, void* hi, void* lo, int32_t dk, float* norms, float* qraw, cudaStream_t st) {
   int64_t blocks = (nq + 7) / 8;
   if (blocks > 152 * 16) blocks = 152 * 16;
   if (blocks < 1) blocks = 1;
   k_entry_queries<<<(int)blocks, 256, 0, st>>>(Q, nq, d, dpad, metric, mean, xo, static_cast<__nv_bfloat16*>(hi),
-                                               static_cast<__nv_bfloat16*>(lo), hi ? dk : dpad, norms);
+                                               static_cast<__nv_bfloat16*>(lo), hi ? dk : dpad, norms, qraw);
 }
 
 // Bitonic sort of one float per lane across the warp, ascending.

@@ -112,9 +112,10 @@ cudaError_t launch_layer_rows_f32(const void* vec, const float* scale, int64_t s
                                   cudaStream_t st);
 // Queries as the search kernel sees them (angular: normalised the same
 // way), minus `mean`: squared norms, and FP32 rows (xo, dpad wide) and / or
-// split BF16 planes (hi, lo, dk wide), each output nullable.
+// split BF16 planes (hi, lo, dk wide), each output nullable; qraw
+// (nullable, nq x d): the rows as read (d <= 1024).
 void launch_entry_queries(const float* Q, int64_t nq, int32_t d, int32_t dpad, int32_t metric, const float* mean,
-                          float* xo, void* hi, void* lo, int32_t dk, float* norms, cudaStream_t st);
+                          float* xo, void* hi, void* lo, int32_t dk, float* norms, float* qraw, cudaStream_t st);
 // Per query, the 32 smallest keys of its row of a distance-key matrix (nq
 // rows of ldo 16-bit keys as the tile launch's mode 3 writes them, s
 // columns), guided by the rows' 32-column chunk minima (cmin, rows of ldc
