@@ -49,20 +49,20 @@ void require(bool ok, const std::string& msg) {
   if (!ok) throw Failure(HENN_ERR_INVALID_ARG, msg);
 }
 
-// Stream-ordered scratch allocation, released when the owner goes out of
-// scope (also on failure).
 // The device address of a host buffer in page-locked memory the device can
 // address (cudaHostAlloc / cudaMallocHost, or registered with mapping), else
 // nullptr (pageable memory, which has to be staged).
 static void* mapped_host(const void* p) {
   cudaPointerAttributes at;
   if (p == nullptr || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
-    cudaGetLastError();  // clear a sticky query error
+    cudaGetLastError();  // clear the failed query's error
     return nullptr;
   }
   return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
 }
 
+// Stream-ordered scratch allocation, released when the owner goes out of
+// scope (also on failure).
 struct Scratch {
   cudaStream_t st;
   cudaMemPool_t pool;
