@@ -12,6 +12,9 @@ the query preparation, tile and top-32 selection launches.  The end-to-end
 figure (`e2e`) times the same call with the queries and the result buffers
 in page-locked host memory, which the kernels read and write in place over
 the host link (5.12 MB in, 1.2 MB out per step, inside the timed region).
+After the timed regions a `serving` entry reports the resident serving loop
+on the same index under an open-loop request stream (achieved queries/s,
+p50 / p99 latency at two offered rates).
 
 The beam (ef, ef_upper, descend_all, ef_l1, exact_upper, exact_method,
 rerank_mult) is DEFAULT_BEAM unless --sweep or --beam picks another.  Its
@@ -533,6 +536,8 @@ def run_ours(args):
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
+    # ---- the serving loop on the same index (after every timed region)
+    serving = None if args.shape else _serving_leg(H, idx_bf16, Q, sizes)
     peaks, src = _peaks()
     # the search kernel's own device time (events around its launch), not the step's
     k_avg = statistics.mean(ms for ms, _ in kern) / 1e3
@@ -579,6 +584,8 @@ def run_ours(args):
         "gpu_launches": args.steps * launches_per_step,
         "clocks": clocks,
     }
+    if serving is not None:
+        line["serving"] = serving
     if rank == 0 and not args.no_cpu_baseline:
         layers = _export_layers(idx_bf16)
         qps, cores, secs, (qps_all, ncores) = _cpu_oracle_on_index(layers, X, Q, beam, args.cpu_nq)
@@ -618,6 +625,33 @@ def _build_roofline(info):
             "engine": engine, "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
             "executed_frac": mult * achieved / peak, "tile_seconds": info["tile_seconds"],
             "algorithmic_flops": info["tile_flops"], "peak_source": f"{src} bf16 sustained"}
+
+
+def _serving_leg(H, index, Q, sizes, rates=(5e5, 2e6), seconds=2.0):
+    """The resident serving loop (henn_serve_*) on the bench's index: an
+    open-loop Poisson request stream (batches log-uniform in [1, 4096],
+    k in {10, 100}, ef log-uniform in [64, 512]; serve_bench's mix) at two
+    offered rates, 2 s each; achieved queries/s and p50 / p99 latency.  Layer
+    3 gives its exact candidate set (in-kernel sort), seeding width-16 beams
+    on layer 2 and width-8 beams on layer 1.  Outside every timed region;
+    a failure is reported in the line instead of ending the run."""
+    from paper_2505_17368_gb300 import serve_bench
+
+    beam = dict(ef_upper=16, descend_all=1, ef_l1=8, exact_upper=int(sizes[3]) if len(sizes) > 3 else 0)
+    try:
+        srv = H.Server(index, ring_rows=1 << 17, max_requests=4096, max_k=100, max_ef=512, **beam)
+        try:
+            out = []
+            for r in rates:
+                res = serve_bench.run_rate(srv, Q, r, seconds, 4096, seed=int(r) % 1000)
+                out.append({k: res[k] for k in ("offered_qps", "achieved_qps", "p50_ms", "p99_ms", "requests")})
+        finally:
+            srv.close()
+    except Exception as e:  # noqa: BLE001 -- reported, the headline stands
+        return {"error": str(e)[:300]}
+    return {"workload": WORKLOAD, "form": "bf16 + fp32 rerank", "beam": beam,
+            "mix": "Poisson arrivals; batch log-uniform [1, 4096], k in {10, 100}, ef log-uniform [64, 512]",
+            "rates": out}
 
 
 def _profile_traffic(beam, rerank_mult=4):
@@ -663,7 +697,8 @@ def main():
                     help="ef,ef_upper,descend_all,ef_l1,exact_upper,exact_method[,rerank_mult] instead of "
                          "DEFAULT_BEAM (exact_upper may be L<i>, the size of layer i)")
     ap.add_argument("--shape", default=None,
-                    help="warps_per_block,team_size,hash_bits,tile_n: a fixed launch shape instead of the autotuner's")
+                    help="warps_per_block,team_size,hash_bits,tile_n: a fixed launch shape instead of the "
+                         "autotuner's (for runs under a profiler; the serving leg is skipped then)")
     args = ap.parse_args()
     if args.warmup < 3:
         ap.error("--warmup must be >= 3")
