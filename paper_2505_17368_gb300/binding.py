@@ -381,9 +381,10 @@ class Index:
         a certified rescore (EXACT_TILES) or a scan (EXACT_SCAN).
         out: (ids, dists) to write into instead of new arrays -- CUDA tensors
         for device queries; for host queries numpy arrays (int64 and float32,
-        C-contiguous, shape (nq, stride)), for instance views of page-locked
-        tensors, into which the results are copied directly (into pageable
-        memory the driver stages the copy through a buffer of its own).
+        C-contiguous, shape (nq, stride)).  Page-locked host buffers (for
+        instance views of pinned tensors) are read and written in place by the
+        kernels -- the queries, and the results when both arrays are; pageable
+        ones are staged through device memory by copies.
         time_kernel: record the search launches' device time (last_search_ms).
         team_size: warps per query (1, 2 or 4; same results).
         tile_n: columns per tensor-core tile of the TILES exact layer (128 or 256; same results).
