@@ -250,3 +250,47 @@ def test_tied_distances_equal_scan():
             if efu == 1:
                 # most queries kept the certified candidates (fewer evaluations than a scan)
                 assert out[H.EXACT_TILES][2][:, 0].sum() < out[H.EXACT_SCAN][2][:, 0].sum()
+
+
+@pytest.mark.parametrize("case", ["angular-bf16-d96", "f32-d200", "per-query-k-ef"])
+def test_page_locked_host_buffers_equal_device(case):
+    """Queries and results in page-locked host memory are read and written in
+    place by the kernels (the query preparation leaving a device copy for
+    the search kernel): the same answers and counters as device-resident
+    queries, for the angular metric (normalised from the staged row), rows
+    wider than 128 values, and per-query k / ef (those arrays staged)."""
+    if case == "angular-bf16-d96":
+        X, _ = synth.gaussian_mixture(20000, 96, 100, seed=7, normalise=True)
+        Q, _ = synth.gaussian_mixture(1000, 96, 100, seed=107, normalise=True)
+        kw = dict(metric=H.ANGULAR, storage=H.BF16)
+    elif case == "f32-d200":
+        X, r = synth.gaussian_mixture(10000, 200, 100, seed=8, rescale_to_255=True)
+        Q, _ = synth.gaussian_mixture(700, 200, 100, seed=108, rescale_from=r, rescale_to_255=True)
+        kw = dict(storage=H.F32)
+    else:
+        X, r = synth.gaussian_mixture(20000, 128, 100, seed=9, rescale_to_255=True)
+        Q, _ = synth.gaussian_mixture(1000, 128, 100, seed=109, rescale_from=r, rescale_to_255=True)
+        kw = dict(storage=H.BF16)
+    Q = np.ascontiguousarray(Q)
+    gidx = _gpu_index(X, seed=3, **kw)
+    sizes = gidx.info()["sizes"]
+    sk = dict(ef_upper=16, descend_all=1, exact_upper=sizes[2] if len(sizes) > 2 else sizes[1],
+              exact_method=H.EXACT_TILES)
+    nq = len(Q)
+    if case == "per-query-k-ef":
+        rng = np.random.default_rng(3)
+        k = rng.choice([1, 10, 32], nq).astype(np.int32)
+        ef = rng.integers(16, 96, nq).astype(np.int32)
+        stride = 32
+        kd, efd = torch.from_numpy(k).to(DEV), torch.from_numpy(ef).to(DEV)
+    else:
+        k, ef, stride = 10, 48, 10
+        kd, efd = k, ef
+    a_ids, a_d, a_st = gidx.search(torch.from_numpy(Q).to(DEV), k=kd, ef=efd, out_stride=stride, stats=True, **sk)
+    Qh = torch.from_numpy(Q).pin_memory()
+    ids_h = torch.empty((nq, stride), dtype=torch.int64).pin_memory()
+    d_h = torch.empty((nq, stride), dtype=torch.float32).pin_memory()
+    b_ids, b_d, b_st = gidx.search(Qh.numpy(), k=k, ef=ef, out_stride=stride, stats=True,
+                                   out=(ids_h.numpy(), d_h.numpy()), **sk)
+    assert np.array_equal(a_ids.cpu().numpy(), b_ids) and np.array_equal(a_d.cpu().numpy(), b_d)
+    assert np.array_equal(a_st.cpu().numpy(), b_st)
