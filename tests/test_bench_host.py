@@ -97,3 +97,16 @@ def test_profile_traffic_without_summary(tmp_path, monkeypatch):
     monkeypatch.setattr(bench, "ROOT", str(tmp_path))
     assert not os.path.exists(tmp_path / "profiles")
     assert bench._profile_traffic((48, 8, 1, 0, 3677, 1)) is None
+
+
+def test_serving_leg_reports_a_failure_instead_of_raising():
+    """The serving measurement runs after the timed regions; a failure there
+    (here a server that cannot be created) is reported in the line and the
+    headline stands."""
+    class _FakeH:
+        class Server:
+            def __init__(self, *a, **kw):
+                raise RuntimeError("no serving kernel on this host")
+
+    out = bench._serving_leg(_FakeH, index=None, Q=np.zeros((4, 128), np.float32), sizes=[1000, 100, 37, 5])
+    assert out == {"error": "no serving kernel on this host"}
