@@ -536,8 +536,9 @@ def run_ours(args):
         if i >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
     e2e_tmax, e2e_units = aggregate(sum(e2e_t), args.nq * args.steps)
-    # ---- the serving loop on the same index (after every timed region)
-    serving = None if args.shape else _serving_leg(H, idx_bf16, Q, sizes)
+    # ---- the serving loop on the same index (after every timed region; rank 0's GPU only, so
+    # that the other ranks' host threads do not compete with its submitter and poller)
+    serving = None if (args.shape or rank != 0) else _serving_leg(H, idx_bf16, Q, sizes)
     peaks, src = _peaks()
     # the search kernel's own device time (events around its launch), not the step's
     k_avg = statistics.mean(ms for ms, _ in kern) / 1e3
