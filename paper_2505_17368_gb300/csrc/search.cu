@@ -373,8 +373,8 @@ __device__ __noinline__ int beam(const int32_t* __restrict__ adj, const void* ve
   int nw;
   if (nseed > 0) {
     nw = min(nseed, ef);
-    if (lane == 0)
-      for (int j = 0; j < nw; ++j) mark((int32_t)key_index(W[j] & kKeyMask));
+    // the seeds are distinct points: each lane marks its own
+    for (int j = lane; j < nw; j += 32) mark((int32_t)key_index(W[j] & kKeyMask));
   } else {
     if (lane == 0) mark(entry);
     float d0 = rows_dist<VT, G, CPL>(vec, scale, stride, entry, 1, qs, nchunk);
@@ -1220,16 +1220,30 @@ __global__ void __launch_bounds__(256) k_select_top32(const uint16_t* __restrict
         const int c = 32 * j + lane;
         mk[j] = c < nch ? (__float_as_uint(__ldg(cm + c)) >> 15) & 0xFFFFu : 0xFFFFu;
       }
-      uint32_t p = 0;
-#pragma unroll 1
-      for (int b = 15; b >= 0; --b) {
-        const uint32_t t = p | (1u << b);
-        int cnt = 0;
+      // fewer than 32 chunks: T = +inf (key 0xFF00; no minimum is NaN).
+      // Else T's key lies between the smallest and the largest minimum, so
+      // their common leading bits are its own and the search starts below
+      uint32_t p = 0xFFFFu;
+      if (nch >= 32) {
+        uint32_t lo = 0xFFFFu, hi = 0u;
 #pragma unroll
-        for (int j = 0; j < 4; ++j) cnt += __popc(__ballot_sync(0xffffffffu, mk[j] < t));
-        if (cnt <= 31) p = t;
+        for (int j = 0; j < 4; ++j) {
+          lo = min(lo, mk[j]);
+          if (32 * j + lane < nch) hi = max(hi, mk[j]);
+        }
+        lo = __reduce_min_sync(0xffffffffu, lo);
+        hi = __reduce_max_sync(0xffffffffu, hi);
+        const int free_bits = lo == hi ? 0 : 32 - __clz(lo ^ hi);  // bits below the common prefix
+        p = lo & ~((1u << free_bits) - 1u);
+#pragma unroll 1
+        for (int b = free_bits - 1; b >= 0; --b) {
+          const uint32_t t = p | (1u << b);
+          int cnt = 0;
+#pragma unroll
+          for (int j = 0; j < 4; ++j) cnt += __popc(__ballot_sync(0xffffffffu, mk[j] < t));
+          if (cnt <= 31) p = t;
+        }
       }
-      // fewer than 32 finite minima: T = +inf (key 0xFF00; no minimum is NaN)
       pk = min(p, 0xFF00u);
       T = pk == 0xFF00u ? kInf : __uint_as_float(pk << 15);
     } else {
@@ -1327,6 +1341,12 @@ __global__ void __launch_bounds__(256) k_select_top32(const uint16_t* __restrict
         __syncwarp();
         for (int b = 0; b < n; b += 32) {
           uint64_t kk = b + lane < n ? stg[b + lane] : kEmpty;
+          if (b == 0) {
+            // the first batch is the running list itself, sorted
+            mine = warp_sort_asc(kk);
+            worst = shfl64(mine, 31);
+            continue;
+          }
           if (!__any_sync(0xffffffffu, kk < worst)) continue;
           // the running list and the reversed sorted batch: their
           // element-wise minimum holds the 32 smallest as a bitonic sequence
