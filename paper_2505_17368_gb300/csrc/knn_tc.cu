@@ -137,6 +137,7 @@ __device__ __forceinline__ void tma_store_2d(const CUtensorMap* map, const void*
   asm volatile("cp.async.bulk.commit_group;" ::: "memory");
 }
 __device__ __forceinline__ void bulk_wait_read_le1() { asm volatile("cp.async.bulk.wait_group.read 1;" ::: "memory"); }
+__device__ __forceinline__ void bulk_wait_read_all() { asm volatile("cp.async.bulk.wait_group.read 0;" ::: "memory"); }
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 // (a, b) <- (c - 2a, d - 2b) as one paired FMA, each element rounded as
@@ -298,8 +299,11 @@ __device__ __forceinline__ void heap_replace(uint64_t* heap, uint64_t key) {
 
 using namespace tc;
 
-template <bool kStream, int BN>
-__global__ void __launch_bounds__(192, 1)
+// EPI: epilogue warps, 4 (one per TMEM sub-partition; the per-row lists of
+// modes 0-2 need it) or 8 (mode 3: two per sub-partition, each taking half of
+// every tile's chunks); the launch has 64 + 32 * EPI threads
+template <bool kStream, int BN, int EPI>
+__global__ void __launch_bounds__(64 + 32 * EPI, 1)
     k_tile_topk_tc(const __grid_constant__ CUtensorMap ta_hi, const __grid_constant__ CUtensorMap ta_lo,
                    const __grid_constant__ CUtensorMap tb_hi, const __grid_constant__ CUtensorMap tb_lo,
                    const __grid_constant__ CUtensorMap to_d,
@@ -335,7 +339,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int i = 0; i < 2; ++i) {
       tc::mbar_init(&sm.tfull[i], 1);
-      tc::mbar_init(&sm.tempty[i], 4);
+      tc::mbar_init(&sm.tempty[i], EPI);  // every epilogue warp frees it
     }
     tc::mbar_init(&sm.afull, 1);
     sm.abort = 0;
@@ -488,9 +492,13 @@ __global__ void __launch_bounds__(192, 1)
       }
     }
   } else {
-    // ---------------- epilogue: warps 2..5
+    // ---------------- epilogue: warps 2..5, or 2..9 in mode 3 (two warps
+    // per TMEM sub-partition, each taking half of every tile's chunks)
     const int ew = warp - 2;
     const int sub = warp & 3;  // TMEM sub-partition of this warp
+    constexpr int halves = EPI / 4;
+    const int qlo = (ew >> 2) * (BN / 32) / halves, qhi = qlo + (BN / 32) / halves;  // this warp's chunks
+    const int ews = ew & 3;  // per-sub-partition staging, shared by its warps on disjoint chunks
     const int row_l = 32 * sub + lane;
     const int64_t grow = r0 + row_l;
     const float nrow = grow < s ? norms[grow] : 0.f;
@@ -503,16 +511,15 @@ __global__ void __launch_bounds__(192, 1)
     float thr_adj = kInf;
     uint64_t* heap = sm.heap[row_l];
     uint64_t root = kEmpty;
-    // mode 3 keeps no lists: the heap space holds each warp's two 4 KB
-    // store boxes (1024-byte aligned)
-    uint32_t* m3_stage = reinterpret_cast<uint32_t*>(&sm.heap[0][0]) + ew * 2048;
-    int m3_buf = 0;
+    // mode 3 keeps no lists: the heap space holds each warp's 4 KB store
+    // box (1024-byte aligned)
+    uint32_t* m3_stage = reinterpret_cast<uint32_t*>(&sm.heap[0][0]) + ew * 1024;
     bool ok = true;
     float pn[BN / 32];  // column norms of the next tile, one per lane and chunk
 #pragma unroll
     for (int q = 0; q < BN / 32; ++q) {
       const int64_t c = (int64_t)t0 * BN + q * 32 + lane;
-      pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
+      pn[q] = c < sc && q >= qlo && q < qhi ? __ldg(norms_c + c) : 0.f;
     }
     for (int lt = 0; lt < nt; ++lt) {
       const int t = t0 + lt;
@@ -525,16 +532,17 @@ __global__ void __launch_bounds__(192, 1)
       tc::fence_after();
       // this tile's column norms, staged once (read back as broadcasts);
       // the next tile's are loaded now and land while this one is drained
-      float* ncs = sm.ncol[ew];
+      float* ncs = sm.ncol[ews];
 #pragma unroll
-      for (int q = 0; q < BN / 32; ++q) ncs[q * 32 + lane] = pn[q];
+      for (int q = 0; q < BN / 32; ++q)
+        if (q >= qlo && q < qhi) ncs[q * 32 + lane] = pn[q];
 #pragma unroll
       for (int q = 0; q < BN / 32; ++q) {
         const int64_t c = (int64_t)(t + 1) * BN + q * 32 + lane;
-        pn[q] = c < sc ? __ldg(norms_c + c) : 0.f;
+        pn[q] = c < sc && q >= qlo && q < qhi ? __ldg(norms_c + c) : 0.f;
       }
       if (mode == 3 && out_cmin)
-        for (int q = 0; q < BN / 32; ++q) sm.s[ew][lane][q] = kInf;
+        for (int q = qlo; q < qhi; ++q) sm.s[ews][lane][q] = kInf;
       __syncwarp();
       const uint32_t tacc = tmem + ((uint32_t)(32 * sub) << 16) + (uint32_t)(as * BN);
       // n_col - 2<a,b> for the 32 columns of chunk q, in place, and their
@@ -570,7 +578,7 @@ __global__ void __launch_bounds__(192, 1)
         if (keep) {
           // this lane's row: stage the passing values, then offer them to
           // the row's heap one by one
-          float* srow = sm.s[ew][lane];
+          float* srow = sm.s[ews][lane];
 #pragma unroll
           for (int j = 0; j < 32; ++j) srow[j] = v[j];
           do {
@@ -618,7 +626,7 @@ __global__ void __launch_bounds__(192, 1)
       // mode 3: the distances as 16-bit keys, two 32-column chunks (64
       // columns, one 128-byte row of the box) at a time behind one TMEM wait
 #pragma unroll 1
-      for (int q = 0; q < BN / 32 && mode == 3; q += 2) {
+      for (int q = qlo; q < qhi && mode == 3; q += 2) {
         const int64_t c0 = (int64_t)t * BN + q * 32;
         uint32_t ra[32], rb[32];
         tc::tmem_ld32_issue(tacc + (uint32_t)q * 32, ra);
@@ -631,8 +639,8 @@ __global__ void __launch_bounds__(192, 1)
         // keys staged in this warp's 32 x 64 box in shared memory (128-byte
         // rows, 16-byte pieces swizzled by row, as the tensor map's 128B
         // swizzle expects) and written by one bulk tensor store
-        uint32_t* buf = m3_stage + m3_buf * 1024;
-        if (lane == 0) tc::bulk_wait_read_le1();  // the store that read buf two pairs ago
+        uint32_t* buf = m3_stage;
+        if (lane == 0) tc::bulk_wait_read_all();  // this warp's last store has read the box
         __syncwarp();
         uint4* brow = reinterpret_cast<uint4*>(buf + lane * 32);
         float cm[2] = {kInf, kInf};  // each chunk's minimum for this row (fminf passes over a NaN)
@@ -683,21 +691,19 @@ __global__ void __launch_bounds__(192, 1)
         if (out_cmin) {
           // the lower ends of the minima's key buckets: the minimum of a
           // chunk's key lower ends
-          sm.s[ew][lane][q] = key16_floor(cm[0]);
-          sm.s[ew][lane][q + 1] = key16_floor(cm[1]);
+          sm.s[ews][lane][q] = key16_floor(cm[0]);
+          sm.s[ews][lane][q + 1] = key16_floor(cm[1]);
         }
         asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
         __syncwarp();
         if (lane == 0) tc::tma_store_2d(&to_d, buf, (int)c0, (int)(r0 + 32 * sub));
-        m3_buf ^= 1;
         __syncwarp();
       }
       if (mode == 3 && out_cmin && grow < s) {
-        // this row's chunk minima of the tile, BN / 32 floats, as 16-byte stores
-        float4* dst = reinterpret_cast<float4*>(out_cmin + grow * ldc + (int64_t)t * (BN / 32));
-        const float* src = sm.s[ew][lane];
-#pragma unroll
-        for (int j = 0; j < BN / 128; ++j) dst[j] = make_float4(src[4 * j], src[4 * j + 1], src[4 * j + 2], src[4 * j + 3]);
+        // this row's chunk minima of this warp's chunks, as 8-byte stores
+        float2* dst = reinterpret_cast<float2*>(out_cmin + grow * ldc + (int64_t)t * (BN / 32) + qlo);
+        const float* src = sm.s[ews][lane] + qlo;
+        for (int j = 0; j < (qhi - qlo) / 2; ++j) dst[j] = make_float2(src[2 * j], src[2 * j + 1]);
       }
       tc::fence_before();
       __syncwarp();
@@ -823,16 +829,20 @@ struct TileVariant {
   size_t smem;
 };
 
-static cudaError_t tile_variant(int32_t kc, int32_t bn, TileVariant* v) {
-  static std::atomic<bool> attr_set[4][64];
+static cudaError_t tile_variant(int32_t kc, int32_t bn, bool matrix, TileVariant* v) {
+  static std::atomic<bool> attr_set[8][64];
   const int stream = kc > MAX_KC_RES ? 1 : 0;
   const int narrow = bn == 128 ? 1 : 0;
-  const int which = 2 * stream + narrow;
+  const int which = 4 * (matrix ? 1 : 0) + 2 * stream + narrow;
   switch (which) {
-    case 0: v->fn = k_tile_topk_tc<false, 256>; v->smem = sizeof(SmemRes<256>); break;
-    case 1: v->fn = k_tile_topk_tc<false, 128>; v->smem = sizeof(SmemRes<128>); break;
-    case 2: v->fn = k_tile_topk_tc<true, 256>; v->smem = sizeof(SmemStr<256>); break;
-    default: v->fn = k_tile_topk_tc<true, 128>; v->smem = sizeof(SmemStr<128>); break;
+    case 0: v->fn = k_tile_topk_tc<false, 256, 4>; v->smem = sizeof(SmemRes<256>); break;
+    case 1: v->fn = k_tile_topk_tc<false, 128, 4>; v->smem = sizeof(SmemRes<128>); break;
+    case 2: v->fn = k_tile_topk_tc<true, 256, 4>; v->smem = sizeof(SmemStr<256>); break;
+    case 3: v->fn = k_tile_topk_tc<true, 128, 4>; v->smem = sizeof(SmemStr<128>); break;
+    case 4: v->fn = k_tile_topk_tc<false, 256, 8>; v->smem = sizeof(SmemRes<256>); break;
+    case 5: v->fn = k_tile_topk_tc<false, 128, 8>; v->smem = sizeof(SmemRes<128>); break;
+    case 6: v->fn = k_tile_topk_tc<true, 256, 8>; v->smem = sizeof(SmemStr<256>); break;
+    default: v->fn = k_tile_topk_tc<true, 128, 8>; v->smem = sizeof(SmemStr<128>); break;
   }
   v->smem += 1024;
   int dev = 0;
@@ -857,7 +867,7 @@ cudaError_t launch_tile_topk_tc(const float* xo, const float* norms, int64_t s, 
       !make_map(&mbl, lo, s, dk, BN_MAX))
     return cudaErrorInvalidValue;
   TileVariant v;
-  cudaError_t e = tile_variant(dk / BK, BN_MAX, &v);
+  cudaError_t e = tile_variant(dk / BK, BN_MAX, false, &v);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (s + BM - 1) / BM;
   CUtensorMap none;  // no matrix output in modes 0 and 1
@@ -902,7 +912,7 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   TileVariant v;
-  e = tile_variant(dk / BK, BN, &v);
+  e = tile_variant(dk / BK, BN, out_d != nullptr, &v);
   if (e != cudaSuccess) return e;
   const int64_t nrb = (na + BM - 1) / BM;
   // mode 3: split each row block's tiles over nsplit CTAs (one CTA per SM
@@ -928,7 +938,8 @@ cudaError_t launch_tile_cross_tc(const void* a_hi, const void* a_lo, const float
   long long spin_limit;
   int32_t hold;
   wait_policy(&spin_limit, &hold);
-  v.fn<<<(unsigned)(nrb * nsplit), 192, v.smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
+  // mode 3: eight epilogue warps (two per TMEM sub-partition); mode 2: four
+  v.fn<<<(unsigned)(nrb * nsplit), out_d ? 64 + 32 * 8 : 64 + 32 * 4, v.smem, st>>>(mah, mal, mbh, mbl, mo, a_norms, b_norms, na, nb, dk / BK,
                                                      out_d ? 3 : 2, out, out_d, ldo, out_cmin, ldc, nsplit, err,
                                                      spin_limit, hold);
   return cudaGetLastError();
