@@ -391,10 +391,11 @@ def run_reference(args):
     ef, efu, da, l1, xu, _, _ = beam
     oracle.set_threads(1)
     secs = []
-    for _ in range(args.steps):
+    for i in range(args.warmup + args.steps):
         t0 = time.perf_counter()
         oracle.search(idx, X, Q, k=K, ef=ef, ef_upper=efu, ef_l1=l1, descend_all=da, exact_upper=xu)
-        secs.append(time.perf_counter() - t0)
+        if i >= args.warmup:  # the first W steps are untimed warm-up
+            secs.append(time.perf_counter() - t0)
     qps = args.ref_nq / statistics.median(secs)
     sample = (f"FP64 oracle, own index on the first {args.ref_n} of the 1M mixture points (same generator; "
               f"layers {[int(s) for s in idx['sizes']]}), {args.ref_nq} queries per step answered sequentially on "
